@@ -1,0 +1,636 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU oracle for the FFT-based (Scoccimarro-type)
+ * polyspectrum estimator of Tomlinson, Jeong & Kim, arXiv:1904.11055.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file.
+ * Only tests/, __graft_entry__.smoke() and bench.py (its cpu_baseline leg and
+ * its --impl reference arm) load the shared library built from it.  It shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * Conventions (paper Sec. 1 for the transform pair, App. A for the discrete
+ * FFTW form):
+ *   forward  dhat(q) = sum_x delta(x) exp(-2 pi i q.x / N)      (unnormalised)
+ *   inverse  D(x)    = sum_q F(q)     exp(+2 pi i q.x / N)      (unnormalised)
+ *   grid index m in [0,N) carries the integer wavevector component
+ *   q = m for m < ceil(N/2), q = m - N otherwise.
+ *   Shell s (0-based) holds the q != 0 with edges[s]^2 <= |q|^2 < edges[s+1]^2,
+ *   the half-width binning |q - k_s| < dk/2 of Sec. 2 and App. A written as
+ *   edges k_s -/+ dk/2.
+ *
+ * Every routine is written in the order of the paper's equations; no blocking,
+ * fusion or reordering beyond what the definitions state.  Sums over grid cells
+ * are accumulated in FP64 in blocks of ORC_BLOCK cells (plain summation inside a
+ * block, plain summation of block totals), which is a rounding-order choice only.
+ *
+ * Return codes: 0 ok, negative on bad arguments / allocation failure / a check
+ * that failed (see orc_last_error()).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_BLOCK 4096
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+    double re, im;
+} cplx;
+
+static char g_err[256] = "";
+static int g_threads = 1;
+
+static int fail(int code, const char* msg) {
+    snprintf(g_err, sizeof g_err, "%s", msg);
+    return code;
+}
+
+const char* orc_last_error(void) { return g_err; }
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return g_threads; }
+
+/* ------------------------------------------------------------------------- */
+/* a tiny static-chunk parallel-for over [0, n) on g_threads pthreads         */
+/* ------------------------------------------------------------------------- */
+typedef void (*range_fn)(void* ctx, int64_t begin, int64_t end, int tid);
+
+typedef struct {
+    range_fn fn;
+    void* ctx;
+    int64_t begin, end;
+    int tid;
+} par_job;
+
+static void* par_trampoline(void* p) {
+    par_job* j = (par_job*)p;
+    j->fn(j->ctx, j->begin, j->end, j->tid);
+    return NULL;
+}
+
+static void par_for(int64_t n, range_fn fn, void* ctx) {
+    int nt = g_threads;
+    if (nt > n) nt = (int)(n > 0 ? n : 1);
+    if (nt <= 1) {
+        fn(ctx, 0, n, 0);
+        return;
+    }
+    pthread_t th[256];
+    par_job jobs[256];
+    if (nt > 256) nt = 256;
+    for (int t = 0; t < nt; t++) {
+        jobs[t].fn = fn;
+        jobs[t].ctx = ctx;
+        jobs[t].begin = n * t / nt;
+        jobs[t].end = n * (t + 1) / nt;
+        jobs[t].tid = t;
+        pthread_create(&th[t], NULL, par_trampoline, &jobs[t]);
+    }
+    for (int t = 0; t < nt; t++) pthread_join(th[t], NULL);
+}
+
+/* ------------------------------------------------------------------------- */
+/* own FFT: recursive mixed-radix decimation in time, any length              */
+/* X[k] = sum_{r<p} W_n^{r k} Y_r[k mod m],  Y_r = DFT_m(x[r], x[r+p], ...)  */
+/* with W_n = exp(sign * 2 pi i / n) and p the smallest prime factor of n.    */
+/* ------------------------------------------------------------------------- */
+static int smallest_factor(int n) {
+    for (int p = 2; p * p <= n; p++)
+        if (n % p == 0) return p;
+    return n;
+}
+
+static void fft_rec(cplx* out, const cplx* in, int n, int is, const cplx* tw, int ntw, cplx* tmp) {
+    if (n == 1) {
+        out[0] = in[0];
+        return;
+    }
+    int p = smallest_factor(n), m = n / p;
+    for (int r = 0; r < p; r++) fft_rec(out + (size_t)r * m, in + (size_t)r * is, m, is * p, tw, ntw, tmp);
+    int step = ntw / n;
+    for (int k = 0; k < n; k++) {
+        double ar = 0.0, ai = 0.0;
+        for (int r = 0; r < p; r++) {
+            cplx y = out[(size_t)r * m + (k % m)];
+            cplx w = tw[(size_t)(((int64_t)r * k) % n) * step];
+            ar += w.re * y.re - w.im * y.im;
+            ai += w.re * y.im + w.im * y.re;
+        }
+        tmp[k].re = ar;
+        tmp[k].im = ai;
+    }
+    memcpy(out, tmp, sizeof(cplx) * (size_t)n);
+}
+
+static cplx* twiddles(int n, int sign) {
+    cplx* tw = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+    if (!tw) return NULL;
+    for (int j = 0; j < n; j++) {
+        double a = 2.0 * ORC_PI * (double)j / (double)n;
+        tw[j].re = cos(a);
+        tw[j].im = sign * sin(a);
+    }
+    return tw;
+}
+
+/* in-place 1-D transform of n complex values spaced `stride` apart */
+int orc_fft1d(double* data, int n, int sign) {
+    if (n < 1 || (sign != 1 && sign != -1)) return fail(-1, "orc_fft1d: bad n or sign");
+    cplx* a = (cplx*)data;
+    cplx* tw = twiddles(n, sign);
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * 2 * (size_t)n);
+    if (!tw || !buf) return fail(-2, "orc_fft1d: out of memory");
+    fft_rec(buf, a, n, 1, tw, n, buf + n);
+    memcpy(a, buf, sizeof(cplx) * (size_t)n);
+    free(tw);
+    free(buf);
+    return 0;
+}
+
+typedef struct {
+    cplx* a;
+    int n[3];
+    int axis;
+    const cplx* tw;
+    cplx* scratch; /* per thread: 3 * n[axis] */
+} fft3_ctx;
+
+static void fft3_lines(void* vctx, int64_t begin, int64_t end, int tid) {
+    fft3_ctx* c = (fft3_ctx*)vctx;
+    int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
+    int len = c->n[c->axis];
+    cplx* line = c->scratch + (size_t)tid * 3 * len;
+    cplx* out = line + len;
+    cplx* tmp = out + len;
+    for (int64_t L = begin; L < end; L++) {
+        /* enumerate lines orthogonal to `axis` and their element stride */
+        size_t base, stride;
+        if (c->axis == 2) {
+            base = (size_t)L * n2;
+            stride = 1;
+        } else if (c->axis == 1) {
+            size_t i0 = (size_t)(L / n2), i2 = (size_t)(L % n2);
+            base = i0 * n1 * n2 + i2;
+            stride = (size_t)n2;
+        } else {
+            base = (size_t)L;
+            stride = (size_t)n1 * n2;
+        }
+        for (int t = 0; t < len; t++) line[t] = c->a[base + (size_t)t * stride];
+        fft_rec(out, line, len, 1, c->tw, len, tmp);
+        for (int t = 0; t < len; t++) c->a[base + (size_t)t * stride] = out[t];
+    }
+    (void)n0;
+}
+
+/* in-place 3-D transform of an n0 x n1 x n2 complex array (last index fastest) */
+int orc_fft3d(double* data, int n0, int n1, int n2, int sign) {
+    if (n0 < 1 || n1 < 1 || n2 < 1 || (sign != 1 && sign != -1)) return fail(-1, "orc_fft3d: bad args");
+    fft3_ctx c;
+    c.a = (cplx*)data;
+    c.n[0] = n0;
+    c.n[1] = n1;
+    c.n[2] = n2;
+    for (int axis = 0; axis < 3; axis++) {
+        int len = c.n[axis];
+        cplx* tw = twiddles(len, sign);
+        cplx* scratch = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)len * (size_t)(g_threads > 0 ? g_threads : 1));
+        if (!tw || !scratch) {
+            free(tw);
+            free(scratch);
+            return fail(-2, "orc_fft3d: out of memory");
+        }
+        c.axis = axis;
+        c.tw = tw;
+        c.scratch = scratch;
+        int64_t nlines = ((int64_t)n0 * n1 * n2) / len;
+        par_for(nlines, fft3_lines, &c);
+        free(tw);
+        free(scratch);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* shells (Sec. 2: |q - k_i| < dk/2, written with explicit edges)             */
+/* ------------------------------------------------------------------------- */
+static int freq_of(int m, int N) { return (m < (N + 1) / 2) ? m : m - N; }
+
+static int shell_of_q2(int64_t q2, int nshell, const double* edges) {
+    if (q2 == 0) return -1;
+    double d = (double)q2;
+    for (int s = 0; s < nshell; s++)
+        if (edges[s] * edges[s] <= d && d < edges[s + 1] * edges[s + 1]) return s;
+    return -1;
+}
+
+/* shell index (or -1) of every grid mode, laid out like the N^3 grid */
+int orc_shell_map(int N, int nshell, const double* edges, int32_t* shell) {
+    if (N < 2 || nshell < 1) return fail(-1, "orc_shell_map: bad args");
+    for (int s = 0; s < nshell; s++)
+        if (!(edges[s] >= 0.0 && edges[s + 1] > edges[s])) return fail(-1, "orc_shell_map: edges must increase");
+    for (int a = 0; a < N; a++)
+        for (int b = 0; b < N; b++)
+            for (int c = 0; c < N; c++) {
+                int64_t qa = freq_of(a, N), qb = freq_of(b, N), qc = freq_of(c, N);
+                shell[((size_t)a * N + b) * N + c] = shell_of_q2(qa * qa + qb * qb + qc * qc, nshell, edges);
+            }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* bins: k_1 >= k_2 >= ... >= k_n, row-major with k_n fastest (Sec. 4.2),     */
+/* kept when the polygon inequality k_1 <= k_2 + ... + k_n holds on the       */
+/* shell centres (App. B, Eq. polygon).  rule 1 keeps every sorted tuple.     */
+/* Bins are reported with 1-based shell numbers, as in the paper.             */
+/* ------------------------------------------------------------------------- */
+static int64_t bins_rec(int order, int nshell, int rule, const double* centre, int depth, int* cur, int* out,
+                        int64_t nb) {
+    if (depth == order) {
+        double rest = 0.0;
+        for (int t = 1; t < order; t++) rest += centre[cur[t] - 1];
+        if (rule == 1 || centre[cur[0] - 1] <= rest + 1e-9 * centre[cur[0] - 1]) {
+            if (out)
+                for (int t = 0; t < order; t++) out[nb * order + t] = cur[t];
+            nb++;
+        }
+        return nb;
+    }
+    int hi = depth == 0 ? nshell : cur[depth - 1];
+    for (int v = 1; v <= hi; v++) {
+        cur[depth] = v;
+        nb = bins_rec(order, nshell, rule, centre, depth + 1, cur, out, nb);
+    }
+    return nb;
+}
+
+int64_t orc_enumerate_bins(int nshell, const double* edges, int order, int rule, int32_t* out) {
+    if (nshell < 1 || order < 2 || order > 8) return fail(-1, "orc_enumerate_bins: bad args");
+    double* centre = (double*)malloc(sizeof(double) * (size_t)nshell);
+    int cur[8];
+    for (int s = 0; s < nshell; s++) centre[s] = 0.5 * (edges[s] + edges[s + 1]);
+    int64_t nb = bins_rec(order, nshell, rule, centre, 0, cur, (int*)out, 0);
+    free(centre);
+    return nb;
+}
+
+/* ------------------------------------------------------------------------- */
+/* forward transform of a real field: dhat(q) = sum_x delta(x) e^{-i q.x}     */
+/* ------------------------------------------------------------------------- */
+int orc_forward(int N, const double* delta, double* dhat /* 2*N^3, interleaved complex */) {
+    size_t n3 = (size_t)N * N * N;
+    cplx* a = (cplx*)dhat;
+    for (size_t i = 0; i < n3; i++) {
+        a[i].re = delta[i];
+        a[i].im = 0.0;
+    }
+    return orc_fft3d(dhat, N, N, N, -1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* shell fields: D_s(x) = sum_{q in S_s} F(q) e^{+i q.x}  (Eq. Bkfast; App. A) */
+/* With F = dhat this is I_{k_s}[x] up to the (2 pi)^3/N^3 factor of App. A;  */
+/* with F = 1 it is the counting field iota_{k_s}[x] (Eq. Vn).                 */
+/* `imag_max` (optional) receives max |Im D| / max |Re D| over the shells.     */
+/* ------------------------------------------------------------------------- */
+int orc_shell_fields(int N, const double* dhat /* complex N^3, or NULL for F = 1 */, const int32_t* shell_map,
+                     int nsel, const int32_t* shells /* 0-based shells to build */,
+                     double* fields /* nsel * N^3 */, double* imag_max) {
+    size_t n3 = (size_t)N * N * N;
+    cplx* work = (cplx*)malloc(sizeof(cplx) * n3);
+    if (!work) return fail(-2, "orc_shell_fields: out of memory");
+    double worst = 0.0;
+    for (int t = 0; t < nsel; t++) {
+        int s = shells[t];
+        const cplx* F = (const cplx*)dhat;
+        for (size_t i = 0; i < n3; i++) {
+            if (shell_map[i] == s) {
+                work[i].re = F ? F[i].re : 1.0;
+                work[i].im = F ? F[i].im : 0.0;
+            } else {
+                work[i].re = 0.0;
+                work[i].im = 0.0;
+            }
+        }
+        int rc = orc_fft3d((double*)work, N, N, N, +1);
+        if (rc) {
+            free(work);
+            return rc;
+        }
+        double mre = 0.0, mim = 0.0;
+        double* f = fields + (size_t)t * n3;
+        for (size_t i = 0; i < n3; i++) {
+            f[i] = work[i].re;
+            if (fabs(work[i].re) > mre) mre = fabs(work[i].re);
+            if (fabs(work[i].im) > mim) mim = fabs(work[i].im);
+        }
+        double r = mre > 0.0 ? mim / mre : mim;
+        if (r > worst) worst = r;
+    }
+    if (imag_max) *imag_max = worst;
+    free(work);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* product sums over the grid (Eq. estimator, discrete form of App. A):       */
+/*   S_b = sum_x prod_t D_{b_t}(x),   A_b = sum_x |prod_t D_{b_t}(x)|        */
+/* `slot` maps a 1-based shell number to its row in `fields` (or -1).         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    size_t n3;
+    int order;
+    const double* fields;
+    const int32_t* slot;
+    const int32_t* bins;
+    double* S;
+    double* A;
+} sums_ctx;
+
+static void sums_range(void* vctx, int64_t begin, int64_t end, int tid) {
+    sums_ctx* c = (sums_ctx*)vctx;
+    (void)tid;
+    for (int64_t b = begin; b < end; b++) {
+        const double* f[8];
+        for (int t = 0; t < c->order; t++) f[t] = c->fields + (size_t)c->slot[c->bins[b * c->order + t]] * c->n3;
+        double tot = 0.0, atot = 0.0;
+        for (size_t x0 = 0; x0 < c->n3; x0 += ORC_BLOCK) {
+            size_t x1 = x0 + ORC_BLOCK < c->n3 ? x0 + ORC_BLOCK : c->n3;
+            double blk = 0.0, ablk = 0.0;
+            for (size_t x = x0; x < x1; x++) {
+                double p = 1.0;
+                for (int t = 0; t < c->order; t++) p *= f[t][x];
+                blk += p;
+                ablk += fabs(p);
+            }
+            tot += blk;
+            atot += ablk;
+        }
+        c->S[b] = tot;
+        if (c->A) c->A[b] = atot;
+    }
+}
+
+int orc_product_sums(int N, const double* fields, const int32_t* slot, int order, int64_t nbins, const int32_t* bins,
+                     double* S, double* A) {
+    sums_ctx c = {(size_t)N * N * N, order, fields, slot, bins, S, A};
+    for (int64_t b = 0; b < nbins * order; b++)
+        if (slot[bins[b]] < 0) return fail(-1, "orc_product_sums: bin uses a shell with no field");
+    par_for(nbins, sums_range, &c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* whole estimator (Eqs. estimator, volume, Vn; App. A):                      */
+/*   count_b = (1/N^3) sum_x prod iota  (an integer: the number of closed     */
+/*             n-gons of grid modes, Eq. Ncalc with V_f = k_F^3)              */
+/*   B_b     = (V^{n-1}/N^{3n}) * S_b / (N^3 count_b)                         */
+/*   R_b     = S_b / (N^3 count_b),  scale_b = A_b / (N^3 count_b)            */
+/* Only the shells used by `bins` are transformed, so a sample of bins at a   */
+/* large N costs one inverse FFT per distinct shell.                          */
+/* ------------------------------------------------------------------------- */
+int orc_estimate(int N, double L, const double* delta, int nshell, const double* edges, int order, int64_t nbins,
+                 const int32_t* bins, double* B, double* R, double* scale, int64_t* counts, double* S_out,
+                 double* imag_max) {
+    if (N < 2 || L <= 0.0 || order < 2 || order > 8 || nbins < 0) return fail(-1, "orc_estimate: bad args");
+    size_t n3 = (size_t)N * N * N;
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    int32_t* slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nshell + 1));
+    int32_t* sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)nshell);
+    if (!smap || !slot || !sel) return fail(-2, "orc_estimate: out of memory");
+    int rc = orc_shell_map(N, nshell, edges, smap);
+    if (rc) return rc;
+    for (int s = 0; s <= nshell; s++) slot[s] = -1;
+    int nsel = 0;
+    for (int64_t i = 0; i < nbins * order; i++) {
+        int k = bins[i];
+        if (k < 1 || k > nshell) return fail(-1, "orc_estimate: bin shell out of range");
+        if (slot[k] < 0) {
+            slot[k] = nsel;
+            sel[nsel++] = k - 1;
+        }
+    }
+    double* dhat = (double*)malloc(sizeof(double) * 2 * n3);
+    double* fields = (double*)malloc(sizeof(double) * n3 * (size_t)(nsel > 0 ? nsel : 1));
+    double* S = (double*)malloc(sizeof(double) * (size_t)(nbins > 0 ? nbins : 1));
+    double* A = (double*)malloc(sizeof(double) * (size_t)(nbins > 0 ? nbins : 1));
+    double* C = (double*)malloc(sizeof(double) * (size_t)(nbins > 0 ? nbins : 1));
+    if (!dhat || !fields || !S || !A || !C) return fail(-2, "orc_estimate: out of memory");
+    double im1 = 0.0, im2 = 0.0;
+    rc = orc_forward(N, delta, dhat);
+    if (!rc) rc = orc_shell_fields(N, dhat, smap, nsel, sel, fields, &im1);
+    if (!rc) rc = orc_product_sums(N, fields, slot, order, nbins, bins, S, A);
+    /* counting fields: the same pipeline on a grid of unity (Sec. 4) */
+    if (!rc) rc = orc_shell_fields(N, NULL, smap, nsel, sel, fields, &im2);
+    if (!rc) rc = orc_product_sums(N, fields, slot, order, nbins, bins, C, NULL);
+    if (!rc) {
+        double n3d = (double)n3;
+        double norm = pow(L * L * L, order - 1) / pow(n3d, order);
+        for (int64_t b = 0; b < nbins; b++) {
+            double v = C[b] / n3d;
+            double r = nearbyint(v);
+            if (fabs(v - r) > 1e-6) {
+                rc = fail(-3, "orc_estimate: polygon count is not an integer");
+                break;
+            }
+            int64_t cnt = (int64_t)r;
+            if (counts) counts[b] = cnt;
+            if (S_out) S_out[b] = S[b];
+            double den = n3d * (double)cnt;
+            if (R) R[b] = cnt > 0 ? S[b] / den : 0.0;
+            if (scale) scale[b] = cnt > 0 ? A[b] / den : 0.0;
+            if (B) B[b] = cnt > 0 ? norm * S[b] / den : 0.0;
+        }
+    }
+    if (imag_max) *imag_max = im1 > im2 ? im1 : im2;
+    free(smap);
+    free(slot);
+    free(sel);
+    free(dhat);
+    free(fields);
+    free(S);
+    free(A);
+    free(C);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* direct sampling of polygons (Eq. estimateBk and its n-gon form): loop over */
+/* q_1..q_{n-1} in their shells, close with q_n = -(q_1+...+q_{n-1}) mod N,  */
+/* keep the tuple when q_n lies in shell k_n.                                 */
+/*   S_b = N^3 * Re sum prod dhat(q_t),   count_b = number of such tuples    */
+/* `dhat` may be NULL (a grid of unity: only counts).                         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int N, order, nshell;
+    const cplx* dhat;
+    const int32_t* smap;
+    const int32_t* bins;
+    int32_t** modes; /* per shell: flat grid indices */
+    int32_t* nmodes;
+    double* S;
+    int64_t* counts;
+} direct_ctx;
+
+static void direct_range(void* vctx, int64_t begin, int64_t end, int tid) {
+    direct_ctx* c = (direct_ctx*)vctx;
+    (void)tid;
+    int N = c->N, n = c->order;
+    for (int64_t b = begin; b < end; b++) {
+        const int32_t* k = c->bins + b * n;
+        int idx[8];
+        int64_t cnt = 0;
+        double sre = 0.0, sim = 0.0;
+        int depth = 0;
+        idx[0] = -1;
+        /* iterative odometer over q_1 .. q_{n-1} */
+        while (depth >= 0) {
+            idx[depth]++;
+            if (idx[depth] >= c->nmodes[k[depth] - 1]) {
+                depth--;
+                continue;
+            }
+            if (depth < n - 2) {
+                depth++;
+                idx[depth] = -1;
+                continue;
+            }
+            int sa = 0, sb = 0, sc = 0;
+            double pre = 1.0, pim = 0.0;
+            for (int t = 0; t < n - 1; t++) {
+                int32_t g = c->modes[k[t] - 1][idx[t]];
+                int a = g / (N * N), bb = (g / N) % N, cc = g % N;
+                sa += a;
+                sb += bb;
+                sc += cc;
+                if (c->dhat) {
+                    double r2 = pre * c->dhat[g].re - pim * c->dhat[g].im;
+                    double i2 = pre * c->dhat[g].im + pim * c->dhat[g].re;
+                    pre = r2;
+                    pim = i2;
+                }
+            }
+            int la = ((-sa) % N + N) % N, lb = ((-sb) % N + N) % N, lc = ((-sc) % N + N) % N;
+            int32_t gl = ((int32_t)la * N + lb) * N + lc;
+            if (c->smap[gl] == k[n - 1] - 1) {
+                cnt++;
+                if (c->dhat) {
+                    sre += pre * c->dhat[gl].re - pim * c->dhat[gl].im;
+                    sim += pre * c->dhat[gl].im + pim * c->dhat[gl].re;
+                }
+            }
+        }
+        c->counts[b] = cnt;
+        if (c->S) c->S[b] = (double)N * N * N * sre;
+        (void)sim;
+    }
+}
+
+int orc_direct_sample(int N, const double* delta /* NULL: counts only */, int nshell, const double* edges, int order,
+                      int64_t nbins, const int32_t* bins, double* S, int64_t* counts) {
+    if (N < 2 || order < 2 || order > 8) return fail(-1, "orc_direct_sample: bad args");
+    size_t n3 = (size_t)N * N * N;
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    int rc = orc_shell_map(N, nshell, edges, smap);
+    if (rc) return rc;
+    int32_t** modes = (int32_t**)calloc((size_t)nshell, sizeof(int32_t*));
+    int32_t* nm = (int32_t*)calloc((size_t)nshell, sizeof(int32_t));
+    for (size_t i = 0; i < n3; i++)
+        if (smap[i] >= 0) nm[smap[i]]++;
+    for (int s = 0; s < nshell; s++) modes[s] = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nm[s] + 1));
+    int32_t* fill = (int32_t*)calloc((size_t)nshell, sizeof(int32_t));
+    for (size_t i = 0; i < n3; i++)
+        if (smap[i] >= 0) modes[smap[i]][fill[smap[i]]++] = (int32_t)i;
+    double* dhat = NULL;
+    if (delta) {
+        dhat = (double*)malloc(sizeof(double) * 2 * n3);
+        rc = orc_forward(N, delta, dhat);
+    }
+    if (!rc) {
+        direct_ctx c = {N, order, nshell, (const cplx*)dhat, smap, bins, modes, nm, delta ? S : NULL, counts};
+        par_for(nbins, direct_range, &c);
+    }
+    for (int s = 0; s < nshell; s++) free(modes[s]);
+    free(modes);
+    free(nm);
+    free(fill);
+    free(smap);
+    free(dhat);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* adjoint of the estimator for L = sum_b g_b B_b (g = dL/dB).                */
+/* B_b = c_b S_b with c_b = V^{n-1}/N^{3n} / (N^3 count_b) and               */
+/* S_b = sum_x prod_t D_{b_t}(x); D_m = inverse(mask_m * forward(delta)).    */
+/*   G_m(x) = dL/dD_m(x) = sum_b g_b c_b sum_{t: b_t = m} prod_{u != t} D_{b_u}(x) */
+/*   dL/ddelta(y) = sum_m sum_x G_m(x) K_m(x - y),  K_m(r) = sum_{q in S_m} e^{i q.r} */
+/*               = sum_q [sum_m mask_m(q) Ghat_m(q)] e^{+i q.y}               */
+/* with Ghat_m(q) = sum_x G_m(x) e^{-i q.x} (K_m is real and even).          */
+/* `counts` must be the bins' exact polygon counts.                           */
+/* ------------------------------------------------------------------------- */
+int orc_gradient(int N, double L, const double* delta, int nshell, const double* edges, int order, int64_t nbins,
+                 const int32_t* bins, const int64_t* counts, const double* dLdB, double* grad) {
+    if (N < 2 || order < 2 || order > 8) return fail(-1, "orc_gradient: bad args");
+    size_t n3 = (size_t)N * N * N;
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    int rc = orc_shell_map(N, nshell, edges, smap);
+    if (rc) return rc;
+    int32_t* all = (int32_t*)malloc(sizeof(int32_t) * (size_t)nshell);
+    int32_t* slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nshell + 1));
+    slot[0] = -1;
+    for (int s = 0; s < nshell; s++) {
+        all[s] = s;
+        slot[s + 1] = s;
+    }
+    double* dhat = (double*)malloc(sizeof(double) * 2 * n3);
+    double* D = (double*)malloc(sizeof(double) * n3 * (size_t)nshell);
+    double* G = (double*)calloc(n3 * (size_t)nshell, sizeof(double));
+    cplx* H = (cplx*)calloc(n3, sizeof(cplx));
+    cplx* work = (cplx*)malloc(sizeof(cplx) * n3);
+    if (!dhat || !D || !G || !H || !work) return fail(-2, "orc_gradient: out of memory");
+    rc = orc_forward(N, delta, dhat);
+    if (!rc) rc = orc_shell_fields(N, dhat, smap, nshell, all, D, NULL);
+    if (!rc) {
+        double n3d = (double)n3;
+        double norm = pow(L * L * L, order - 1) / pow(n3d, order);
+        for (int64_t b = 0; b < nbins; b++) {
+            if (counts[b] <= 0) continue;
+            double w = dLdB[b] * norm / (n3d * (double)counts[b]);
+            const int32_t* k = bins + b * order;
+            for (int t = 0; t < order; t++) {
+                double* g = G + (size_t)(k[t] - 1) * n3;
+                for (size_t x = 0; x < n3; x++) {
+                    double p = w;
+                    for (int u = 0; u < order; u++)
+                        if (u != t) p *= D[(size_t)(k[u] - 1) * n3 + x];
+                    g[x] += p;
+                }
+            }
+        }
+        for (int m = 0; m < nshell && !rc; m++) {
+            const double* g = G + (size_t)m * n3;
+            for (size_t x = 0; x < n3; x++) {
+                work[x].re = g[x];
+                work[x].im = 0.0;
+            }
+            rc = orc_fft3d((double*)work, N, N, N, -1);
+            for (size_t q = 0; q < n3 && !rc; q++)
+                if (smap[q] == m) H[q] = work[q];
+        }
+    }
+    if (!rc) rc = orc_fft3d((double*)H, N, N, N, +1);
+    if (!rc)
+        for (size_t x = 0; x < n3; x++) grad[x] = H[x].re;
+    free(smap);
+    free(all);
+    free(slot);
+    free(dhat);
+    free(D);
+    free(G);
+    free(H);
+    free(work);
+    return rc;
+}

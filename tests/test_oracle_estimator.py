@@ -1,0 +1,252 @@
+"""Pins for the FP64 oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something other than itself:
+  * shell membership and bin enumeration: independent numpy / itertools code;
+  * polygon counts: direct enumeration of closed n-gons (Sec. 4, Eq. Ncalc) and
+    the golden file written from that enumeration;
+  * product sums: brute-force direct sampling of all triangles / quadrilaterals
+    (Eq. estimateBk and its n-gon form);
+  * n = 2: the textbook shell-averaged power spectrum from numpy.fft;
+  * plane waves: closed forms for the connected and the disconnected case;
+  * iid skewed noise: E[B] = kappa_3 (V/N^3)^2 for every bin (normalisation);
+  * Gaussian fields: near-zero mean bispectrum;
+  * analytic triangle counts (Eq. Ntri) within the paper's stated accuracy;
+  * the adjoint: central finite differences of the estimator.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import fieldgen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def np_shell_map(N, edges):
+    m = np.fft.fftfreq(N) * N
+    qx, qy, qz = np.meshgrid(m, m, m, indexing="ij")
+    q2 = qx * qx + qy * qy + qz * qz
+    out = -np.ones((N, N, N), dtype=np.int32)
+    for s in range(len(edges) - 1):
+        sel = (q2 >= edges[s] ** 2) & (q2 < edges[s + 1] ** 2) & (q2 > 0)
+        out[sel] = s
+    return out
+
+
+def itertools_bins(nshell, order, centres=None, all_sorted=False):
+    c = np.arange(1, nshell + 1, dtype=float) if centres is None else np.asarray(centres)
+    out = []
+    for k in itertools.product(range(nshell, 0, -1), repeat=order):
+        if any(k[t] < k[t + 1] for t in range(order - 1)):
+            continue
+        if all_sorted or c[k[0] - 1] <= sum(c[v - 1] for v in k[1:]) + 1e-9:
+            out.append(k)
+    out.sort()  # row-major order, k_n fastest, ascending
+    return np.array(out, dtype=np.int32).reshape(-1, order)
+
+
+# --------------------------------------------------------------------------- shells and bins
+@pytest.mark.parametrize("N,width,nshell,first", [(16, 1.0, 7, 0), (20, 1.0, 9, 0), (24, 1.5, 7, 0), (15, 1.0, 7, 0),
+                                                  (16, 1.0, 4, 2)])
+def test_shell_map_matches_numpy(N, width, nshell, first):
+    e = fieldgen.unit_edges(nshell + first, width)[first:]
+    assert np.array_equal(oracle.shell_map(N, e), np_shell_map(N, e))
+
+
+@pytest.mark.parametrize("nshell,order,width,expected", [(16, 3, 1.0, 508), (64, 3, 1.0, 24432),
+                                                         (32, 4, 1.5, 45135), (32, 3, 1.0, 3384)])
+def test_bin_enumeration(nshell, order, width, expected):
+    e = fieldgen.unit_edges(nshell, width)
+    got = oracle.enumerate_bins(e, order)
+    assert got.shape == (expected, order)
+    if nshell <= 32:
+        ref = itertools_bins(nshell, order, centres=width * np.arange(1, nshell + 1))
+        assert np.array_equal(got, ref)
+    # paper order: k_1 >= ... >= k_n, row-major with k_n fastest
+    assert np.all(np.diff(got, axis=1) <= 0)
+    keys = [tuple(r) for r in got]
+    assert keys == sorted(keys)
+
+
+def test_all_sorted_rule():
+    e = fieldgen.unit_edges(6)
+    got = oracle.enumerate_bins(e, 3, oracle.RULE_ALL_SORTED)
+    assert np.array_equal(got, itertools_bins(6, 3, all_sorted=True))
+
+
+# --------------------------------------------------------------------------- counts
+def _golden_counts(name):
+    path = os.path.join(GOLDEN, name)
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return np.array([[int(v) for v in r] for r in rows], dtype=np.int64)
+
+
+def test_counts_match_golden_enumeration():
+    g = _golden_counts("counts_n3_N16_unit6.txt")
+    e = fieldgen.unit_edges(6)
+    r = oracle.estimate(np.zeros((16, 16, 16)), 1.0, e, 3, bins=g[:, :3].astype(np.int32))
+    assert np.array_equal(r["counts"], g[:, 3])
+
+
+@pytest.mark.parametrize("N,order,width,nshell", [(16, 3, 1.0, 6), (20, 3, 1.0, 5), (16, 3, 1.5, 4),
+                                                  (12, 4, 1.0, 4), (15, 3, 1.0, 4)])
+def test_counts_match_direct_enumeration(N, order, width, nshell):
+    e = fieldgen.unit_edges(nshell, width)
+    bins = oracle.enumerate_bins(e, order, oracle.RULE_ALL_SORTED)
+    r = oracle.estimate(np.zeros((N, N, N)), 1.0, e, order, bins=bins)
+    _, cnt = oracle.direct_sample(None, e, order, bins, N=N)
+    assert np.array_equal(r["counts"], cnt)
+
+
+def test_counts_n2_are_mode_counts():
+    N, e = 16, fieldgen.unit_edges(6)
+    bins = oracle.enumerate_bins(e, 2, oracle.RULE_ALL_SORTED)
+    r = oracle.estimate(np.zeros((N, N, N)), 1.0, e, 2, bins=bins)
+    smap = np_shell_map(N, e)
+    for (i, j), c in zip(bins, r["counts"]):
+        assert c == (np.sum(smap == i - 1) if i == j else 0)
+
+
+def test_triangle_counts_follow_eq_ntri():
+    """Eq. Ntri (8 pi^2 k1 k2 k3 dk^3, 4 pi^2 when folded) is good to 10-20 % (Sec. 4.2)."""
+    N, e = 48, fieldgen.unit_edges(12)
+    r = oracle.estimate(np.zeros((N, N, N)), 1.0, e, 3)
+    k = r["bins"].astype(float)
+    ntri = np.where(k[:, 0] == k[:, 1] + k[:, 2], 4.0, 8.0) * np.pi ** 2 * k.prod(axis=1)
+    ratio = r["counts"] / ntri
+    big = k[:, 2] >= 5
+    assert big.sum() > 20
+    assert np.all((ratio[big] > 0.75) & (ratio[big] < 1.45))
+    assert abs(np.median(ratio[big]) - 1.0) < 0.05
+
+
+# --------------------------------------------------------------------------- product sums
+@pytest.mark.parametrize("N,order,nshell,kind,seed", [(16, 3, 6, "white", 1), (18, 3, 5, "lognormal", 2),
+                                                      (12, 4, 4, "white", 3), (16, 2, 6, "white", 4)])
+def test_sums_match_direct_sampling(N, order, nshell, kind, seed):
+    e = fieldgen.unit_edges(nshell)
+    d = fieldgen.field(kind, N, seed, np.float64)
+    r = oracle.estimate(d, 1.0, e, order)
+    S, cnt = oracle.direct_sample(d, e, order, r["bins"])
+    assert np.array_equal(cnt, r["counts"])
+    tol = 1e-12 * r["scale"] * N ** 3 * r["counts"]
+    assert np.all(np.abs(S - r["S"]) <= tol + 1e-300)
+    assert r["imag_max"] < 1e-12
+
+
+def test_power_spectrum_textbook():
+    """n = 2 reduces to P(k) = V/N^6 <|dhat(q)|^2> over the shell (App. A with n = 2)."""
+    N, L, e = 24, 300.0, fieldgen.unit_edges(9)
+    d = fieldgen.field("gaussian", N, 11, np.float64)
+    r = oracle.estimate(d, L, e, 2, bins=np.array([[i, i] for i in range(1, 10)], dtype=np.int32))
+    dk = np.fft.fftn(d)
+    smap = np_shell_map(N, e)
+    for s in range(9):
+        sel = smap == s
+        pk = L ** 3 / N ** 6 * np.mean(np.abs(dk[sel]) ** 2)
+        assert r["counts"][s] == sel.sum()
+        assert abs(r["B"][s] - pk) <= 1e-12 * pk
+
+
+def _wave_field(N, waves):
+    return fieldgen.plane_waves(N, waves)
+
+
+def test_plane_waves_bispectrum_closed_form():
+    N, L = 16, 200.0
+    e = fieldgen.unit_edges(6)
+    q1, q2 = np.array([3, 0, 0]), np.array([0, 2, 0])
+    q3 = -(q1 + q2)  # |q3|^2 = 13 -> shell 4
+    A = [1.3, 0.7, 0.9]
+    phi = [0.4, -1.1, 2.0]
+    d = _wave_field(N, [(q1, A[0], phi[0]), (q2, A[1], phi[1]), (q3, A[2], phi[2])])
+    r = oracle.estimate(d, L, e, 3, rule=oracle.RULE_ALL_SORTED)
+    n3 = N ** 3
+    S_closed = n3 * 2.0 * (n3 / 2.0) ** 3 * A[0] * A[1] * A[2] * np.cos(sum(phi))
+    idx = [i for i, b in enumerate(r["bins"]) if tuple(b) == (4, 3, 2)][0]
+    assert abs(r["S"][idx] - S_closed) < 1e-10 * abs(S_closed)
+    _, cnt = oracle.direct_sample(None, e, 3, r["bins"][idx:idx + 1], N=N)
+    B_closed = (L ** 3) ** 2 / n3 ** 3 * S_closed / (n3 * cnt[0])
+    assert abs(r["B"][idx] - B_closed) < 1e-10 * abs(B_closed)
+    others = np.delete(r["S"], idx)
+    assert np.abs(others).max() < 1e-9 * abs(S_closed)
+
+
+def test_plane_waves_trispectrum_closed_forms():
+    N, L = 16, 200.0
+    e = fieldgen.unit_edges(6)
+    q1, q2, q3 = np.array([2, 0, 0]), np.array([0, 3, 0]), np.array([0, 0, 4])
+    q4 = -(q1 + q2 + q3)  # |q4|^2 = 29 -> shell 5
+    A = [1.1, 0.8, 1.4, 0.6]
+    phi = [0.3, 1.2, -0.5, 0.9]
+    d = _wave_field(N, [(q1, A[0], phi[0]), (q2, A[1], phi[1]), (q3, A[2], phi[2]), (q4, A[3], phi[3])])
+    want = np.array([[5, 4, 3, 2], [3, 3, 2, 2]], dtype=np.int32)
+    r = oracle.estimate(d, L, e, 4, bins=want)
+    n3 = N ** 3
+    connected = n3 * 2.0 * (n3 / 2.0) ** 4 * np.prod(A) * np.cos(sum(phi))
+    paired = n3 * 4.0 * (n3 / 2.0) ** 4 * A[0] ** 2 * A[1] ** 2
+    assert abs(r["S"][0] - connected) < 1e-10 * abs(connected)
+    assert abs(r["S"][1] - paired) < 1e-10 * abs(paired)
+
+
+def test_iid_skewed_noise_normalisation():
+    """iid noise with third cumulant k3 has B(k1,k2,k3) = k3 (V/N^3)^2 in every bin (Sec. 1 convention)."""
+    N, L, e = 32, 500.0, fieldgen.unit_edges(10)
+    p = 0.2
+    k3 = p * (1 - p) * (1 - 2 * p)
+    vals = []
+    for seed in range(6):
+        d = (np.random.default_rng(100 + seed).random((N, N, N)) < p).astype(float) - p
+        r = oracle.estimate(d, L, e, 3)
+        vals.append(r["B"] / (L ** 3 / N ** 3) ** 2)
+    vals = np.array(vals)
+    mean, err = vals.mean(), vals.std() / np.sqrt(vals.size)
+    assert abs(mean - k3) < 4 * err + 0.02 * k3
+    assert err < 0.15 * k3
+
+
+def test_gaussian_mean_bispectrum_near_zero():
+    N, e = 24, fieldgen.unit_edges(8)
+    ratios = []
+    for seed in range(8):
+        d = fieldgen.field("gaussian", N, 500 + seed, np.float64)
+        r = oracle.estimate(d, 1.0, e, 3)
+        ratios.append(r["R"] / r["scale"])
+    ratios = np.array(ratios)
+    mean, err = ratios.mean(), ratios.std() / np.sqrt(ratios.size)
+    assert abs(mean) < 4 * err
+
+
+def test_lognormal_bispectrum_is_positive_on_average():
+    """A lognormal field is positively skewed: its mean bispectrum is positive (sanity of the sign)."""
+    N, e = 24, fieldgen.unit_edges(8)
+    d = fieldgen.field("lognormal", N, 9, np.float64)
+    r = oracle.estimate(d, 1.0, e, 3)
+    assert np.mean(r["B"]) > 0
+
+
+# --------------------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("order,nshell", [(3, 4), (4, 3)])
+def test_gradient_matches_central_differences(order, nshell):
+    N, L = 12, 100.0
+    e = fieldgen.unit_edges(nshell)
+    rng = np.random.default_rng(42 + order)
+    d = rng.standard_normal((N, N, N))
+    r = oracle.estimate(d, L, e, order)
+    w = rng.standard_normal(len(r["bins"]))
+    g = oracle.gradient(d, L, e, order, r["bins"], r["counts"], w)
+
+    def loss(x):
+        return float(np.dot(w, oracle.estimate(x, L, e, order, bins=r["bins"])["B"]))
+
+    h = 1e-3
+    for v in rng.choice(N ** 3, size=6, replace=False):
+        i = np.unravel_index(v, d.shape)
+        dp, dm = d.copy(), d.copy()
+        dp[i] += h
+        dm[i] -= h
+        fd = (loss(dp) - loss(dm)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * (abs(g[i]) + np.abs(g).max() * 1e-3)
