@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the polyspectrum estimator on GB300.
+
+One step = one poly_estimate of one 256^3 lognormal field with 64 unit-width
+shells (n = 3, 24,432 triangle bins): forward transform, 64 shell fields,
+product-sum contraction, reduction and normalisation (counts are plan-time).
+The metric is configs/s = output bins per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank estimates its own field (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.  `--impl reference` times the FP64
+CPU oracle (the plain definition of the method) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bispectrum configs/s at 256³ N_max=64, split-BF16 vs FP32 on GB300 at rel err ≤1e-5"
+N, L, NSHELL, ORDER, SEED = 256, 1000.0, 64, 3, 2
+WORKLOAD = "bispectrum, 256^3 lognormal field (seed 2), 64 unit shells k_F..64k_F, n=3, 24432 bins"
+SAMPLE_SHELLS = (59, 60, 61, 62, 63, 64)  # CPU baseline sample: the bins among these shells
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1904_11055_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, src_files):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != source_hash(*src_files):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(delta_f32):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    import numpy as np
+
+    import fieldgen
+    import oracle
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    edges = fieldgen.unit_edges(NSHELL)
+    allb = oracle.enumerate_bins(edges, ORDER)
+    sel = np.array([i for i, b in enumerate(allb) if set(b.tolist()) <= set(SAMPLE_SHELLS)])
+    t0 = time.perf_counter()
+    oracle.estimate(delta_f32.astype(np.float64), L, edges, ORDER, bins=allb[sel])
+    dt = time.perf_counter() - t0
+    return {"value": len(sel) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sel)} bins among shells {SAMPLE_SHELLS[0]}-{SAMPLE_SHELLS[-1]} of the 256^3 field "
+                      f"(full forward FFT, 6 shell + 6 counting fields, FP64), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import fieldgen
+    import oracle
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    edges = fieldgen.unit_edges(NSHELL)
+    delta = fieldgen.field("lognormal", N, SEED, np.float32).astype(np.float64)
+    allb = oracle.enumerate_bins(edges, ORDER)
+    shells = (63, 64)  # per step: the 4 bins among the two outermost shells (keeps K steps within minutes)
+    sel = allb[[i for i, b in enumerate(allb) if set(b.tolist()) <= set(shells)]]
+    for _ in range(args.warmup):
+        oracle.estimate(delta, L, edges, ORDER, bins=sel)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.estimate(delta, L, edges, ORDER, bins=sel)
+    dt = time.perf_counter() - t0
+    val = len(sel) * args.steps / dt
+    sample = f"{len(sel)} bins among shells 63-64 of the 256^3 field per step (full forward FFT, FP64)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "configs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "N_max": NSHELL, "order": ORDER, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "configs/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "configs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def time_precision(ps, torch, plan, d, args, flush_buf, dist_ok):
+    """Device-timed K steps (L2 flushed between steps); returns per-step ms and stage means."""
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.estimate(d)
+    ps.poly_plan_set_timing(plan.handle, True)
+    plan.estimate(d)
+    torch.cuda.synchronize()
+    launches0 = ps.poly_plan_stats(plan.handle)["launches"]
+    out = torch.empty(plan.nbins, dtype=torch.float64, device=d.device)
+    step_ms, stages = [], []
+    if dist_ok:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush_buf.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.estimate(d, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stages.append(ps.poly_plan_stats(plan.handle))
+    torch.cuda.synchronize()
+    if dist_ok:
+        torch.distributed.barrier()
+    launches = ps.poly_plan_stats(plan.handle)["launches"] - launches0
+    ps.poly_plan_set_timing(plan.handle, False)
+    mean = {k: statistics.fmean(s[k] for s in stages) for k in ("ms_forward", "ms_fields", "ms_contract", "ms_reduce")}
+    return step_ms, mean, launches
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import fieldgen
+    import paper_1904_11055_gb300 as ps
+    from paper_1904_11055_gb300 import build as psbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist_ok = world > 1
+    if dist_ok:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not dist_ok:
+        psbuild.build()
+    if dist_ok:
+        torch.distributed.barrier()
+    peaks, peak_src = load_peaks()
+
+    delta_np = fieldgen.field("lognormal", N, SEED + rank, np.float32)
+    d = torch.from_numpy(delta_np).cuda()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    edges = fieldgen.unit_edges(NSHELL)
+
+    precisions = [args.precision] if args.precision != "auto" else ["split_bf16", "fp32"]
+    results = {}
+    for prec in precisions:
+        try:
+            plan = ps.Plan(N, L, ORDER, edges, prec)
+        except ps.PolyError as e:
+            if e.status == 6:
+                results[prec] = {"unavailable": str(e)}
+                continue
+            raise
+        step_ms, stage, launches = None, None, None
+        with ClockSampler(local) as clk:
+            step_ms, stage, launches = time_precision(ps, torch, plan, d, args, flush_buf, dist_ok)
+        total_ms = sum(step_ms)
+        if dist_ok:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = plan.nbins * args.steps * world / (total_ms / 1e3)
+        # end to end through the host-buffer entry point (pinned input, H2D + D2H every step)
+        pinned = torch.from_numpy(delta_np).pin_memory().numpy()
+        out_h = np.empty(plan.nbins)
+        ps.poly_estimate_host(plan.handle, pinned, out_h, None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ps.poly_estimate_host(plan.handle, pinned, out_h, None)
+        e2e_s = time.perf_counter() - t0
+        if dist_ok:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        n3 = N ** 3
+        useful_flops = plan.nbins * n3 * ORDER
+        if prec == "split_bf16":
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            achieved = useful_flops / (stage["ms_contract"] * 1e-3) / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": traffic_for("contract_tc", ["contract_tc.cu"]), "kernel": "tc_contract",
+                    "peak_source": f"bf16 dense sustained, {peak_src}"}
+            try:
+                exe = ps_tc_executed_flops(ps, plan)
+                roof["executed_tflops"] = exe / (stage["ms_contract"] * 1e-3) / 1e12
+            except Exception:
+                pass
+        else:
+            mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+            achieved = useful_flops / (stage["ms_contract"] * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": traffic_for("contract_cc", ["contract_cc.cu"]), "kernel": "contract_cc_kernel",
+                    "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz ({peak_src} max clock)"}
+        field_bytes = NSHELL * n3 * 4 + n3 * 4
+        fields_roof = {"bound": "hbm", "achieved": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9,
+                       "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                       "traffic": traffic_for("inv_plane", ["fields.cu", "fft.cuh"]), "kernel": "inv_plane_kernel",
+                       "peak_source": peak_src}
+        results[prec] = {"value": value, "ms_per_step": total_ms / args.steps, "roofline": roof,
+                         "fields_roofline": fields_roof, "stage_ms": stage, "gpu_launches": launches,
+                         "clocks": clk.summary(),
+                         "e2e": {"value": plan.nbins * args.steps * world / e2e_s, "unit": "configs/s",
+                                 "h2d_bytes_per_step": n3 * 4, "d2h_bytes_per_step": plan.nbins * 8},
+                         "nbins": plan.nbins}
+        plan.close()
+    if rank != 0:
+        if dist_ok:
+            torch.distributed.destroy_process_group()
+        return
+    head_prec = next((p for p in precisions if "value" in results.get(p, {})), None)
+    if head_prec is None:
+        print(json.dumps({"metric": METRIC, "error": "no precision available", "results": results}), flush=True)
+        return
+    h = results[head_prec]
+    line = {
+        "metric": METRIC, "value": h["value"], "unit": "configs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3" if head_prec == "split_bf16" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "N_max": NSHELL, "order": ORDER, "nbins": h["nbins"], "L": L,
+                   "precision": head_prec, "l2": "256 MiB buffer written between timed steps (L2 flushed)",
+                   "parallelism": f"replica per GPU x{world}" if world > 1 else "1 GPU"},
+        "roofline": h["roofline"], "fields_roofline": h["fields_roofline"], "stage_ms": h["stage_ms"],
+        "e2e": h["e2e"], "gpu_launches": h["gpu_launches"], "clocks": h["clocks"],
+        "precisions": {p: ({k: r[k] for k in ("value", "ms_per_step", "roofline", "stage_ms", "e2e")}
+                           if "value" in r else r) for p, r in results.items()},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(delta_np)
+    print(json.dumps(line), flush=True)
+    if dist_ok:
+        torch.distributed.destroy_process_group()
+
+
+def ps_tc_executed_flops(ps, plan):
+    raise NotImplementedError
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "split_bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

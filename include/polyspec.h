@@ -1,0 +1,170 @@
+/*
+ * polyspec.h -- C ABI of the GB300 (sm_103a) polyspectrum library.
+ *
+ * The library computes the FFT-based (Scoccimarro-type) angle-averaged
+ * polyspectrum estimator of Tomlinson, Jeong & Kim, arXiv:1904.11055:
+ *
+ *   B_b = (V^{n-1} / N^{3n}) * S_b / (N^3 count_b),                      (App. A)
+ *   S_b = sum_x prod_{t=1..n} D_{k_t}(x),                                (Eq. estimator)
+ *   D_k(x) = sum_{q in shell k} dhat(q) e^{+2 pi i q.x / N},             (Eq. Bkfast; App. A)
+ *   count_b = N^{-3} sum_x prod_t iota_{k_t}(x),                         (Eqs. volume, Vn, Ncalc)
+ *   iota_k(x) = sum_{q in shell k} e^{+2 pi i q.x / N},
+ *
+ * for one real N^3 field delta(x) in a periodic box of side L (V = L^3),
+ * dhat(q) = sum_x delta(x) e^{-2 pi i q.x / N} (the unnormalised FFTW
+ * convention of App. A), integer wavevectors q in units of k_F = 2 pi / L,
+ * shell k = {q != 0 : edges[k-1]^2 <= |q|^2 < edges[k]^2} (the half-width
+ * binning |q - k_i| < dk/2 of Sec. 2 written with explicit edges), and bins
+ * b = (k_1 >= k_2 >= ... >= k_n) in the row-major order of Sec. 4.2 (k_n
+ * fastest) that satisfy the polygon inequality k_1 <= k_2 + ... + k_n on the
+ * shell centres (App. B, Eq. polygon).  count_b is the exact number of closed
+ * n-gons of grid modes (an integer, returned bit-exact).
+ *
+ * Conventions of every entry point:
+ *  - Arrays are plain pointers.  "device" means memory of the plan's CUDA
+ *    device; "host" means ordinary (pageable or pinned) host memory.
+ *  - Real grids are C order [x][y][z], z fastest, N^3 elements.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    calls are stream-ordered and asynchronous unless stated otherwise.
+ *  - The caller owns every buffer it passes; the plan owns its workspace and
+ *    its cached counts.  Output buffers must not alias inputs.
+ *  - Argument errors return synchronously and leave outputs untouched.
+ *    Errors raised on the device surface as POLY_ERR_CUDA / POLY_ERR_TIMEOUT
+ *    from poly_plan_sync() or the next call on the plan.
+ *  - No exception or longjmp crosses this boundary.  A plan is not
+ *    thread-safe: serialise calls on one plan.
+ */
+#ifndef POLYSPEC_H
+#define POLYSPEC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct poly_plan_s* poly_plan;
+
+typedef enum {
+    POLY_OK = 0,
+    POLY_ERR_ARG = 1,         /* bad argument (NULL, sizes, unsorted edges, bad order, ...) */
+    POLY_ERR_ALIAS = 2,       /* n * K >= N: closures wrap around the periodic grid (Sec. 4.3) */
+    POLY_ERR_ALLOC = 3,       /* device or host allocation failed */
+    POLY_ERR_CUDA = 4,        /* a CUDA runtime call or kernel failed */
+    POLY_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (see poly_plan_sync) */
+    POLY_ERR_UNSUPPORTED = 6, /* valid request outside what this build implements */
+    POLY_ERR_COUNT = 7        /* a polygon count came out non-integral (numerical failure) */
+} poly_status;
+
+typedef enum {
+    POLY_FP32 = 0,       /* FP32 input and fields; FP32 CUDA-core products, FP64 reduction */
+    POLY_SPLIT_BF16 = 1, /* FP32 input and fields; split-BF16 (hi+lo, 3 products) tcgen05 contraction */
+    POLY_TF32X3 = 2,     /* reserved; returns POLY_ERR_UNSUPPORTED */
+    POLY_FP64 = 3        /* FP64 input, fields and contraction (the plain method) */
+} poly_precision;
+
+/* plan flags */
+#define POLY_BINS_ALL_SORTED 0x1u /* every sorted tuple instead of the polygon-inequality set */
+#define POLY_ALLOW_ALIAS 0x2u     /* accept n*K >= N; the periodic (mod N) estimator is returned */
+
+/*
+ * Create a plan for grid size N (one of 16, 24, 32, 48, 64, 96, 128, 160, 256),
+ * box side L > 0, order n in [2, 4], `nshell` shells with `nshell + 1`
+ * strictly increasing edges (host array, units of k_F, edges[0] >= 0).
+ * K = the largest integer with K^2 < edges[nshell]^2 must satisfy 2K+1 <= N,
+ * and n*K < N unless POLY_ALLOW_ALIAS.  Plan creation enumerates the bins,
+ * builds the shell tables and tiles, allocates the workspace (nshell * N^3
+ * fields of the plan's precision plus small buffers) on the current CUDA
+ * device and computes the exact counts (FP64 counting fields on the
+ * 1/48 symmetry wedge, cached per (N, edges, n, flags) in the process).
+ * It synchronises the device.  On failure *out is set to NULL.
+ */
+poly_status poly_plan_create(poly_plan* out, int N, double L, int order, int nshell, const double* edges,
+                             poly_precision prec, unsigned flags);
+
+/* Number of bins the plan outputs. */
+poly_status poly_plan_nbins(poly_plan plan, int64_t* nbins);
+
+/* Bins as 1-based shell numbers, host array of nbins * order int32, paper order. */
+poly_status poly_plan_bins(poly_plan plan, int32_t* idx);
+
+/* Exact polygon counts count_b, host array of nbins int64 (Eq. Ncalc). */
+poly_status poly_plan_counts(poly_plan plan, int64_t* counts);
+
+/*
+ * Estimate B_b for one field.  delta_x: device, N^3 real (float for POLY_FP32 /
+ * POLY_SPLIT_BF16, double for POLY_FP64).  out: device, nbins double, B_b.
+ * scale_or_null: device, nbins double or NULL; if given, receives
+ * sum_x |prod_t D_{k_t}(x)| / (N^3 count_b) (the scale of the stated error
+ * bound), at the cost of a second contraction.  Asynchronous on `stream`.
+ */
+poly_status poly_estimate(poly_plan plan, const void* delta_x, double* out, double* scale_or_null, void* stream);
+
+/*
+ * The same as poly_estimate with HOST buffers: copies delta_x (host, N^3 real)
+ * to the device, estimates, copies B_b to out (host, nbins double) and
+ * synchronises `stream` before returning.
+ */
+poly_status poly_estimate_host(poly_plan plan, const void* delta_x_host, double* out_host, void* stream);
+
+/*
+ * Gradient of L = sum_b dL_dB[b] * B_b with respect to delta(x).
+ * dL_dB: device, nbins double.  dL_ddelta: device, N^3 real of the plan's
+ * input type, overwritten.  Recomputes the shell fields from delta_x (it
+ * never stores pair products), contracts dL/dB with products of the other
+ * fields, transforms each result forward, keeps its own shell and applies one
+ * inverse transform (the adjoint of the estimator).  Asynchronous on `stream`.
+ */
+poly_status poly_backward(poly_plan plan, const void* delta_x, const double* dL_dB, void* dL_ddelta, void* stream);
+
+/*
+ * Estimate `count` fields, possibly of different plans (e.g. different grid
+ * sizes), in one stream-ordered batch: fields[i] is a device pointer for
+ * plans[i] and outs[i] a device array of plans[i]'s nbins doubles.  Results
+ * are bit-identical to calling poly_estimate on each field.
+ */
+poly_status poly_estimate_batched(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
+                                  void* stream);
+
+/* Wait for the plan's work on `stream` and report device-side errors. */
+poly_status poly_plan_sync(poly_plan plan, void* stream);
+
+/* Release the plan and its workspace (NULL is ignored). */
+void poly_plan_destroy(poly_plan plan);
+
+/* Per-plan instrumentation: launch counter and CUDA events per stage. */
+typedef struct {
+    int64_t launches;   /* kernels this plan has launched since creation (excluding plan-time work) */
+    float ms_forward;   /* last timed estimate: forward R2C transform */
+    float ms_fields;    /* last timed estimate: shell gather + inverse transforms (all shells) */
+    float ms_contract;  /* last timed estimate: the product-sum contraction kernel */
+    float ms_reduce;    /* last timed estimate: cross-tile reduction + normalisation */
+} poly_stats;
+
+/*
+ * enable != 0: every following estimate records CUDA events between its
+ * stages on its stream (a few microseconds of overhead); 0 disables.
+ */
+poly_status poly_plan_set_timing(poly_plan plan, int enable);
+
+/* Launch count and stage durations of the last timed estimate (waits for its events). */
+poly_status poly_plan_stats(poly_plan plan, poly_stats* out);
+
+/* Static description of a status code. */
+const char* poly_status_string(poly_status status);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* poly_last_error(void);
+
+/*
+ * Test hook: make the n-th following workspace allocation of poly_plan_create
+ * fail (n >= 1; 0 disables).  Exercises the allocation-failure path on the
+ * host without touching the device.
+ */
+void poly_debug_fail_alloc_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYSPEC_H */

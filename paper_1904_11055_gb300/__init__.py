@@ -1,0 +1,269 @@
+"""Thin Python binding of libpolyspec.so (the C ABI in include/polyspec.h).
+
+The functions below carry the ABI's names and only marshal arguments; every step
+of the estimator runs in the CUDA library.  There is no CPU fallback: importing
+works without a GPU, but any call that needs the library raises if it was not
+built (``paper_1904_11055_gb300.build.build()``) or if CUDA is unavailable.
+
+``Plan`` wraps a plan handle for torch tensors (device memory and streams only),
+and ``PolyspectrumFunction`` is the torch.autograd.Function whose backward is the
+library's hand-written adjoint (``poly_backward``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpolyspec.so")
+
+POLY_OK = 0
+STATUS = {0: "POLY_OK", 1: "POLY_ERR_ARG", 2: "POLY_ERR_ALIAS", 3: "POLY_ERR_ALLOC", 4: "POLY_ERR_CUDA",
+          5: "POLY_ERR_TIMEOUT", 6: "POLY_ERR_UNSUPPORTED", 7: "POLY_ERR_COUNT"}
+POLY_FP32, POLY_SPLIT_BF16, POLY_TF32X3, POLY_FP64 = 0, 1, 2, 3
+PRECISIONS = {"fp32": POLY_FP32, "split_bf16": POLY_SPLIT_BF16, "tf32x3": POLY_TF32X3, "fp64": POLY_FP64}
+POLY_BINS_ALL_SORTED = 0x1
+POLY_ALLOW_ALIAS = 0x2
+
+# every symbol include/polyspec.h declares
+ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_plan_counts", "poly_estimate",
+               "poly_estimate_host", "poly_backward", "poly_estimate_batched", "poly_plan_sync", "poly_plan_destroy",
+               "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
+               "poly_plan_stats")
+
+
+class poly_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms_forward", ctypes.c_float), ("ms_fields", ctypes.c_float),
+                ("ms_contract", ctypes.c_float), ("ms_reduce", ctypes.c_float)]
+
+_lib = None
+
+
+class PolyError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({msg})" if msg else ""))
+
+
+def load_library():
+    """Load libpolyspec.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1904_11055_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, f64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint
+    L.poly_plan_create.argtypes = [ctypes.POINTER(P), i32, f64, i32, i32, P, i32, u32]
+    L.poly_plan_nbins.argtypes = [P, ctypes.POINTER(i64)]
+    L.poly_plan_bins.argtypes = [P, P]
+    L.poly_plan_counts.argtypes = [P, P]
+    L.poly_estimate.argtypes = [P, P, P, P, P]
+    L.poly_estimate_host.argtypes = [P, P, P, P]
+    L.poly_backward.argtypes = [P, P, P, P, P]
+    L.poly_estimate_batched.argtypes = [P, P, P, i32, P]
+    L.poly_plan_sync.argtypes = [P, P]
+    L.poly_plan_destroy.argtypes = [P]
+    L.poly_plan_destroy.restype = None
+    L.poly_status_string.argtypes = [i32]
+    L.poly_status_string.restype = ctypes.c_char_p
+    L.poly_last_error.restype = ctypes.c_char_p
+    L.poly_plan_set_timing.argtypes = [P, i32]
+    L.poly_plan_stats.argtypes = [P, ctypes.POINTER(poly_stats)]
+    L.poly_debug_fail_alloc_after.argtypes = [i32]
+    L.poly_debug_fail_alloc_after.restype = None
+    for name in ABI_SYMBOLS:
+        if name not in ("poly_plan_destroy", "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after"):
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != POLY_OK:
+        raise PolyError(status, where, load_library().poly_last_error().decode())
+
+
+# ---------------------------------------------------------------- ABI-named calls
+def poly_plan_create(N: int, L: float, order: int, edges, prec: int = POLY_FP32, flags: int = 0) -> int:
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load_library().poly_plan_create(ctypes.byref(h), int(N), float(L), int(order), e.size - 1,
+                                           e.ctypes.data_as(ctypes.c_void_p), int(prec), int(flags)),
+           "poly_plan_create")
+    return h.value
+
+
+def poly_plan_nbins(plan: int) -> int:
+    n = ctypes.c_int64()
+    _check(load_library().poly_plan_nbins(plan, ctypes.byref(n)), "poly_plan_nbins")
+    return n.value
+
+
+def poly_plan_bins(plan: int, order: int) -> np.ndarray:
+    out = np.empty((poly_plan_nbins(plan), order), dtype=np.int32)
+    _check(load_library().poly_plan_bins(plan, out.ctypes.data_as(ctypes.c_void_p)), "poly_plan_bins")
+    return out
+
+
+def poly_plan_counts(plan: int) -> np.ndarray:
+    out = np.empty(poly_plan_nbins(plan), dtype=np.int64)
+    _check(load_library().poly_plan_counts(plan, out.ctypes.data_as(ctypes.c_void_p)), "poly_plan_counts")
+    return out
+
+
+def poly_estimate(plan: int, delta_ptr: int, out_ptr: int, scale_ptr: int | None, stream: int | None) -> None:
+    _check(load_library().poly_estimate(plan, delta_ptr, out_ptr, scale_ptr, stream), "poly_estimate")
+
+
+def poly_estimate_host(plan: int, delta_host: np.ndarray, out_host: np.ndarray, stream: int | None = None) -> None:
+    _check(load_library().poly_estimate_host(plan, delta_host.ctypes.data_as(ctypes.c_void_p),
+                                             out_host.ctypes.data_as(ctypes.c_void_p), stream),
+           "poly_estimate_host")
+
+
+def poly_backward(plan: int, delta_ptr: int, dLdB_ptr: int, grad_ptr: int, stream: int | None) -> None:
+    _check(load_library().poly_backward(plan, delta_ptr, dLdB_ptr, grad_ptr, stream), "poly_backward")
+
+
+def poly_estimate_batched(plans, field_ptrs, out_ptrs, stream: int | None) -> None:
+    n = len(plans)
+    P = ctypes.c_void_p * n
+    _check(load_library().poly_estimate_batched(P(*plans), P(*field_ptrs), P(*out_ptrs), n, stream),
+           "poly_estimate_batched")
+
+
+def poly_plan_sync(plan: int, stream: int | None = None) -> None:
+    _check(load_library().poly_plan_sync(plan, stream), "poly_plan_sync")
+
+
+def poly_plan_destroy(plan: int) -> None:
+    load_library().poly_plan_destroy(plan)
+
+
+def poly_plan_set_timing(plan: int, enable: bool) -> None:
+    _check(load_library().poly_plan_set_timing(plan, int(bool(enable))), "poly_plan_set_timing")
+
+
+def poly_plan_stats(plan: int) -> dict:
+    st = poly_stats()
+    _check(load_library().poly_plan_stats(plan, ctypes.byref(st)), "poly_plan_stats")
+    return {k: getattr(st, k) for k, _ in poly_stats._fields_}
+
+
+def poly_status_string(status: int) -> str:
+    return load_library().poly_status_string(int(status)).decode()
+
+
+def poly_debug_fail_alloc_after(n: int) -> None:
+    load_library().poly_debug_fail_alloc_after(int(n))
+
+
+# ---------------------------------------------------------------- torch-facing wrapper
+def _stream_handle(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+class Plan:
+    """A plan for one (N, L, n, edges, precision); owns the library handle."""
+
+    def __init__(self, N: int, L: float, order: int, edges, precision: str | int = "fp32", flags: int = 0):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.N, self.L, self.order, self.prec, self.flags = int(N), float(L), int(order), prec, int(flags)
+        self.edges = np.ascontiguousarray(edges, dtype=np.float64)
+        self.handle = poly_plan_create(N, L, order, self.edges, prec, flags)
+        self.nbins = poly_plan_nbins(self.handle)
+        self.bins = poly_plan_bins(self.handle, order)
+        self.counts = poly_plan_counts(self.handle)
+
+    @property
+    def real_dtype(self):
+        import torch
+
+        return torch.float64 if self.prec == POLY_FP64 else torch.float32
+
+    def estimate(self, delta, out=None, scale: bool = False, stream=None):
+        """delta: CUDA tensor [N,N,N] of the plan's real dtype.  Returns B (float64) [and scale]."""
+        import torch
+
+        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
+        assert delta.numel() == self.N ** 3
+        out = torch.empty(self.nbins, dtype=torch.float64, device=delta.device) if out is None else out
+        sc = torch.empty(self.nbins, dtype=torch.float64, device=delta.device) if scale else None
+        poly_estimate(self.handle, delta.data_ptr(), out.data_ptr(), sc.data_ptr() if scale else None,
+                      _stream_handle(stream))
+        return (out, sc) if scale else out
+
+    def estimate_host(self, delta: np.ndarray) -> np.ndarray:
+        d = np.ascontiguousarray(delta, dtype=np.float64 if self.prec == POLY_FP64 else np.float32)
+        assert d.size == self.N ** 3
+        out = np.empty(self.nbins, dtype=np.float64)
+        poly_estimate_host(self.handle, d, out, None)
+        return out
+
+    def backward(self, delta, dLdB, grad=None, stream=None):
+        import torch
+
+        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
+        g = dLdB.to(device=delta.device, dtype=torch.float64).contiguous()
+        grad = torch.empty_like(delta) if grad is None else grad
+        poly_backward(self.handle, delta.data_ptr(), g.data_ptr(), grad.data_ptr(), _stream_handle(stream))
+        return grad
+
+    def sync(self, stream=None):
+        poly_plan_sync(self.handle, _stream_handle(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            poly_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_batched(plans, fields, outs=None, stream=None):
+    """Estimate many fields (of possibly different plans) in one call; returns the output tensors."""
+    import torch
+
+    if outs is None:
+        outs = [torch.empty(p.nbins, dtype=torch.float64, device=f.device) for p, f in zip(plans, fields)]
+    poly_estimate_batched([p.handle for p in plans], [f.data_ptr() for f in fields], [o.data_ptr() for o in outs],
+                          _stream_handle(stream))
+    return outs
+
+
+def _make_function():
+    import torch
+
+    class PolyspectrumFunction(torch.autograd.Function):
+        """B = estimate(delta); backward returns the library's adjoint dL/d delta."""
+
+        @staticmethod
+        def forward(ctx, delta, plan):
+            ctx.plan = plan
+            ctx.save_for_backward(delta)
+            return plan.estimate(delta.contiguous())
+
+        @staticmethod
+        def backward(ctx, gB):
+            (delta,) = ctx.saved_tensors
+            return ctx.plan.backward(delta.contiguous(), gB), None
+
+    return PolyspectrumFunction
+
+
+def polyspectrum(delta, plan: Plan):
+    """Differentiable estimate: torch.autograd sees dL/d delta from poly_backward."""
+    global PolyspectrumFunction
+    if "PolyspectrumFunction" not in globals():
+        PolyspectrumFunction = _make_function()
+    return PolyspectrumFunction.apply(delta, plan)

@@ -1,0 +1,46 @@
+// Internal launch interface between the plan code and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+// ---- fields.cu --------------------------------------------------------------
+int ps_supported_n(int n);
+int ps_plane_needs_spill(int n, int K, int is_double);
+size_t ps_spill_elems(int n, int K, int nblocks, int is_double);
+// delta [N^3] real -> W [N][(2K+1)(K+1)] -> fhat [(2K+1)(K+1)][2K+1] (complex, same precision)
+cudaError_t ps_forward(int n, int is_double, const void* delta, int K, const void* tw_fwd, void* W, void* fhat,
+                       void* spill, cudaStream_t st);
+// shells s0..s0+ns-1, planes x0..x0+nx-1 -> out[(s-s0)*out_stride + (x-x0)*N*N + y*N + z]
+cudaError_t ps_inverse(int n, int is_double, int unity, const void* fhat, const void* lines, const int* line_off,
+                       int s0, int ns, int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride,
+                       void* spill, cudaStream_t st);
+
+// ---- contract_cc.cu -----------------------------------------------------------
+// One GEMM tile of the CUDA-core contraction: up to 64 rows x 64 cols, each row
+// (col) the product of one or two of the tile's local fields.
+struct PsTile {
+    int row_off, nrow, col_off, ncol, field_off, nfield;
+    unsigned region_mask;  // bit w: warp w's 32x16 region holds at least one needed entry
+    int pad_;
+};
+constexpr int kCcTM = 64, kCcTN = 64, kCcMaxFields = 128;
+// cells per chunk of the CUDA-core contraction
+inline int ps_cc_chunk(int is_double) { return is_double ? 16 : 32; }
+
+// partial[(split * ntiles + tile) * 64 * 64 + r * 64 + c] = sum over the split's cells
+cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
+                           int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
+                           const short2* rowf, const short2* colf, int nsplit, int64_t chunks_per_split,
+                           double* partial, cudaStream_t st);
+// S[b] = sum_split partial[split * slot_stride + slot[b]]
+cudaError_t ps_reduce_slots(const double* partial, int nsplit, int64_t slot_stride, const int64_t* slot,
+                            int64_t nbins, double* S, cudaStream_t st);
+// out[b] = norm * S[b] / (N^3 count[b])  (0 where count == 0)
+cudaError_t ps_normalise(const double* S, const int64_t* counts, int64_t nbins, double norm, double n3, double* out,
+                         cudaStream_t st);
+
+// ---- misc.cu -------------------------------------------------------------------
+// out[s * out_stride + w] = in[s * in_stride + idx[w]] for s < ns, w < nw
+cudaError_t ps_gather_cells(int is_double, const void* in, size_t in_stride, int ns, const int32_t* idx, int64_t nw,
+                            void* out, size_t out_stride, cudaStream_t st);

@@ -1,0 +1,713 @@
+// Host side of the polyspectrum library: plan construction (shell tables, bin
+// enumeration, contraction tiles, exact counts) and the C ABI of polyspec.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/polyspec.h"
+#include "kernels.h"
+#include "plan_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+int g_fail_alloc_after = 0;
+
+poly_status set_error(poly_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+poly_status cuda_error(cudaError_t e, const char* where) {
+    return set_error(POLY_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PS_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_error(e_, #call);   \
+    } while (0)
+
+#define PS_TRY(call)                          \
+    do {                                      \
+        poly_status s_ = (call);              \
+        if (s_ != POLY_OK) return s_;         \
+    } while (0)
+
+// ---- counts cache (per process) -----------------------------------------
+struct CountKey {
+    int N, order;
+    unsigned rule;
+    std::vector<double> edges;
+    bool operator<(const CountKey& o) const {
+        return std::tie(N, order, rule, edges) < std::tie(o.N, o.order, o.rule, o.edges);
+    }
+};
+std::mutex g_count_mu;
+std::map<CountKey, std::vector<int64_t>> g_count_cache;
+
+bool member(const double* edges, int s, long long q2) {
+    if (q2 == 0) return false;
+    const double d = (double)q2;
+    return edges[s] * edges[s] <= d && d < edges[s + 1] * edges[s + 1];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// allocation helper with the failure-injection hook
+// ---------------------------------------------------------------------------
+poly_status ps_alloc(PsPlan* p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (g_fail_alloc_after > 0 && --g_fail_alloc_after == 0)
+        return set_error(POLY_ERR_ALLOC, "injected allocation failure");
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return set_error(POLY_ERR_ALLOC, std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                                             cudaGetErrorString(e));
+    }
+    p->allocations.push_back(*ptr);
+    return POLY_OK;
+}
+
+template <typename V>
+static poly_status upload(PsPlan* p, void** dptr, const std::vector<V>& h) {
+    PS_TRY(ps_alloc(p, dptr, h.size() * sizeof(V)));
+    if (!h.empty()) PS_CUDA(cudaMemcpy(*dptr, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return POLY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// bins: k_1 >= ... >= k_n (1-based), row-major with k_n fastest, polygon rule
+// ---------------------------------------------------------------------------
+static void enumerate_bins(int nshell, const std::vector<double>& edges, int order, bool all_sorted,
+                           std::vector<int32_t>& out) {
+    std::vector<double> c(nshell);
+    for (int s = 0; s < nshell; s++) c[s] = 0.5 * (edges[s] + edges[s + 1]);
+    std::vector<int> k(order, 1);
+    // iterate in lexicographic order of (k_1, ..., k_n) with k_1 >= k_2 >= ...
+    std::vector<int> cur(order);
+    std::function<void(int)> rec = [&](int d) {
+        if (d == order) {
+            double rest = 0;
+            for (int t = 1; t < order; t++) rest += c[cur[t] - 1];
+            if (all_sorted || c[cur[0] - 1] <= rest + 1e-9 * c[cur[0] - 1])
+                for (int t = 0; t < order; t++) out.push_back(cur[t]);
+            return;
+        }
+        const int hi = d == 0 ? nshell : cur[d - 1];
+        for (int v = 1; v <= hi; v++) {
+            cur[d] = v;
+            rec(d + 1);
+        }
+    };
+    rec(0);
+}
+
+// ---------------------------------------------------------------------------
+// shell line tables: per shell, the (ky, kz >= 0) lines crossing it and the
+// |kx| run [a, b] on each line (membership is monotone in |kx|)
+// ---------------------------------------------------------------------------
+static void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines) {
+    const int K = p->K;
+    for (int ky = -K; ky <= K; ky++)
+        for (int kz = 0; kz <= K; kz++) {
+            const long long rho2 = (long long)ky * ky + (long long)kz * kz;
+            int a = -1, b = -1;
+            for (int kx = 0; kx <= K; kx++)
+                if (member(e, s, rho2 + (long long)kx * kx)) {
+                    if (a < 0) a = kx;
+                    b = kx;
+                }
+            if (a >= 0) {
+                lines.push_back((short)ky);
+                lines.push_back((short)kz);
+                lines.push_back((short)a);
+                lines.push_back((short)b);
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core contraction tiles: rows = products of the first ra shells of a
+// bin, cols = products of the rest; rows grouped 64 at a time after sorting by
+// their column span, each group's column union cut into chunks of 64.
+// ---------------------------------------------------------------------------
+static void build_cc_tiles(PsPlan* p, CcTiles& t) {
+    const int n = p->order;
+    const int ra = n >= 3 ? 2 : 1, ca = n - ra;
+    auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra == 2 ? b[1] : -1); };
+    auto ckey = [&](const int32_t* b) { return std::make_pair(b[ra], ca == 2 ? b[ra + 1] : -1); };
+    std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> rows;  // row -> sorted col keys
+    for (int64_t i = 0; i < p->nbins; i++) rows[rkey(&p->bins[i * n])].push_back(ckey(&p->bins[i * n]));
+    struct RowInfo {
+        std::pair<int, int> key;
+        std::vector<std::pair<int, int>> cols;
+    };
+    std::vector<RowInfo> ri;
+    for (auto& kv : rows) {
+        auto cols = kv.second;
+        std::sort(cols.begin(), cols.end());
+        cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+        ri.push_back({kv.first, cols});
+    }
+    std::stable_sort(ri.begin(), ri.end(), [](const RowInfo& a, const RowInfo& b) {
+        return std::make_pair(a.cols.front(), a.cols.back()) < std::make_pair(b.cols.front(), b.cols.back());
+    });
+    std::map<std::tuple<int, int, int, int>, int64_t> slot_of;  // (row key, col key) -> slot
+    for (size_t g = 0; g < ri.size(); g += kCcTM) {
+        const size_t g1 = std::min(ri.size(), g + kCcTM);
+        std::vector<std::pair<int, int>> cu;
+        for (size_t r = g; r < g1; r++) cu.insert(cu.end(), ri[r].cols.begin(), ri[r].cols.end());
+        std::sort(cu.begin(), cu.end());
+        cu.erase(std::unique(cu.begin(), cu.end()), cu.end());
+        for (size_t c0 = 0; c0 < cu.size(); c0 += kCcTN) {
+            const size_t c1 = std::min(cu.size(), c0 + kCcTN);
+            PsTile tile{};
+            tile.row_off = (int)t.rowf.size();
+            tile.nrow = (int)(g1 - g);
+            tile.col_off = (int)t.colf.size();
+            tile.ncol = (int)(c1 - c0);
+            tile.field_off = (int)t.field_ids.size();
+            std::map<int, int> local;  // shell (0-based) -> local field index
+            auto loc = [&](int shell1) -> short {
+                if (shell1 < 0) return -1;
+                auto it = local.find(shell1 - 1);
+                if (it != local.end()) return (short)it->second;
+                int id = (int)local.size();
+                local[shell1 - 1] = id;
+                t.field_ids.push_back(shell1 - 1);
+                return (short)id;
+            };
+            for (size_t r = g; r < g1; r++) {
+                short2 f;
+                f.x = loc(ri[r].key.first);
+                f.y = loc(ri[r].key.second);
+                t.rowf.push_back(f);
+            }
+            std::map<std::pair<int, int>, int> cidx;
+            for (size_t c = c0; c < c1; c++) {
+                short2 f;
+                f.x = loc(cu[c].first);
+                f.y = loc(cu[c].second);
+                t.colf.push_back(f);
+                cidx[cu[c]] = (int)(c - c0);
+            }
+            tile.nfield = (int)local.size();
+            const int tid = (int)t.tiles.size();
+            for (size_t r = g; r < g1; r++)
+                for (auto& ck : ri[r].cols) {
+                    auto it = cidx.find(ck);
+                    if (it == cidx.end()) continue;
+                    const int rr = (int)(r - g), cc = it->second;
+                    tile.region_mask |= 1u << ((rr / 32) * 4 + cc / 16);
+                    slot_of[{ri[r].key.first, ri[r].key.second, ck.first, ck.second}] =
+                        (int64_t)tid * (kCcTM * kCcTN) + rr * kCcTN + cc;
+                }
+            t.tiles.push_back(tile);
+        }
+    }
+    t.slot.resize(p->nbins);
+    for (int64_t i = 0; i < p->nbins; i++) {
+        auto rk = rkey(&p->bins[i * n]);
+        auto ck = ckey(&p->bins[i * n]);
+        t.slot[i] = slot_of.at({rk.first, rk.second, ck.first, ck.second});
+    }
+}
+
+static int choose_splits(int ntiles, int64_t nchunks, int sms) {
+    int want = std::max(1, (4 * sms + ntiles - 1) / ntiles);
+    int64_t maxs = std::max<int64_t>(1, nchunks / 16);
+    return (int)std::min<int64_t>(want, maxs);
+}
+
+// ---------------------------------------------------------------------------
+// exact counts: FP64 counting fields on the symmetry wedge
+//   0 <= x <= y <= z <= floor(N/2), weight = orbit size under coordinate
+//   permutations and sign flips (x_c -> N - x_c); sum_wedge w prod iota = sum_x prod iota.
+// ---------------------------------------------------------------------------
+static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
+    CountKey key{p->N, p->order, p->flags & POLY_BINS_ALL_SORTED, p->edges};
+    {
+        std::lock_guard<std::mutex> lk(g_count_mu);
+        auto it = g_count_cache.find(key);
+        if (it != g_count_cache.end()) {
+            p->counts = it->second;
+            return POLY_OK;
+        }
+    }
+    const int N = p->N, h = N / 2;
+    std::vector<int32_t> widx;
+    std::vector<double> wgt;
+    for (int x = 0; x <= h; x++)
+        for (int y = x; y <= h; y++)
+            for (int z = y; z <= h; z++) {
+                int perms = (x == y && y == z) ? 1 : (x == y || y == z) ? 3 : 6;
+                double w = perms;
+                for (int v : {x, y, z}) w *= (v == 0 || 2 * v == N) ? 1.0 : 2.0;
+                widx.push_back((int32_t)(((int64_t)x * N + y) * N + z));
+                wgt.push_back(w);
+            }
+    const int64_t nw = (int64_t)widx.size();
+    // device buffers (freed at the end of this function)
+    std::vector<void*> tmp;
+    auto talloc = [&](void** ptr, size_t bytes) -> poly_status {
+        cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(POLY_ERR_ALLOC, "counts workspace allocation failed");
+        }
+        tmp.push_back(*ptr);
+        return POLY_OK;
+    };
+    auto cleanup = [&]() {
+        for (void* q : tmp) cudaFree(q);
+    };
+    poly_status rc = POLY_OK;
+    void *d_widx = nullptr, *d_wgt = nullptr, *d_iota = nullptr, *d_planes = nullptr, *d_spill = nullptr,
+         *d_part = nullptr, *d_S = nullptr;
+    const int sb = std::min(8, p->nshell);  // shells per inverse batch
+    const size_t plane_elems = (size_t)(h + 1) * N * N;
+    const bool spill = ps_plane_needs_spill(N, p->K, 1) == 1;
+    const CcTiles& t = p->cc;
+    const int64_t nchunks = (nw + ps_cc_chunk(1) - 1) / ps_cc_chunk(1);
+    const int nsplit = choose_splits((int)t.tiles.size(), nchunks, p->sms);
+    const int64_t cps = (nchunks + nsplit - 1) / nsplit;
+    const int64_t slot_stride = (int64_t)t.tiles.size() * kCcTM * kCcTN;
+    do {
+        if ((rc = talloc(&d_widx, widx.size() * 4))) break;
+        if ((rc = talloc(&d_wgt, wgt.size() * 8))) break;
+        if ((rc = talloc(&d_iota, (size_t)p->nshell * nw * 8))) break;
+        if ((rc = talloc(&d_planes, (size_t)sb * plane_elems * 8))) break;
+        if (spill && (rc = talloc(&d_spill, ps_spill_elems(N, p->K, (h + 1) * sb, 1) * 16))) break;
+        if ((rc = talloc(&d_part, (size_t)nsplit * slot_stride * 8))) break;
+        if ((rc = talloc(&d_S, (size_t)std::max<int64_t>(1, p->nbins) * 8))) break;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(d_widx, widx.data(), widx.size() * 4, cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(d_wgt, wgt.data(), wgt.size() * 8, cudaMemcpyHostToDevice, st))) {
+            rc = cuda_error(e, "counts upload");
+            break;
+        }
+        for (int s0 = 0; s0 < p->nshell && !rc; s0 += sb) {
+            const int ns = std::min(sb, p->nshell - s0);
+            if ((e = ps_inverse(N, 1, 1, nullptr, p->d_lines, p->d_line_off, s0, ns, p->K, 0, h + 1, p->d_tw_inv,
+                                d_planes, plane_elems, d_spill, st))) {
+                rc = cuda_error(e, "counting fields");
+                break;
+            }
+            if ((e = ps_gather_cells(1, d_planes, plane_elems, ns, (const int32_t*)d_widx, nw,
+                                     (double*)d_iota + (size_t)s0 * nw, nw, st))) {
+                rc = cuda_error(e, "wedge gather");
+                break;
+            }
+        }
+        if (rc) break;
+        if ((e = ps_contract_cc(1, 1, 0, d_iota, (size_t)nw, nw, d_wgt, (const PsTile*)p->d_cc_tiles,
+                                (int)t.tiles.size(), (const int*)p->d_cc_field_ids, (const short2*)p->d_cc_rowf,
+                                (const short2*)p->d_cc_colf, nsplit, cps, (double*)d_part, st)) ||
+            (e = ps_reduce_slots((double*)d_part, nsplit, slot_stride, (const int64_t*)p->d_cc_slot, p->nbins,
+                                 (double*)d_S, st))) {
+            rc = cuda_error(e, "count contraction");
+            break;
+        }
+        std::vector<double> S(p->nbins);
+        if ((e = cudaMemcpyAsync(S.data(), d_S, p->nbins * 8, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            rc = cuda_error(e, "count readback");
+            break;
+        }
+        const double n3 = (double)N * N * N;
+        p->counts.resize(p->nbins);
+        for (int64_t b = 0; b < p->nbins; b++) {
+            const double v = S[b] / n3, r = std::nearbyint(v);
+            if (std::fabs(v - r) > 1e-3 || r < 0) {
+                char msg[160];
+                snprintf(msg, sizeof msg, "polygon count of bin %lld is not an integer: %.6f", (long long)b, v);
+                rc = set_error(POLY_ERR_COUNT, msg);
+                break;
+            }
+            p->counts[b] = (int64_t)r;
+        }
+    } while (0);
+    cleanup();
+    if (rc == POLY_OK) {
+        std::lock_guard<std::mutex> lk(g_count_mu);
+        g_count_cache[key] = p->counts;
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// plan lifetime
+// ---------------------------------------------------------------------------
+static void free_plan(PsPlan* p) {
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (p->device >= 0 && cur != p->device) cudaSetDevice(p->device);
+    for (void* q : p->allocations) cudaFree(q);
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+    ps_tc_free(p);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
+                               poly_precision prec, unsigned flags) {
+    if (!edges || nshell < 1 || nshell > 128) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
+    if (order < 2 || order > 4) return set_error(POLY_ERR_UNSUPPORTED, "order must be 2, 3 or 4");
+    if (!(L > 0) || !std::isfinite(L)) return set_error(POLY_ERR_ARG, "L must be positive");
+    if (flags & ~(POLY_BINS_ALL_SORTED | POLY_ALLOW_ALIAS)) return set_error(POLY_ERR_ARG, "unknown flag");
+    if (!ps_supported_n(N)) return set_error(POLY_ERR_UNSUPPORTED, "grid size N not in the supported set");
+    if (prec == POLY_TF32X3) return set_error(POLY_ERR_UNSUPPORTED, "POLY_TF32X3 is not implemented");
+    if (prec != POLY_FP32 && prec != POLY_SPLIT_BF16 && prec != POLY_FP64)
+        return set_error(POLY_ERR_ARG, "unknown precision");
+    for (int s = 0; s <= nshell; s++)
+        if (!std::isfinite(edges[s])) return set_error(POLY_ERR_ARG, "edges must be finite");
+    if (edges[0] < 0) return set_error(POLY_ERR_ARG, "edges must be non-negative");
+    for (int s = 0; s < nshell; s++)
+        if (!(edges[s + 1] > edges[s])) return set_error(POLY_ERR_ARG, "edges must increase strictly");
+    p->N = N;
+    p->L = L;
+    p->order = order;
+    p->nshell = nshell;
+    p->edges.assign(edges, edges + nshell + 1);
+    p->prec = prec;
+    p->flags = flags;
+    p->is_double = prec == POLY_FP64;
+    const double emax2 = edges[nshell] * edges[nshell];
+    int K = 0;
+    while ((double)((long long)(K + 1) * (K + 1)) < emax2) K++;
+    p->K = K;
+    if (2 * K + 1 > N) return set_error(POLY_ERR_ARG, "outer shell edge exceeds the Nyquist frequency");
+    if ((long long)order * K >= N && !(flags & POLY_ALLOW_ALIAS))
+        return set_error(POLY_ERR_ALIAS, "n * K >= N: polygon closures would wrap around the grid");
+
+    enumerate_bins(nshell, p->edges, order, (flags & POLY_BINS_ALL_SORTED) != 0, p->bins);
+    p->nbins = (int64_t)p->bins.size() / order;
+
+    PS_CUDA(cudaGetDevice(&p->device));
+    cudaDeviceProp prop;
+    PS_CUDA(cudaGetDeviceProperties(&prop, p->device));
+    p->sms = prop.multiProcessorCount;
+    if (prec == POLY_SPLIT_BF16 && !(prop.major == 10 && prop.minor == 3))
+        return set_error(POLY_ERR_UNSUPPORTED, "POLY_SPLIT_BF16 needs an sm_103 device");
+    cudaStream_t st = nullptr;
+
+    // twiddles e^{-/+ 2 pi i m / N}, FP64 on the host
+    std::vector<double> twf(2 * N), twi(2 * N);
+    for (int m = 0; m < N; m++) {
+        const double a = 2.0 * 3.14159265358979323846 * (double)m / (double)N;
+        twf[2 * m] = std::cos(a);
+        twf[2 * m + 1] = -std::sin(a);
+        twi[2 * m] = std::cos(a);
+        twi[2 * m + 1] = std::sin(a);
+    }
+    PS_TRY(upload(p, &p->d_tw_fwd, twf));
+    PS_TRY(upload(p, &p->d_tw_inv, twi));
+
+    // shell line tables; slot nshell holds the union of all shells (adjoint)
+    std::vector<short> lines;
+    std::vector<int> off{0};
+    for (int s = 0; s < nshell; s++) {
+        build_lines(p, p->edges.data(), s, lines);
+        off.push_back((int)(lines.size() / 4));
+    }
+    {
+        const double ue[2] = {p->edges[0], p->edges[nshell]};
+        build_lines(p, ue, 0, lines);
+        off.push_back((int)(lines.size() / 4));
+    }
+    PS_TRY(upload(p, &p->d_lines, lines));
+    PS_TRY(upload(p, (void**)&p->d_line_off, off));
+
+    // contraction tiles (CUDA-core path; the counts use them too)
+    build_cc_tiles(p, p->cc);
+    PS_TRY(upload(p, &p->d_cc_tiles, p->cc.tiles));
+    PS_TRY(upload(p, &p->d_cc_field_ids, p->cc.field_ids));
+    PS_TRY(upload(p, &p->d_cc_rowf, p->cc.rowf));
+    PS_TRY(upload(p, &p->d_cc_colf, p->cc.colf));
+    PS_TRY(upload(p, &p->d_cc_slot, p->cc.slot));
+
+    // workspace
+    const size_t n3 = (size_t)N * N * N;
+    const size_t es = p->is_double ? 8 : 4;
+    const size_t nl = (size_t)(2 * K + 1) * (K + 1);
+    PS_TRY(ps_alloc(p, &p->d_W, (size_t)N * nl * 2 * es));
+    PS_TRY(ps_alloc(p, &p->d_fhat, nl * (2 * K + 1) * 2 * es));
+    PS_TRY(ps_alloc(p, &p->d_fields, (size_t)nshell * n3 * es));
+    if (ps_plane_needs_spill(N, K, p->is_double) == 1)
+        PS_TRY(ps_alloc(p, &p->d_spill, ps_spill_elems(N, K, N * nshell, p->is_double) * 2 * es));
+    const int64_t chunk = ps_cc_chunk(p->is_double);
+    const int64_t nchunks = ((int64_t)n3 + chunk - 1) / chunk;
+    p->cc_nsplit = choose_splits((int)p->cc.tiles.size(), nchunks, p->sms);
+    p->cc_cps = (nchunks + p->cc_nsplit - 1) / p->cc_nsplit;
+    p->cc_slot_stride = (int64_t)p->cc.tiles.size() * kCcTM * kCcTN;
+    PS_TRY(ps_alloc(p, (void**)&p->d_partial, (size_t)p->cc_nsplit * p->cc_slot_stride * 8));
+    PS_TRY(ps_alloc(p, (void**)&p->d_S, (size_t)std::max<int64_t>(1, p->nbins) * 8));
+    PS_TRY(ps_alloc(p, (void**)&p->d_counts, (size_t)std::max<int64_t>(1, p->nbins) * 8));
+    PS_TRY(ps_alloc(p, &p->d_in_stage, n3 * es));
+    PS_TRY(ps_alloc(p, (void**)&p->d_out_stage, (size_t)std::max<int64_t>(1, p->nbins) * 8));
+    if (prec == POLY_SPLIT_BF16) PS_TRY(ps_tc_prepare(p));
+
+    // exact counts (plan time, cached)
+    PS_TRY(compute_counts(p, st));
+    PS_CUDA(cudaMemcpy(p->d_counts, p->counts.data(), p->nbins * 8, cudaMemcpyHostToDevice));
+    PS_CUDA(cudaDeviceSynchronize());
+    return POLY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pipeline pieces used by estimate / backward / batched
+// ---------------------------------------------------------------------------
+static void mark(PsPlan* p, int i, cudaStream_t st) {
+    if (p->timing) cudaEventRecord(p->ev[i], st);
+}
+
+poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st) {
+    cudaError_t e;
+    mark(p, 0, st);
+    if ((e = ps_forward(p->N, p->is_double, delta, p->K, p->d_tw_fwd, p->d_W, p->d_fhat, p->d_spill, st)))
+        return cuda_error(e, "forward transform");
+    p->launches += 2;
+    mark(p, 1, st);
+    if ((e = ps_inverse(p->N, p->is_double, 0, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, 0, p->N,
+                        p->d_tw_inv, p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, st)))
+        return cuda_error(e, "shell fields");
+    p->launches += 1;
+    mark(p, 2, st);
+    return POLY_OK;
+}
+
+poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st) {
+    cudaError_t e;
+    if (p->prec == POLY_SPLIT_BF16 && !absval) return ps_tc_sums(p, st);
+    const size_t n3 = (size_t)p->N * p->N * p->N;
+    if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->d_fields, n3, (int64_t)n3, nullptr,
+                            (const PsTile*)p->d_cc_tiles, (int)p->cc.tiles.size(), (const int*)p->d_cc_field_ids,
+                            (const short2*)p->d_cc_rowf, (const short2*)p->d_cc_colf, p->cc_nsplit, p->cc_cps,
+                            p->d_partial, st)))
+        return cuda_error(e, "contraction");
+    if (!absval) mark(p, 3, st);
+    if ((e = ps_reduce_slots(p->d_partial, p->cc_nsplit, p->cc_slot_stride, (const int64_t*)p->d_cc_slot, p->nbins,
+                             p->d_S, st)))
+        return cuda_error(e, "contraction");
+    p->launches += 2;
+    return POLY_OK;
+}
+
+double ps_norm(const PsPlan* p) {
+    const double n3 = (double)p->N * p->N * p->N;
+    return std::pow(p->L * p->L * p->L, p->order - 1) / std::pow(n3, p->order);
+}
+
+poly_status ps_estimate_impl(PsPlan* p, const void* delta, double* out, double* scale, cudaStream_t st) {
+    PS_TRY(ps_fields(p, delta, st));
+    PS_TRY(ps_sums(p, false, st));
+    const double n3 = (double)p->N * p->N * p->N;
+    cudaError_t e;
+    if ((e = ps_normalise(p->d_S, p->d_counts, p->nbins, ps_norm(p), n3, out, st)))
+        return cuda_error(e, "normalise");
+    p->launches += 1;
+    mark(p, 4, st);
+    if (p->timing) p->ev_recorded = true;
+    if (scale) {
+        PS_TRY(ps_sums(p, true, st));
+        if ((e = ps_normalise(p->d_S, p->d_counts, p->nbins, 1.0, n3, scale, st))) return cuda_error(e, "scale");
+        p->launches += 1;
+    }
+    return POLY_OK;
+}
+
+static poly_status enter(poly_plan p, int* prev) {
+    if (!p) return set_error(POLY_ERR_ARG, "NULL plan");
+    *prev = -1;
+    cudaGetDevice(prev);
+    if (*prev != p->device) {
+        cudaError_t e = cudaSetDevice(p->device);
+        if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+    }
+    return POLY_OK;
+}
+
+static void leave(poly_plan p, int prev) {
+    if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+poly_status poly_plan_create(poly_plan* out, int N, double L, int order, int nshell, const double* edges,
+                             poly_precision prec, unsigned flags) {
+    if (!out) return set_error(POLY_ERR_ARG, "NULL output pointer");
+    *out = nullptr;
+    g_last_error.clear();
+    PsPlan* p = new (std::nothrow) PsPlan();
+    if (!p) return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    poly_status s;
+    try {
+        s = create_plan(p, N, L, order, nshell, edges, prec, flags);
+    } catch (const std::bad_alloc&) {
+        s = set_error(POLY_ERR_ALLOC, "host allocation failed");
+    } catch (const std::exception& ex) {
+        s = set_error(POLY_ERR_ARG, ex.what());
+    }
+    if (s != POLY_OK) {
+        free_plan(p);
+        return s;
+    }
+    *out = p;
+    return POLY_OK;
+}
+
+poly_status poly_plan_nbins(poly_plan p, int64_t* nbins) {
+    if (!p || !nbins) return set_error(POLY_ERR_ARG, "NULL argument");
+    *nbins = p->nbins;
+    return POLY_OK;
+}
+
+poly_status poly_plan_bins(poly_plan p, int32_t* idx) {
+    if (!p || !idx) return set_error(POLY_ERR_ARG, "NULL argument");
+    std::memcpy(idx, p->bins.data(), p->bins.size() * sizeof(int32_t));
+    return POLY_OK;
+}
+
+poly_status poly_plan_counts(poly_plan p, int64_t* counts) {
+    if (!p || !counts) return set_error(POLY_ERR_ARG, "NULL argument");
+    std::memcpy(counts, p->counts.data(), p->counts.size() * sizeof(int64_t));
+    return POLY_OK;
+}
+
+poly_status poly_estimate(poly_plan p, const void* delta_x, double* out, double* scale_or_null, void* stream) {
+    if (!p || !delta_x || !out) return set_error(POLY_ERR_ARG, "NULL argument");
+    if ((const void*)out == delta_x || (const void*)scale_or_null == delta_x || out == scale_or_null)
+        return set_error(POLY_ERR_ARG, "output aliases an input");
+    int prev;
+    PS_TRY(enter(p, &prev));
+    poly_status s = ps_estimate_impl(p, delta_x, out, scale_or_null, (cudaStream_t)stream);
+    leave(p, prev);
+    return s;
+}
+
+poly_status poly_estimate_host(poly_plan p, const void* delta_x_host, double* out_host, void* stream) {
+    if (!p || !delta_x_host || !out_host) return set_error(POLY_ERR_ARG, "NULL argument");
+    int prev;
+    PS_TRY(enter(p, &prev));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)p->N * p->N * p->N * (p->is_double ? 8 : 4);
+    poly_status s = POLY_OK;
+    cudaError_t e = cudaMemcpyAsync(p->d_in_stage, delta_x_host, bytes, cudaMemcpyHostToDevice, st);
+    if (e) s = cuda_error(e, "host to device copy");
+    if (!s) s = ps_estimate_impl(p, p->d_in_stage, p->d_out_stage, nullptr, st);
+    if (!s && (e = cudaMemcpyAsync(out_host, p->d_out_stage, p->nbins * 8, cudaMemcpyDeviceToHost, st)))
+        s = cuda_error(e, "device to host copy");
+    if (!s && (e = cudaStreamSynchronize(st))) s = cuda_error(e, "stream synchronise");
+    if (!s) s = ps_check_device_error(p);
+    leave(p, prev);
+    return s;
+}
+
+poly_status poly_backward(poly_plan p, const void* delta_x, const double* dL_dB, void* dL_ddelta, void* stream) {
+    if (!p || !delta_x || !dL_dB || !dL_ddelta) return set_error(POLY_ERR_ARG, "NULL argument");
+    if (dL_ddelta == delta_x || dL_ddelta == (const void*)dL_dB) return set_error(POLY_ERR_ARG, "output aliases an input");
+    int prev;
+    PS_TRY(enter(p, &prev));
+    poly_status s = ps_backward_impl(p, delta_x, dL_dB, dL_ddelta, (cudaStream_t)stream);
+    leave(p, prev);
+    return s;
+}
+
+poly_status poly_estimate_batched(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
+                                  void* stream) {
+    if (count < 0 || (count > 0 && (!plans || !fields || !outs))) return set_error(POLY_ERR_ARG, "bad batch");
+    for (int i = 0; i < count; i++)
+        if (!plans[i] || !fields[i] || !outs[i]) return set_error(POLY_ERR_ARG, "NULL entry in batch");
+    return ps_batched_impl(plans, fields, outs, count, (cudaStream_t)stream);
+}
+
+poly_status poly_plan_sync(poly_plan p, void* stream) {
+    int prev;
+    if (!p) return set_error(POLY_ERR_ARG, "NULL plan");
+    prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->device) cudaSetDevice(p->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    poly_status s = e ? cuda_error(e, "stream synchronise") : ps_check_device_error(p);
+    leave(p, prev);
+    return s;
+}
+
+void poly_plan_destroy(poly_plan p) { free_plan(p); }
+
+poly_status poly_plan_set_timing(poly_plan p, int enable) {
+    if (!p) return set_error(POLY_ERR_ARG, "NULL plan");
+    if (enable && !p->ev[0]) {
+        int prev;
+        PS_TRY(enter(p, &prev));
+        for (auto& e : p->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r) {
+                leave(p, prev);
+                return cuda_error(r, "cudaEventCreate");
+            }
+        }
+        leave(p, prev);
+    }
+    p->timing = enable != 0;
+    p->ev_recorded = false;
+    return POLY_OK;
+}
+
+poly_status poly_plan_stats(poly_plan p, poly_stats* out) {
+    if (!p || !out) return set_error(POLY_ERR_ARG, "NULL argument");
+    std::memset(out, 0, sizeof *out);
+    out->launches = p->launches;
+    if (!p->ev_recorded) return POLY_OK;
+    int prev;
+    PS_TRY(enter(p, &prev));
+    float ms[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaEventSynchronize(p->ev[4]);
+    for (int i = 0; i < 4 && !e; i++) e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
+    leave(p, prev);
+    if (e) return cuda_error(e, "stage events");
+    out->ms_forward = ms[0];
+    out->ms_fields = ms[1];
+    out->ms_contract = ms[2];
+    out->ms_reduce = ms[3];
+    return POLY_OK;
+}
+
+const char* poly_status_string(poly_status s) {
+    switch (s) {
+        case POLY_OK: return "ok";
+        case POLY_ERR_ARG: return "invalid argument";
+        case POLY_ERR_ALIAS: return "grid too small: polygon closures alias (n*K >= N)";
+        case POLY_ERR_ALLOC: return "allocation failed";
+        case POLY_ERR_CUDA: return "CUDA error";
+        case POLY_ERR_TIMEOUT: return "device wait timed out";
+        case POLY_ERR_UNSUPPORTED: return "unsupported configuration";
+        case POLY_ERR_COUNT: return "non-integral polygon count";
+    }
+    return "unknown status";
+}
+
+const char* poly_last_error(void) { return g_last_error.c_str(); }
+
+void poly_debug_fail_alloc_after(int n) { g_fail_alloc_after = n > 0 ? n : 0; }
+
+}  // extern "C"

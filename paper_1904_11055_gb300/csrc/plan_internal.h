@@ -1,0 +1,90 @@
+// Plan state shared by the host-side translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/polyspec.h"
+#include "kernels.h"
+
+struct CcTiles {
+    std::vector<PsTile> tiles;
+    std::vector<int> field_ids;
+    std::vector<short2> rowf, colf;
+    std::vector<int64_t> slot;  // per bin: tile * 64 * 64 + r * 64 + c
+};
+
+struct TcState;  // tensor-core contraction state (contract_tc.cu)
+
+struct poly_plan_s {
+    // configuration
+    int N = 0;
+    double L = 0;
+    int order = 0;
+    int nshell = 0;
+    std::vector<double> edges;
+    poly_precision prec = POLY_FP32;
+    unsigned flags = 0;
+    int is_double = 0;
+    int K = 0;  // largest integer wavevector component inside the outer shell
+    int device = -1;
+    int sms = 0;
+    // bins and counts (host)
+    int64_t nbins = 0;
+    std::vector<int32_t> bins;
+    std::vector<int64_t> counts;
+    // device tables
+    void* d_tw_fwd = nullptr;  // Cx<double>[N], e^{-2 pi i m/N}
+    void* d_tw_inv = nullptr;  // Cx<double>[N], e^{+2 pi i m/N}
+    void* d_lines = nullptr;   // short4 per (shell, line): ky, kz, a, b
+    int* d_line_off = nullptr; // nshell + 2 offsets (last slot: union of all shells)
+    // CUDA-core contraction
+    CcTiles cc;
+    void *d_cc_tiles = nullptr, *d_cc_field_ids = nullptr, *d_cc_rowf = nullptr, *d_cc_colf = nullptr,
+         *d_cc_slot = nullptr;
+    int cc_nsplit = 1;
+    int64_t cc_cps = 0, cc_slot_stride = 0;
+    // workspace
+    void* d_W = nullptr;       // forward intermediate, N x (2K+1)(K+1) complex
+    void* d_fhat = nullptr;    // pruned half spectrum, (2K+1)(K+1)(2K+1) complex
+    void* d_fields = nullptr;  // nshell x N^3 real
+    void* d_spill = nullptr;   // plane-kernel overflow (FP64 at large K)
+    double* d_partial = nullptr;
+    double* d_S = nullptr;
+    int64_t* d_counts = nullptr;
+    void* d_in_stage = nullptr;    // host-buffer entry point staging
+    double* d_out_stage = nullptr;
+    // adjoint workspace (allocated on first backward)
+    void* d_G = nullptr;      // nshell x N^3 real
+    void* d_ghat = nullptr;   // union spectrum
+    void* d_wt = nullptr;     // per-bin weights for the adjoint contraction
+    // tensor-core contraction
+    TcState* tc = nullptr;
+    // instrumentation
+    int64_t launches = 0;
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool ev_recorded = false;
+    // every device allocation owned by the plan
+    std::vector<void*> allocations;
+};
+typedef poly_plan_s PsPlan;
+
+poly_status ps_alloc(PsPlan* p, void** ptr, size_t bytes);
+poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st);
+poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st);
+poly_status ps_estimate_impl(PsPlan* p, const void* delta, double* out, double* scale, cudaStream_t st);
+double ps_norm(const PsPlan* p);
+
+// contract_tc.cu
+poly_status ps_tc_prepare(PsPlan* p);
+poly_status ps_tc_sums(PsPlan* p, cudaStream_t st);
+void ps_tc_free(PsPlan* p);
+poly_status ps_check_device_error(PsPlan* p);
+
+// adjoint.cu / batched
+poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, void* dL_ddelta, cudaStream_t st);
+poly_status ps_batched_impl(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
+                            cudaStream_t st);

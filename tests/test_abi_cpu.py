@@ -1,0 +1,80 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads,
+exports every entry point include/polyspec.h declares, and validates arguments
+before it touches the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1904_11055_gb300 as ps
+from paper_1904_11055_gb300 import build as psbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    psbuild.build()
+    return ps.load_library()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "polyspec.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(poly_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_symbols() == sorted(ps.ABI_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert ps.poly_status_string(code) != "unknown status"
+    assert ps.poly_status_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("kwargs,status", [
+    (dict(N=64, order=5), 6),                                          # order outside [2, 4]
+    (dict(N=50), 6),                                                   # N not supported
+    (dict(N=64, edges=[0.5, 1.5, 1.5]), 1),                            # edges not increasing
+    (dict(N=64, edges=[-1.0, 1.5]), 1),                                # negative edge
+    (dict(N=32, edges=np.arange(18) + 0.5), 1),                        # beyond Nyquist (2K+1 > N)
+    (dict(N=64, edges=np.arange(23) + 0.5), 2),                        # 3 * 22 >= 64: aliasing
+    (dict(N=64, L=-1.0), 1),                                           # bad box size
+    (dict(N=64, prec=2), 6),                                           # TF32x3 not implemented
+])
+def test_argument_validation_before_device(lib, kwargs, status):
+    args = dict(N=64, L=1000.0, order=3, edges=np.arange(17) + 0.5, prec=0, flags=0)
+    args.update(kwargs)
+    with pytest.raises(ps.PolyError) as ei:
+        ps.poly_plan_create(args["N"], args["L"], args["order"], args["edges"], args["prec"], args["flags"])
+    assert ei.value.status == status
+
+
+def test_plan_create_without_device_fails_cleanly(lib):
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(ps.PolyError) as ei:
+        ps.poly_plan_create(32, 100.0, 3, np.arange(9) + 0.5)
+    assert ei.value.status == 4  # POLY_ERR_CUDA
+
+
+def test_null_plan_is_rejected(lib):
+    import ctypes
+
+    n = ctypes.c_int64()
+    assert lib.poly_plan_nbins(None, ctypes.byref(n)) == 1
+    assert lib.poly_estimate(None, None, None, None, None) == 1
+    lib.poly_plan_destroy(None)

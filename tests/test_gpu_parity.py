@@ -1,0 +1,158 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Error measure (the bound of the benchmark spec, same physical prefactor on
+both sides): err_b = |B_gpu - B_ref| / (c_n * scale_ref_b) with
+scale_ref_b = sum_x |prod D| / (N^3 count_b) from the oracle and
+c_n = V^{n-1} / N^{3n}.  Bars: 1e-4 for the plain FP32 path, 1e-5 for the
+split-BF16 tensor-core path, 1e-10 for the FP64 plain method; counts bit-exact.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import fieldgen
+import oracle
+
+torch = pytest.importorskip("torch")
+import paper_1904_11055_gb300 as ps  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TOL = {"fp32": 1e-4, "split_bf16": 1e-5, "fp64": 1e-10}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    from paper_1904_11055_gb300 import build
+
+    build.build()
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+def norm(L, N, n):
+    return (L ** 3) ** (n - 1) / float(N ** 3) ** n
+
+
+def gpu_estimate(delta, L, edges, order, prec, flags=0, bins=None):
+    N = delta.shape[0]
+    plan = ps.Plan(N, L, order, edges, prec, flags)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    d = torch.from_numpy(np.ascontiguousarray(delta)).to("cuda", dt)
+    B = plan.estimate(d)
+    torch.cuda.synchronize()
+    return plan, B.cpu().numpy()
+
+
+def check_against_oracle(delta, L, edges, order, prec, sample=None, flags=0):
+    N = delta.shape[0]
+    plan, B = gpu_estimate(delta, L, edges, order, prec, flags)
+    idx = np.arange(plan.nbins) if sample is None else np.asarray(sample)
+    ref = oracle.estimate(np.asarray(delta, dtype=np.float64), L, edges, order, bins=plan.bins[idx])
+    assert np.array_equal(plan.counts[idx], ref["counts"]), "counts differ from the oracle"
+    err = np.abs(B[idx] - ref["B"]) / (norm(L, N, order) * ref["scale"])
+    return plan, B, ref, err
+
+
+# ------------------------------------------------------------------ counts
+def test_counts_match_golden_enumeration():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "counts_n3_N16_unit6.txt")) if not ln.startswith("#")]
+    g = np.array([[int(v) for v in r] for r in rows if r], dtype=np.int64)
+    plan = ps.Plan(16, 1.0, 3, fieldgen.unit_edges(6), "fp32", ps.POLY_BINS_ALL_SORTED)
+    assert np.array_equal(plan.bins, g[:, :3])
+    assert np.array_equal(plan.counts, g[:, 3])
+
+
+@pytest.mark.parametrize("N,order,nshell,width,flags", [(32, 3, 10, 1.0, 0), (48, 3, 10, 1.5, 0), (32, 4, 7, 1.0, 0),
+                                                        (24, 2, 11, 1.0, 1), (64, 3, 16, 1.0, 0),
+                                                        (96, 3, 32, 1.0, 2)])
+def test_counts_bit_exact(N, order, nshell, width, flags):
+    e = fieldgen.unit_edges(nshell, width)
+    plan = ps.Plan(N, 1.0, order, e, "fp32", flags)
+    ref = oracle.estimate(np.zeros((N, N, N)), 1.0, e, order, bins=plan.bins)
+    assert np.array_equal(plan.bins, oracle.enumerate_bins(e, order, flags & 1))
+    assert np.array_equal(plan.counts, ref["counts"])
+
+
+# ------------------------------------------------------------------ the plain FP64 method (64^3 Gaussian, 16 shells)
+def test_fp64_plain_method_64cube():
+    d = fieldgen.field("gaussian_cut16", 64, 1, np.float64)
+    plan, B, ref, err = check_against_oracle(d, 1000.0, fieldgen.unit_edges(16), 3, "fp64")
+    assert plan.nbins == 508
+    assert err.max() <= TOL["fp64"], err.max()
+
+
+# ------------------------------------------------------------------ FP32 path, several tiles and ragged tails
+@pytest.mark.parametrize("N,order,nshell,kind,seed", [(48, 3, 12, "lognormal", 7), (32, 4, 7, "lognormal", 8),
+                                                      (24, 2, 11, "gaussian", 9), (64, 3, 16, "gaussian_cut16", 1),
+                                                      (16, 3, 4, "white", 10), (96, 3, 20, "lognormal", 11)])
+def test_fp32_matches_oracle(N, order, nshell, kind, seed):
+    d = fieldgen.field(kind, N, seed, np.float32).astype(np.float64)
+    _, _, _, err = check_against_oracle(d, 1000.0, fieldgen.unit_edges(nshell), order, "fp32")
+    assert err.max() <= TOL["fp32"], err.max()
+
+
+def test_fp32_full_size_256cube_sampled():
+    """256^3 lognormal, 64 unit shells (24,432 triangles): sampled bins vs the oracle."""
+    d = fieldgen.field("lognormal", 256, 2, np.float32)
+    e = fieldgen.unit_edges(64)
+    plan, B = gpu_estimate(d, 1000.0, e, 3, "fp32")
+    assert plan.nbins == 24432
+    shells = {64, 63, 41, 40, 33, 32, 31, 17, 9, 2}
+    idx = [i for i, b in enumerate(plan.bins) if set(b.tolist()) <= shells]
+    ref = oracle.estimate(d.astype(np.float64), 1000.0, e, 3, bins=plan.bins[idx])
+    assert np.array_equal(plan.counts[idx], ref["counts"])
+    err = np.abs(B[idx] - ref["B"]) / (norm(1000.0, 256, 3) * ref["scale"])
+    assert len(idx) >= 30
+    assert err.max() <= TOL["fp32"], err.max()
+
+
+# ------------------------------------------------------------------ entry points agree bit for bit
+def test_host_entry_matches_device_entry():
+    d = fieldgen.field("lognormal", 32, 5, np.float32)
+    plan, B = gpu_estimate(d, 500.0, fieldgen.unit_edges(10), 3, "fp32")
+    Bh = plan.estimate_host(d)
+    assert np.array_equal(B, Bh)
+
+
+def test_batched_matches_single_calls():
+    cases = [(32, 8, 21), (48, 12, 22), (32, 8, 23), (24, 7, 24)]
+    plans, fields, singles = [], [], []
+    for N, ns, seed in cases:
+        p = ps.Plan(N, 500.0, 3, fieldgen.unit_edges(ns), "fp32")
+        f = torch.from_numpy(fieldgen.field("lognormal", N, seed, np.float32)).cuda()
+        plans.append(p)
+        fields.append(f)
+        singles.append(p.estimate(f).cpu().numpy())
+    outs = ps.estimate_batched(plans, fields)
+    torch.cuda.synchronize()
+    for o, s in zip(outs, singles):
+        assert np.array_equal(o.cpu().numpy(), s)
+
+
+def test_scale_output_matches_oracle_scale():
+    d = fieldgen.field("lognormal", 32, 12, np.float32).astype(np.float64)
+    e = fieldgen.unit_edges(9)
+    plan = ps.Plan(32, 1000.0, 3, e, "fp32")
+    B, sc = plan.estimate(torch.from_numpy(d).to("cuda", torch.float32), scale=True)
+    ref = oracle.estimate(d, 1000.0, e, 3, bins=plan.bins)
+    assert np.allclose(sc.cpu().numpy(), ref["scale"], rtol=1e-5, atol=0)
+
+
+# ------------------------------------------------------------------ robustness on the host side
+@pytest.mark.parametrize("k", [1, 2, 5, 9, 14])
+def test_allocation_failure_is_reported_and_cleaned_up(k):
+    e = fieldgen.unit_edges(8)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ps.poly_debug_fail_alloc_after(k)
+    try:
+        with pytest.raises(ps.PolyError) as ei:
+            ps.Plan(32, 100.0, 3, e, "fp32")
+        assert ei.value.status == 3
+    finally:
+        ps.poly_debug_fail_alloc_after(0)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 < 8 << 20
