@@ -1,7 +1,7 @@
 // Temporary: tensor-core path, adjoint and batched launch (being written).
 #include "plan_internal.h"
 
-poly_status ps_tc_prepare(PsPlan*) { return POLY_OK; }
+poly_status ps_tc_prepare(PsPlan*) { return POLY_ERR_UNSUPPORTED; }
 poly_status ps_tc_sums(PsPlan*, cudaStream_t) { return POLY_ERR_UNSUPPORTED; }
 void ps_tc_free(PsPlan*) {}
 poly_status ps_check_device_error(PsPlan*) { return POLY_OK; }
