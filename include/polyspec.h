@@ -139,6 +139,8 @@ typedef struct {
     float ms_fields;    /* last timed estimate: shell gather + inverse transforms (all shells) */
     float ms_contract;  /* last timed estimate: the product-sum contraction kernel */
     float ms_reduce;    /* last timed estimate: cross-tile reduction + normalisation */
+    double contract_flops; /* flops the contraction kernel executes per estimate (dense tiles; the tensor
+                              path counts its three split products) */
 } poly_stats;
 
 /*

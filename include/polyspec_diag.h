@@ -1,0 +1,33 @@
+/*
+ * polyspec_diag.h -- diagnostic entry points of the polyspectrum library.
+ *
+ * These exist to check, on the GPU, the hardware layouts the tensor-core
+ * contraction relies on; they are not part of the estimator.  The paper has no
+ * counterpart: they test this implementation, not the method.
+ */
+#ifndef POLYSPEC_DIAG_H
+#define POLYSPEC_DIAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * One-block tcgen05 GEMM on the current device, built exactly like the
+ * contraction's MMA step: D[128][N] = sum_{k<32} A[m][k] * B[n][k] with A
+ * (host, 128 x 32 bf16 bit patterns, row-major) placed in tensor memory by
+ * tcgen05.st, B (host, N x 32 bf16 bit patterns, row-major) placed in shared
+ * memory in the K-major core-matrix layout, FP32 accumulation.  N in
+ * {16, 32, ..., 256}.  D (host, 128 x N float, row-major) receives the result.
+ * Returns 0 on success, 1 for a bad N, 3 allocation failure, 4 CUDA error,
+ * 5 a bounded wait gave up.  Synchronises the device.
+ */
+int poly_diag_tc_gemm(const uint16_t* A_host, const uint16_t* B_host, int N, float* D_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYSPEC_DIAG_H */

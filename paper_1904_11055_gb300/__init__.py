@@ -36,7 +36,7 @@ ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_pl
 
 class poly_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms_forward", ctypes.c_float), ("ms_fields", ctypes.c_float),
-                ("ms_contract", ctypes.c_float), ("ms_reduce", ctypes.c_float)]
+                ("ms_contract", ctypes.c_float), ("ms_reduce", ctypes.c_float), ("contract_flops", ctypes.c_double)]
 
 _lib = None
 

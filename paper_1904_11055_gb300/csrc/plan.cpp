@@ -677,6 +677,14 @@ poly_status poly_plan_stats(poly_plan p, poly_stats* out) {
     if (!p || !out) return set_error(POLY_ERR_ARG, "NULL argument");
     std::memset(out, 0, sizeof *out);
     out->launches = p->launches;
+    {
+        const double n3 = (double)p->N * p->N * p->N;
+        double f = 0;
+        if (p->prec == POLY_SPLIT_BF16) f = ps_tc_executed_flops(p);
+        else
+            for (const auto& t : p->cc.tiles) f += 2.0 * 512.0 * __builtin_popcount(t.region_mask) * n3;
+        out->contract_flops = f;
+    }
     if (!p->ev_recorded) return POLY_OK;
     int prev;
     PS_TRY(enter(p, &prev));

@@ -82,6 +82,7 @@ double ps_norm(const PsPlan* p);
 poly_status ps_tc_prepare(PsPlan* p);
 poly_status ps_tc_sums(PsPlan* p, cudaStream_t st);
 void ps_tc_free(PsPlan* p);
+double ps_tc_executed_flops(const PsPlan* p);
 poly_status ps_check_device_error(PsPlan* p);
 
 // adjoint.cu / batched

@@ -1,10 +1,6 @@
-// Temporary: tensor-core path, adjoint and batched launch (being written).
+// Temporary: adjoint (being written) and the sequential batched launch.
 #include "plan_internal.h"
 
-poly_status ps_tc_prepare(PsPlan*) { return POLY_ERR_UNSUPPORTED; }
-poly_status ps_tc_sums(PsPlan*, cudaStream_t) { return POLY_ERR_UNSUPPORTED; }
-void ps_tc_free(PsPlan*) {}
-poly_status ps_check_device_error(PsPlan*) { return POLY_OK; }
 poly_status ps_backward_impl(PsPlan*, const void*, const double*, void*, cudaStream_t) { return POLY_ERR_UNSUPPORTED; }
 poly_status ps_batched_impl(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
                             cudaStream_t st) {

@@ -59,7 +59,7 @@ def check_against_oracle(delta, L, edges, order, prec, sample=None, flags=0):
 def test_counts_match_golden_enumeration():
     rows = [ln.split() for ln in open(os.path.join(GOLDEN, "counts_n3_N16_unit6.txt")) if not ln.startswith("#")]
     g = np.array([[int(v) for v in r] for r in rows if r], dtype=np.int64)
-    plan = ps.Plan(16, 1.0, 3, fieldgen.unit_edges(6), "fp32", ps.POLY_BINS_ALL_SORTED)
+    plan = ps.Plan(16, 1.0, 3, fieldgen.unit_edges(6), "fp32", ps.POLY_BINS_ALL_SORTED | ps.POLY_ALLOW_ALIAS)
     assert np.array_equal(plan.bins, g[:, :3])
     assert np.array_equal(plan.counts, g[:, 3])
 
@@ -84,28 +84,45 @@ def test_fp64_plain_method_64cube():
 
 
 # ------------------------------------------------------------------ FP32 path, several tiles and ragged tails
-@pytest.mark.parametrize("N,order,nshell,kind,seed", [(48, 3, 12, "lognormal", 7), (32, 4, 7, "lognormal", 8),
-                                                      (24, 2, 11, "gaussian", 9), (64, 3, 16, "gaussian_cut16", 1),
-                                                      (16, 3, 4, "white", 10), (96, 3, 20, "lognormal", 11)])
-def test_fp32_matches_oracle(N, order, nshell, kind, seed):
+CASES = [(48, 3, 12, "lognormal", 7), (32, 4, 7, "lognormal", 8), (24, 2, 11, "gaussian", 9),
+         (64, 3, 16, "gaussian_cut16", 1), (16, 3, 4, "white", 10), (96, 3, 20, "lognormal", 11),
+         (48, 4, 11, "lognormal", 13)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("N,order,nshell,kind,seed", CASES)
+def test_matches_oracle(prec, N, order, nshell, kind, seed):
     d = fieldgen.field(kind, N, seed, np.float32).astype(np.float64)
-    _, _, _, err = check_against_oracle(d, 1000.0, fieldgen.unit_edges(nshell), order, "fp32")
-    assert err.max() <= TOL["fp32"], err.max()
+    _, _, _, err = check_against_oracle(d, 1000.0, fieldgen.unit_edges(nshell), order, prec)
+    assert err.max() <= TOL[prec], err.max()
 
 
-def test_fp32_full_size_256cube_sampled():
-    """256^3 lognormal, 64 unit shells (24,432 triangles): sampled bins vs the oracle."""
-    d = fieldgen.field("lognormal", 256, 2, np.float32)
+@pytest.fixture(scope="module")
+def field256():
+    return fieldgen.field("lognormal", 256, 2, np.float32)
+
+
+@pytest.fixture(scope="module")
+def oracle256(field256):
+    """Oracle on the bins among ten shells of the 256^3, 64-shell workload."""
     e = fieldgen.unit_edges(64)
-    plan, B = gpu_estimate(d, 1000.0, e, 3, "fp32")
-    assert plan.nbins == 24432
+    bins = oracle.enumerate_bins(e, 3)
     shells = {64, 63, 41, 40, 33, 32, 31, 17, 9, 2}
-    idx = [i for i, b in enumerate(plan.bins) if set(b.tolist()) <= shells]
-    ref = oracle.estimate(d.astype(np.float64), 1000.0, e, 3, bins=plan.bins[idx])
+    idx = np.array([i for i, b in enumerate(bins) if set(b.tolist()) <= shells])
+    return idx, oracle.estimate(field256.astype(np.float64), 1000.0, e, 3, bins=bins[idx])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_full_size_256cube_sampled(prec, field256, oracle256):
+    """256^3 lognormal, 64 unit shells (24,432 triangles), the configuration bench.py times."""
+    e = fieldgen.unit_edges(64)
+    plan, B = gpu_estimate(field256, 1000.0, e, 3, prec)
+    assert plan.nbins == 24432
+    idx, ref = oracle256
+    assert len(idx) >= 30
     assert np.array_equal(plan.counts[idx], ref["counts"])
     err = np.abs(B[idx] - ref["B"]) / (norm(1000.0, 256, 3) * ref["scale"])
-    assert len(idx) >= 30
-    assert err.max() <= TOL["fp32"], err.max()
+    assert err.max() <= TOL[prec], err.max()
 
 
 # ------------------------------------------------------------------ entry points agree bit for bit
