@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kPlaneThreads) inv_plane_kernel(
         const int ky = L.x, kz = L.y, a = L.z, b = L.w;
         const Cx<T>* Fl = fhat + ((size_t)(ky + K) * (K + 1) + kz) * nk + K;
         T sr = 0, si = 0;
-        // kx in [a, b] and, when a > 0, kx in [-b, -a]
+        // kx in [a, b] and kx in [-b, -max(a, 1)]
         int m = (int)(((long long)a * x) % N);
         for (int kx = a; kx <= b; kx++) {
             const Cx<T> w = s_tw[m];
@@ -211,9 +211,10 @@ __global__ void __launch_bounds__(kPlaneThreads) inv_plane_kernel(
             m += x;
             if (m >= N) m -= N;
         }
-        if (a > 0) {
-            m = (int)(((long long)(N - a) * x) % N);  // -a * x mod N
-            for (int kx = -a; kx >= -b; kx--) {
+        const int an = a > 0 ? a : 1;  // the negative run, kx in [-b, -max(a, 1)]
+        if (b >= an) {
+            m = (int)(((long long)(N - an) * x) % N);  // -an * x mod N
+            for (int kx = -an; kx >= -b; kx--) {
                 const Cx<T> w = s_tw[m];
                 if (UNITY) {
                     sr += w.re;

@@ -361,6 +361,7 @@ static void free_plan(PsPlan* p) {
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
     ps_tc_free(p);
+    ps_adj_free(p);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
 }

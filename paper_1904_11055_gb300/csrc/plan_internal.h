@@ -16,7 +16,8 @@ struct CcTiles {
     std::vector<int64_t> slot;  // per bin: tile * 64 * 64 + r * 64 + c
 };
 
-struct TcState;  // tensor-core contraction state (contract_tc.cu)
+struct TcState;     // tensor-core contraction state (contract_tc.cu)
+struct AdjTables;  // adjoint entry tables (adjoint.cu)
 
 struct poly_plan_s {
     // configuration
@@ -59,7 +60,7 @@ struct poly_plan_s {
     // adjoint workspace (allocated on first backward)
     void* d_G = nullptr;      // nshell x N^3 real
     void* d_ghat = nullptr;   // union spectrum
-    void* d_wt = nullptr;     // per-bin weights for the adjoint contraction
+    AdjTables* adj = nullptr;
     // tensor-core contraction
     TcState* tc = nullptr;
     // instrumentation
@@ -86,6 +87,7 @@ double ps_tc_executed_flops(const PsPlan* p);
 poly_status ps_check_device_error(PsPlan* p);
 
 // adjoint.cu / batched
+void ps_adj_free(PsPlan* p);
 poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, void* dL_ddelta, cudaStream_t st);
 poly_status ps_batched_impl(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
                             cudaStream_t st);

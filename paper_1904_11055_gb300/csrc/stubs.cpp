@@ -1,7 +1,6 @@
-// Temporary: adjoint (being written) and the sequential batched launch.
+// Temporary: the sequential batched launch.
 #include "plan_internal.h"
 
-poly_status ps_backward_impl(PsPlan*, const void*, const double*, void*, cudaStream_t) { return POLY_ERR_UNSUPPORTED; }
 poly_status ps_batched_impl(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
                             cudaStream_t st) {
     for (int i = 0; i < count; i++) {
