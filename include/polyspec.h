@@ -152,6 +152,37 @@ poly_status poly_plan_set_timing(poly_plan plan, int enable);
 /* Launch count and stage durations of the last timed estimate (waits for its events). */
 poly_status poly_plan_stats(poly_plan plan, poly_stats* out);
 
+/*
+ * Bispectrum of one small field without allocating any device memory.
+ *
+ * The paper has no counterpart; this is for callers that cannot call
+ * cudaMalloc at the moment they need an estimate: code running after its
+ * device-memory budget has been fixed, code inside a framework that owns the
+ * device allocator, or latency-critical loops that must not allocate (an
+ * allocation can synchronise the device).  It computes what poly_estimate
+ * computes for a POLY_FP32 plan of order 3 with the default (polygon) bins,
+ * with the same kernels, but keeps every intermediate in one static device
+ * array of 32 MiB that belongs to the library.  Every GPU that loads the
+ * library holds those 32 MiB until the process exits.
+ *
+ *  N, L, nshell, edges: as for poly_plan_create (order is 3, flags 0).
+ *  delta_x: device, N^3 float.   out: device, nbins double (B_b, paper order).
+ *  counts: HOST, nbins int64: the exact polygon counts of these bins, e.g. from
+ *          poly_plan_counts of a plan with the same N and edges, made earlier.
+ *  stream: cudaStream_t; the call is asynchronous on it.
+ *
+ * Problems whose intermediates do not fit in 32 MiB (roughly nshell * N^3 * 4
+ * bytes of fields plus a few MiB) are rejected with POLY_ERR_UNSUPPORTED and a
+ * message from poly_last_error(); e.g. N = 64 with 16 shells fits, 256^3 does
+ * not.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture.  All calls share the array, and each overwrites it: calls whose
+ * work overlaps on the GPU (other streams or host threads) race, so serialise
+ * them.
+ */
+poly_status poly_estimate_noalloc(int N, double L, int nshell, const double* edges, const float* delta_x,
+                                  const int64_t* counts, double* out, void* stream);
+
 /* Static description of a status code. */
 const char* poly_status_string(poly_status status);
 

@@ -31,7 +31,7 @@ POLY_ALLOW_ALIAS = 0x2
 ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_plan_counts", "poly_estimate",
                "poly_estimate_host", "poly_backward", "poly_estimate_batched", "poly_plan_sync", "poly_plan_destroy",
                "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
-               "poly_plan_stats")
+               "poly_plan_stats", "poly_estimate_noalloc")
 
 
 class poly_stats(ctypes.Structure):
@@ -72,6 +72,7 @@ def load_library():
     L.poly_last_error.restype = ctypes.c_char_p
     L.poly_plan_set_timing.argtypes = [P, i32]
     L.poly_plan_stats.argtypes = [P, ctypes.POINTER(poly_stats)]
+    L.poly_estimate_noalloc.argtypes = [i32, f64, i32, P, P, P, P, P]
     L.poly_debug_fail_alloc_after.argtypes = [i32]
     L.poly_debug_fail_alloc_after.restype = None
     for name in ABI_SYMBOLS:
@@ -149,8 +150,18 @@ def poly_plan_set_timing(plan: int, enable: bool) -> None:
 
 def poly_plan_stats(plan: int) -> dict:
     st = poly_stats()
-    _check(load_library().poly_plan_stats(plan, ctypes.byref(st)), "poly_plan_stats")
+    _check(load_library().poly_plan_stats(plan, ctypes.byref(st)), "poly_plan_stats", "poly_estimate_noalloc")
     return {k: getattr(st, k) for k, _ in poly_stats._fields_}
+
+
+def poly_estimate_noalloc(N: int, L: float, edges, delta_ptr: int, counts: np.ndarray, out_ptr: int,
+                          stream: int | None) -> None:
+    """B_b of a small order-3 FP32 problem with no device allocation (see include/polyspec.h)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    _check(load_library().poly_estimate_noalloc(int(N), float(L), e.size - 1, e.ctypes.data_as(ctypes.c_void_p),
+                                                delta_ptr, c.ctypes.data_as(ctypes.c_void_p), out_ptr, stream),
+           "poly_estimate_noalloc")
 
 
 def poly_status_string(status: int) -> str:

@@ -63,6 +63,8 @@ bool member(const double* edges, int s, long long q2) {
 
 }  // namespace
 
+void ps_set_last_error(const std::string& msg) { g_last_error = msg; }
+
 // ---------------------------------------------------------------------------
 // allocation helper with the failure-injection hook
 // ---------------------------------------------------------------------------
@@ -92,7 +94,7 @@ static poly_status upload(PsPlan* p, void** dptr, const std::vector<V>& h) {
 // ---------------------------------------------------------------------------
 // bins: k_1 >= ... >= k_n (1-based), row-major with k_n fastest, polygon rule
 // ---------------------------------------------------------------------------
-static void enumerate_bins(int nshell, const std::vector<double>& edges, int order, bool all_sorted,
+void enumerate_bins(int nshell, const std::vector<double>& edges, int order, bool all_sorted,
                            std::vector<int32_t>& out) {
     std::vector<double> c(nshell);
     for (int s = 0; s < nshell; s++) c[s] = 0.5 * (edges[s] + edges[s + 1]);
@@ -120,7 +122,7 @@ static void enumerate_bins(int nshell, const std::vector<double>& edges, int ord
 // shell line tables: per shell, the (ky, kz >= 0) lines crossing it and the
 // |kx| run [a, b] on each line (membership is monotone in |kx|)
 // ---------------------------------------------------------------------------
-static void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines) {
+void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines) {
     const int K = p->K;
     for (int ky = -K; ky <= K; ky++)
         for (int kz = 0; kz <= K; kz++) {
@@ -145,7 +147,7 @@ static void build_lines(const PsPlan* p, const double* e, int s, std::vector<sho
 // bin, cols = products of the rest; rows grouped 64 at a time after sorting by
 // their column span, each group's column union cut into chunks of 64.
 // ---------------------------------------------------------------------------
-static void build_cc_tiles(PsPlan* p, CcTiles& t) {
+void build_cc_tiles(PsPlan* p, CcTiles& t) {
     const int n = p->order;
     const int ra = n >= 3 ? 2 : 1, ca = n - ra;
     auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra == 2 ? b[1] : -1); };

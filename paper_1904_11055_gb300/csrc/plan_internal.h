@@ -74,6 +74,11 @@ struct poly_plan_s {
 typedef poly_plan_s PsPlan;
 
 poly_status ps_alloc(PsPlan* p, void** ptr, size_t bytes);
+void ps_set_last_error(const std::string& msg);
+// host-side tables (plan.cpp)
+void enumerate_bins(int nshell, const std::vector<double>& edges, int order, bool all_sorted, std::vector<int32_t>& out);
+void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines);
+void build_cc_tiles(PsPlan* p, CcTiles& t);
 poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st);
 poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st);
 poly_status ps_estimate_impl(PsPlan* p, const void* delta, double* out, double* scale, cudaStream_t st);
