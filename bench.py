@@ -30,6 +30,15 @@ sys.path.insert(0, ROOT)
 METRIC = "bispectrum configs/s at 256³ N_max=64, split-BF16 vs FP32 on GB300 at rel err ≤1e-5"
 N, L, NSHELL, ORDER, SEED = 256, 1000.0, 64, 3, 2
 WORKLOAD = "bispectrum, 256^3 lognormal field (seed 2), 64 unit shells k_F..64k_F, n=3, 24432 bins"
+
+
+def set_workload(n: int, nshell: int, order: int):
+    """Other sizes (profiling cases, trispectrum); the default is the metric's workload."""
+    global N, NSHELL, ORDER, WORKLOAD
+    if (n, nshell, order) == (N, NSHELL, ORDER):
+        return
+    N, NSHELL, ORDER = n, nshell, order
+    WORKLOAD = f"order-{order} polyspectrum, {n}^3 lognormal field (seed 2), {nshell} unit shells (not the metric workload)"
 SAMPLE_SHELLS = (59, 60, 61, 62, 63, 64)  # CPU baseline sample: the bins among these shells
 
 
@@ -76,7 +85,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -313,7 +322,7 @@ def run_ours(args):
         "precisions": {p: ({k: r[k] for k in ("value", "ms_per_step", "roofline", "stage_ms", "e2e")}
                            if "value" in r else r) for p, r in results.items()},
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and (N, NSHELL, ORDER) == (256, 64, 3):
         line["cpu_baseline"] = cpu_baseline(delta_np)
     print(json.dumps(line), flush=True)
     if dist_ok:
@@ -328,7 +337,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "split_bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--N", type=int, default=N, help="grid size (default: the metric workload)")
+    ap.add_argument("--nshell", type=int, default=NSHELL)
+    ap.add_argument("--order", type=int, default=ORDER)
     args = ap.parse_args()
+    set_workload(args.N, args.nshell, args.order)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
