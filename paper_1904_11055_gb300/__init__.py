@@ -150,7 +150,7 @@ def poly_plan_set_timing(plan: int, enable: bool) -> None:
 
 def poly_plan_stats(plan: int) -> dict:
     st = poly_stats()
-    _check(load_library().poly_plan_stats(plan, ctypes.byref(st)), "poly_plan_stats", "poly_estimate_noalloc")
+    _check(load_library().poly_plan_stats(plan, ctypes.byref(st)), "poly_plan_stats")
     return {k: getattr(st, k) for k, _ in poly_stats._fields_}
 
 

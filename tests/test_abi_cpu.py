@@ -78,3 +78,20 @@ def test_null_plan_is_rejected(lib):
     assert lib.poly_plan_nbins(None, ctypes.byref(n)) == 1
     assert lib.poly_estimate(None, None, None, None, None) == 1
     lib.poly_plan_destroy(None)
+
+
+def test_binding_wrappers_marshal_without_a_device(lib):
+    """Every ABI-named wrapper reaches the library and maps a NULL plan to POLY_ERR_ARG."""
+    calls = [
+        lambda: ps.poly_plan_nbins(None),
+        lambda: ps.poly_plan_counts(None),
+        lambda: ps.poly_plan_stats(None),
+        lambda: ps.poly_plan_set_timing(None, True),
+        lambda: ps.poly_plan_sync(None),
+        lambda: ps.poly_estimate(None, None, None, None, None),
+        lambda: ps.poly_backward(None, None, None, None, None),
+    ]
+    for call in calls:
+        with pytest.raises(ps.PolyError) as ei:
+            call()
+        assert ei.value.status == 1
