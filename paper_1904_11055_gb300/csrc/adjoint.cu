@@ -218,10 +218,11 @@ poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, 
         p->launches += 3;
     }
     // one inverse transform over the union of the shells
+    if (!ps_xpre_fits(p, p->nshell, 1)) return POLY_ERR_ARG;
     if ((e = ps_inverse(p->N, dbl, 0, p->d_ghat, p->d_lines, p->d_line_off, p->nshell, 1, p->K, 0, p->N, p->d_tw_inv,
-                        dL_ddelta, (size_t)ncell, p->d_spill, st)))
+                        dL_ddelta, (size_t)ncell, p->d_spill, p->d_xpre, p->max_lines, st)))
         return POLY_ERR_CUDA;
-    p->launches += 1;
+    p->launches += 2;
     return POLY_OK;
 }
 

@@ -17,6 +17,15 @@ namespace ps {
 constexpr int kCcThreads = 256;
 constexpr int kFlushChunks = 32;  // 32 chunks x 32 cells = 1024 cells per FP32 partial sum
 
+PS_DEV void load4(const float* p, float* v) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+PS_DEV void load4(const double* p, double* v) {
+    const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
+}
+
 template <typename T, bool WEIGHTED, bool ABS>
 __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
     const T* __restrict__ fields, size_t fstride, int64_t ncell, const T* __restrict__ weight,
@@ -55,16 +64,33 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
     const int64_t cbeg = (int64_t)blockIdx.y * chunks_per_split;
     const int64_t cend = min(nchunks, cbeg + chunks_per_split);
     __syncthreads();
+    // register prefetch of the next chunk's field values (each thread owns a fixed set of (f, x))
+    constexpr int PF = kCcMaxFields * CH / kCcThreads;
+    const int nload = tile.nfield * CH;
+    T pf[PF];
+    auto fetch = [&](int64_t ch) {
+#pragma unroll
+        for (int k = 0; k < PF; k++) {
+            const int e = tid + k * kCcThreads;
+            if (e < nload) {
+                const int f = e / CH, x = e - (e / CH) * CH;
+                const int64_t cell = ch * CH + x;
+                pf[k] = (ch < cend && cell < ncell) ? fields[(size_t)s_fid[f] * fstride + cell] : (T)0;
+            }
+        }
+    };
+    if (cbeg < cend) fetch(cbeg);
     int since_flush = 0;
     for (int64_t ch = cbeg; ch < cend; ch++) {
         const int64_t base = ch * CH;
-        // 1. the tile's distinct fields for this chunk
-        for (int e = tid; e < tile.nfield * CH; e += kCcThreads) {
-            const int f = e / CH, x = e - (e / CH) * CH;
-            const int64_t cell = base + x;
-            s_d[f][x] = cell < ncell ? fields[(size_t)s_fid[f] * fstride + cell] : (T)0;
+        // 1. this chunk's field values into shared memory, then prefetch the next chunk
+#pragma unroll
+        for (int k = 0; k < PF; k++) {
+            const int e = tid + k * kCcThreads;
+            if (e < nload) s_d[e / CH][e - (e / CH) * CH] = pf[k];
         }
         __syncthreads();
+        fetch(ch + 1);
         // 2. row and column products
         for (int e = tid; e < CH * TM; e += kCcThreads) {
             const int x = e / TM, r = e - (e / TM) * TM;
@@ -93,16 +119,13 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
             s_b[x][c] = v;
         }
         __syncthreads();
-        // 3. 4x4 outer products per lane over the chunk
+        // 3. 4x4 outer products per lane over the chunk (16-byte vector loads)
         if (active) {
 #pragma unroll 8
             for (int x = 0; x < CH; x++) {
                 T a[4], b[4];
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    a[i] = s_a[x][r0 + i];
-                    b[i] = s_b[x][c0 + i];
-                }
+                load4(&s_a[x][r0], a);
+                load4(&s_b[x][c0], b);
 #pragma unroll
                 for (int i = 0; i < 4; i++)
 #pragma unroll

@@ -11,10 +11,12 @@ size_t ps_spill_elems(int n, int K, int nblocks, int is_double);
 // delta [N^3] real -> W [N][(2K+1)(K+1)] -> fhat [(2K+1)(K+1)][2K+1] (complex, same precision)
 cudaError_t ps_forward(int n, int is_double, const void* delta, int K, const void* tw_fwd, void* W, void* fhat,
                        void* spill, cudaStream_t st);
-// shells s0..s0+ns-1, planes x0..x0+nx-1 -> out[(s-s0)*out_stride + (x-x0)*N*N + y*N + z]
+// shells s0..s0+ns-1, planes x0..x0+nx-1 -> out[(s-s0)*out_stride + (x-x0)*N*N + y*N + z].
+// xpre != NULL (and not unity): first run the x pass into xpre (sum over shells of lines * N complex values;
+// max_lines = the largest line count of the shells), then scatter; otherwise gather along x in the plane kernel.
 cudaError_t ps_inverse(int n, int is_double, int unity, const void* fhat, const void* lines, const int* line_off,
                        int s0, int ns, int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride,
-                       void* spill, cudaStream_t st);
+                       void* spill, void* xpre, int max_lines, cudaStream_t st);
 
 // ---- contract_cc.cu -----------------------------------------------------------
 // One GEMM tile of the CUDA-core contraction: up to 64 rows x 64 cols, each row

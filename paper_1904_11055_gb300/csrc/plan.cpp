@@ -305,7 +305,7 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
         for (int s0 = 0; s0 < p->nshell && !rc; s0 += sb) {
             const int ns = std::min(sb, p->nshell - s0);
             if ((e = ps_inverse(N, 1, 1, nullptr, p->d_lines, p->d_line_off, s0, ns, p->K, 0, h + 1, p->d_tw_inv,
-                                d_planes, plane_elems, d_spill, st))) {
+                                d_planes, plane_elems, d_spill, nullptr, 0, st))) {
                 rc = cuda_error(e, "counting fields");
                 break;
             }
@@ -434,6 +434,8 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
         build_lines(p, ue, 0, lines);
         off.push_back((int)(lines.size() / 4));
     }
+    p->line_off = off;
+    for (int s = 0; s <= nshell; s++) p->max_lines = std::max(p->max_lines, off[s + 1] - off[s]);
     PS_TRY(upload(p, &p->d_lines, lines));
     PS_TRY(upload(p, (void**)&p->d_line_off, off));
 
@@ -452,6 +454,12 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     PS_TRY(ps_alloc(p, &p->d_W, (size_t)N * nl * 2 * es));
     PS_TRY(ps_alloc(p, &p->d_fhat, nl * (2 * K + 1) * 2 * es));
     PS_TRY(ps_alloc(p, &p->d_fields, (size_t)nshell * n3 * es));
+    {   // x-pass output, indexed by the global line offset: every line of every shell and of
+        // the union of the shells (used by the adjoint), at every x
+        const size_t lines_all = (size_t)off[nshell + 1];
+        PS_TRY(ps_alloc(p, &p->d_xpre, lines_all * N * 2 * es));
+        p->xpre_lines = lines_all;
+    }
     if (ps_plane_needs_spill(N, K, p->is_double) == 1)
         PS_TRY(ps_alloc(p, &p->d_spill, ps_spill_elems(N, K, N * nshell, p->is_double) * 2 * es));
     const int64_t chunk = ps_cc_chunk(p->is_double);
@@ -476,6 +484,10 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
 // ---------------------------------------------------------------------------
 // pipeline pieces used by estimate / backward / batched
 // ---------------------------------------------------------------------------
+bool ps_xpre_fits(const PsPlan* p, int s0, int ns) {
+    return s0 >= 0 && s0 + ns <= p->nshell + 1 && (size_t)p->line_off[s0 + ns] <= p->xpre_lines;
+}
+
 static void mark(PsPlan* p, int i, cudaStream_t st) {
     if (p->timing) cudaEventRecord(p->ev[i], st);
 }
@@ -487,10 +499,12 @@ poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st) {
         return cuda_error(e, "forward transform");
     p->launches += 2;
     mark(p, 1, st);
+    if (!ps_xpre_fits(p, 0, p->nshell)) return set_error(POLY_ERR_ARG, "x-pass buffer too small");
     if ((e = ps_inverse(p->N, p->is_double, 0, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, 0, p->N,
-                        p->d_tw_inv, p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, st)))
+                        p->d_tw_inv, p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, p->d_xpre,
+                        p->max_lines, st)))
         return cuda_error(e, "shell fields");
-    p->launches += 1;
+    p->launches += 2;  // x pass + plane kernel
     mark(p, 2, st);
     return POLY_OK;
 }

@@ -41,6 +41,10 @@ struct poly_plan_s {
     void* d_tw_inv = nullptr;  // Cx<double>[N], e^{+2 pi i m/N}
     void* d_lines = nullptr;   // short4 per (shell, line): ky, kz, a, b
     int* d_line_off = nullptr; // nshell + 2 offsets (last slot: union of all shells)
+    std::vector<int> line_off; // host copy
+    int max_lines = 0;         // largest line count of one shell (or of the union)
+    void* d_xpre = nullptr;    // x-pass output of the inverse transform
+    size_t xpre_lines = 0;     // lines the x-pass buffer holds (indexed by global line offset)
     // CUDA-core contraction
     CcTiles cc;
     void *d_cc_tiles = nullptr, *d_cc_field_ids = nullptr, *d_cc_rowf = nullptr, *d_cc_colf = nullptr,
@@ -80,6 +84,8 @@ void enumerate_bins(int nshell, const std::vector<double>& edges, int order, boo
 void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines);
 void build_cc_tiles(PsPlan* p, CcTiles& t);
 poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st);
+// true when the x-pass buffer holds shells [s0, s0 + ns) (global line offsets)
+bool ps_xpre_fits(const PsPlan* p, int s0, int ns);
 poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st);
 poly_status ps_estimate_impl(PsPlan* p, const void* delta, double* out, double* scale, cudaStream_t st);
 double ps_norm(const PsPlan* p);
