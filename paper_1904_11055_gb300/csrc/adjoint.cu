@@ -45,9 +45,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_g_kernel(const T* __restrict_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s_d = reinterpret_cast<T*>(smem_raw);  // [nshell][kAdjChunk]
     const int64_t x0 = (int64_t)blockIdx.x * kAdjChunk;
-    for (int i = threadIdx.x; i < nshell * kAdjChunk; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nshell * kAdjChunk; i += blockDim.x) {  // D is cell-tiled over nshell shells
         const int s = i / kAdjChunk, x = i - s * kAdjChunk;
-        s_d[i] = x0 + x < ncell ? D[(size_t)s * ncell + x0 + x] : (T)0;
+        const int64_t cell = x0 + x;
+        s_d[i] = cell < ncell ? D[(size_t)(cell >> 5) * nshell * 32 + (size_t)s * 32 + (cell & 31)] : (T)0;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -220,7 +221,7 @@ poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, 
     // one inverse transform over the union of the shells
     if (!ps_xpre_fits(p, p->nshell, 1)) return POLY_ERR_ARG;
     if ((e = ps_inverse(p->N, dbl, 0, p->d_ghat, p->d_lines, p->d_line_off, p->nshell, 1, p->K, 0, p->N, p->d_tw_inv,
-                        dL_ddelta, (size_t)ncell, p->d_spill, p->d_xpre, p->max_lines, st)))
+                        dL_ddelta, (size_t)ncell, p->d_spill, p->d_xpre, p->max_lines, 0, st)))
         return POLY_ERR_CUDA;
     p->launches += 2;
     return POLY_OK;

@@ -28,7 +28,7 @@ PS_DEV void load4(const double* p, double* v) {
 
 template <typename T, bool WEIGHTED, bool ABS>
 __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
-    const T* __restrict__ fields, size_t fstride, int64_t ncell, const T* __restrict__ weight,
+    const T* __restrict__ fields, size_t fstride, int tile_ns, int64_t ncell, const T* __restrict__ weight,
     const PsTile* __restrict__ tiles, int ntiles, const int* __restrict__ field_ids, const short2* __restrict__ rowf,
     const short2* __restrict__ colf, int64_t chunks_per_split, double* __restrict__ partial) {
     constexpr int CH = sizeof(T) == 8 ? 16 : 32, TM = kCcTM, TN = kCcTN;
@@ -75,7 +75,9 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
             if (e < nload) {
                 const int f = e / CH, x = e - (e / CH) * CH;
                 const int64_t cell = ch * CH + x;
-                pf[k] = (ch < cend && cell < ncell) ? fields[(size_t)s_fid[f] * fstride + cell] : (T)0;
+                const size_t a = tile_ns > 0 ? (size_t)(cell >> 5) * tile_ns * 32 + (size_t)s_fid[f] * 32 + (cell & 31)
+                                             : (size_t)s_fid[f] * fstride + cell;
+                pf[k] = (ch < cend && cell < ncell) ? fields[a] : (T)0;
             }
         }
     };
@@ -173,32 +175,32 @@ __global__ void normalise_kernel(const double* __restrict__ S, const int64_t* __
 using namespace ps;
 
 cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
-                           int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
+                           int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
                            const short2* rowf, const short2* colf, int nsplit, int64_t chunks_per_split,
                            double* partial, cudaStream_t st) {
     dim3 grid(ntiles, nsplit);
     if (is_double) {
         if (weighted)
             contract_cc_kernel<double, true, false><<<grid, kCcThreads, 0, st>>>(
-                (const double*)fields, field_stride, ncell, (const double*)weight, tiles, ntiles, field_ids, rowf,
+                (const double*)fields, field_stride, tile_ns, ncell, (const double*)weight, tiles, ntiles, field_ids, rowf,
                 colf, chunks_per_split, partial);
         else if (absval)
             contract_cc_kernel<double, false, true><<<grid, kCcThreads, 0, st>>>(
-                (const double*)fields, field_stride, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
+                (const double*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
         else
             contract_cc_kernel<double, false, false><<<grid, kCcThreads, 0, st>>>(
-                (const double*)fields, field_stride, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
+                (const double*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
     } else {
         if (weighted) return cudaErrorInvalidValue;
         if (absval)
             contract_cc_kernel<float, false, true><<<grid, kCcThreads, 0, st>>>(
-                (const float*)fields, field_stride, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
+                (const float*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
         else
             contract_cc_kernel<float, false, false><<<grid, kCcThreads, 0, st>>>(
-                (const float*)fields, field_stride, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
+                (const float*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
     }
     return cudaGetLastError();

@@ -10,11 +10,12 @@
 // (round-to-nearest adds), and the per-block sums are reduced in FP64 across
 // blocks in a fixed order.
 //
-// Block layout: 8 producer warps + 1 control warp.  The control thread streams
-// 32-cell chunks of all shell fields into shared memory with TMA (128-byte
-// swizzle) and issues the MMAs; the producers write the pair products of their
-// TMEM lanes (A operand, M = 128 rows per tile) with tcgen05.st and the column
-// factors (B operand) into shared memory in the K-major core-matrix layout.
+// Block layout: 16 producer warps + 1 control warp.  The control thread streams
+// 32-cell chunks of all shell fields (one contiguous block of the cell-tiled
+// field layout) into shared memory with TMA (128-byte swizzle) and issues the
+// MMAs; the producers write the pair products of their TMEM lanes (A operand,
+// M = 128 rows per tile) with tcgen05.st and the column factors (B operand)
+// into shared memory in the K-major core-matrix layout.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -34,8 +35,8 @@
 namespace ps {
 
 constexpr int kTcChunk = 32;         // cells per chunk (K of one pipeline step)
-constexpr int kTcStages = 3;         // TMA stages
-constexpr int kTcProducers = 256;    // 8 warps
+constexpr int kTcStages = 6;         // TMA stages
+constexpr int kTcProducers = 512;    // 16 warps: 4 per TMEM lane quadrant, each owning 8 cells of a chunk
 constexpr int kTcThreads = kTcProducers + 32;
 constexpr int kTcMaxMT = 4;          // M tiles per block
 constexpr int kTcAccMax = 256;       // accumulator columns per block
@@ -62,44 +63,58 @@ struct TcCta {  // one block: a group and a chunk range
 };
 
 // ---------------------------------------------------------------------------------
+// One MMA of a chunk, precomputed per block: accumulator column, A column within
+// the slot, B byte offset within the slot's buffer, instruction descriptor, and
+// flags (bit 0: B = lo part, bit 1: first product of a K-step pair (resets at a window start)).
+struct TcMma {
+    uint32_t d_col, a_col, b_off, idesc_flags;
+};
+constexpr int kTcMaxMma = 256;
+
 template <int RA, int CA>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_contract_kernel(const __grid_constant__ CUtensorMap fmap, int nshell, int stage_bytes, int bbuf_bytes,
-                       int window, const TcCta* __restrict__ ctas, const TcGroup* __restrict__ groups,
-                       const TcMTile* __restrict__ mtiles, const int4* __restrict__ runs,
-                       const short2* __restrict__ rowf, const short2* __restrict__ colf,
-                       double* __restrict__ partial, int* __restrict__ err) {
+                       int slot_cap, int acc_max, int window, const TcCta* __restrict__ ctas,
+                       const TcGroup* __restrict__ groups, const TcMTile* __restrict__ mtiles,
+                       const int4* __restrict__ runs, const short2* __restrict__ rowf,
+                       const short2* __restrict__ colf, double* __restrict__ partial, int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* s_d = base;                                       // kTcStages x stage_bytes (1024-aligned)
-    uint8_t* s_b = s_d + kTcStages * stage_bytes;              // [2 buffers][hi, lo] x bbuf_bytes
-    float* s_acc = (float*)(s_b + 4 * bbuf_bytes);             // [kTcAccMax cols][128 rows]
-    short2* s_rowf = (short2*)(s_acc + kTcAccMax * 128);       // [kTcMaxMT][128]
-    short2* s_colf = s_rowf + kTcMaxMT * 128;                  // [kTcMaxCols]
-    int4* s_runs = (int4*)(s_colf + kTcMaxCols);               // n0, nn, acc col, mtile
-    uint64_t* bars = (uint64_t*)(s_runs + kTcMaxRuns);
-    uint64_t* full = bars;                                     // [kTcStages]
-    uint64_t* empty = bars + kTcStages;                        // [kTcStages]
-    uint64_t* produced = bars + 2 * kTcStages;                 // [2]
-    uint64_t* mma_done = produced + 2;                         // [2]
-    uint64_t* acc_ready = mma_done + 2;
+    uint8_t* s_d = base;                                        // kTcStages x stage_bytes (1024-aligned)
+    uint8_t* s_b = s_d + kTcStages * stage_bytes;               // [slot][hi, lo] x bbuf_bytes
+    float* s_acc = (float*)(s_b + 2 * slot_cap * bbuf_bytes);   // [acc_max cols][128 rows]
+    short2* s_rowf = (short2*)(s_acc + (size_t)acc_max * 128);  // [kTcMaxMT][128]
+    short2* s_colf = s_rowf + kTcMaxMT * 128;                   // [kTcMaxCols]
+    TcMma* s_mma = (TcMma*)(s_colf + kTcMaxCols);               // [kTcMaxMma]
+    uint64_t* bars = (uint64_t*)(s_mma + kTcMaxMma);
+    uint64_t* full = bars;                                      // [kTcStages]
+    uint64_t* empty = full + kTcStages;                         // [kTcStages]
+    uint64_t* produced = empty + kTcStages;                     // [4]
+    uint64_t* mma_done = produced + 4;                          // [4]
+    uint64_t* acc_ready = mma_done + 4;
     uint64_t* acc_free = acc_ready + 1;
     uint64_t* drain = acc_free + 1;
     uint32_t* s_tmem = (uint32_t*)(drain + 1);
     volatile int* s_abort = (volatile int*)(s_tmem + 1);
-    int* s_meta = (int*)(s_tmem + 2);  // nmt, ncol, acc_cols, nruns, mt_run_off[4], mt_nrun[4]
+    int* s_meta = (int*)(s_tmem + 2);  // nmma, nslots, a0
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TcCta cta = ctas[blockIdx.x];
     const TcGroup grp = groups[cta.group];
     const int nch = (int)(cta.c1 - cta.c0);
+    const int nmt = grp.nmt, ncol = grp.ncol, acc_cols = grp.acc_cols;
 
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; s++) {
-            tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], kTcProducers / 32);
+        // TMEM columns: accumulators [0, acc_cols), then the A slots of nmt x 32 columns each
+        const int a0 = (acc_cols + 31) / 32 * 32;
+        int nslots = (512 - a0) / (nmt * 32);
+        nslots = nslots < slot_cap ? nslots : slot_cap;
+        nslots = nslots > 4 ? 4 : nslots;
+        for (int st = 0; st < kTcStages; st++) {
+            tc::mbar_init(&full[st], 1);
+            tc::mbar_init(&empty[st], kTcProducers / 32);
         }
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < 4; b++) {
             tc::mbar_init(&produced[b], kTcProducers / 32);
             tc::mbar_init(&mma_done[b], 1);
         }
@@ -108,25 +123,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc::mbar_init(drain, 1);
         tc::mbar_fence_init();
         *s_abort = 0;
-        int nr = 0;
-        for (int m = 0; m < grp.nmt; m++) {
+        int nm = 0;
+        for (int m = 0; m < nmt; m++) {
             const TcMTile mt = mtiles[grp.mt_off + m];
-            s_meta[4 + m] = nr;
-            s_meta[8 + m] = mt.nrun;
-            for (int r = 0; r < mt.nrun; r++) s_runs[nr++] = runs[mt.run_off + r];
+            for (int r = 0; r < mt.nrun; r++) {
+                const int4 run = runs[mt.run_off + r];  // n0, nn, acc col
+                const uint32_t idesc = tc::idesc_bf16(128, run.y);
+                for (int ks = 0; ks < kTcChunk / 16; ks++) {
+                    const uint32_t boff = (uint32_t)(run.x / 8) * kSBO + (uint32_t)ks * 2 * kLBO;
+                    const uint32_t acol = (uint32_t)(m * 32 + ks * 8);
+                    if (nm + 3 <= kTcMaxMma) {
+                        s_mma[nm++] = TcMma{(uint32_t)run.z, acol, boff, idesc | (ks == 0 ? 2u : 0u)};  // hi x hi
+                        s_mma[nm++] = TcMma{(uint32_t)run.z, acol, boff, idesc | 1u};                    // hi x lo
+                        s_mma[nm++] = TcMma{(uint32_t)run.z, acol + 16, boff, idesc};                   // lo x hi
+                    }
+                }
+            }
         }
-        s_meta[0] = grp.nmt;
-        s_meta[1] = grp.ncol;
-        s_meta[2] = grp.acc_cols;
-        s_meta[3] = nr;
+        s_meta[0] = nm;
+        s_meta[1] = nslots;
+        s_meta[2] = a0;
     }
     for (int i = tid; i < kTcMaxMT * 128; i += kTcThreads) {
         const int m = i >> 7;
-        s_rowf[i] = m < grp.nmt ? rowf[mtiles[grp.mt_off + m].row_off + (i & 127)] : make_short2(-1, -1);
+        s_rowf[i] = m < nmt ? rowf[mtiles[grp.mt_off + m].row_off + (i & 127)] : make_short2(-1, -1);
     }
-    for (int i = tid; i < kTcMaxCols; i += kTcThreads) s_colf[i] = i < grp.ncol ? colf[grp.col_off + i] : make_short2(-1, -1);
-    for (int i = tid; i < grp.acc_cols * 128; i += kTcThreads) s_acc[i] = 0.f;
-    if (warp == 8) {
+    for (int i = tid; i < kTcMaxCols; i += kTcThreads) s_colf[i] = i < ncol ? colf[grp.col_off + i] : make_short2(-1, -1);
+    for (int i = tid; i < acc_cols * 128; i += kTcThreads) s_acc[i] = 0.f;
+    if (warp == kTcProducers / 32) {
         tc::tmem_alloc(s_tmem, 512);
         tc::tmem_relinquish();
     }
@@ -134,154 +158,153 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *s_tmem;
-    const int nmt = s_meta[0], ncol = s_meta[1], acc_cols = s_meta[2];
+    const int nmma = s_meta[0], nslots = s_meta[1], a0 = s_meta[2];
     const uint32_t stage_tx = (uint32_t)nshell * kTcChunk * 4;
+    const uint32_t slot_cols = (uint32_t)(nmt * 32);
 
-    if (warp == 8) {
+    if (warp == kTcProducers / 32) {
         // ------------------------------------------------------------- control thread
         if (lane == 0 && nch > 0) {
             tc::prefetch_tensormap(&fmap);
-            long long last_issued[kTcStages];
-            for (int s = 0; s < kTcStages; s++) last_issued[s] = -1;
-            for (int j = 0; j < kTcStages && j < nch; j++) {
-                tc::mbar_arrive_expect_tx(&full[j], stage_tx);
-                tc::tma_load_2d(s_d + j * stage_bytes, &fmap, (int)((cta.c0 + j) * kTcChunk), 0, &full[j]);
-                last_issued[j] = j;
+            int issued = 0;
+            for (; issued < kTcStages && issued < nch; issued++) {
+                tc::mbar_arrive_expect_tx(&full[issued], stage_tx);
+                tc::tma_load_2d(s_d + issued * stage_bytes, &fmap, 0, (int)((cta.c0 + issued) * nshell), &full[issued]);
             }
+            const uint32_t desc_hi = (kSBO >> 4) | (1u << 14);  // stride byte offset, sm_100 descriptor version
             for (int i = 0; i < nch; i++) {
-                const int b = i & 1, w = i / window;
-                if (!tc::mbar_wait(&produced[b], (i >> 1) & 1, s_abort)) break;
-                if (i % window == 0 && w > 0 && !tc::mbar_wait(acc_free, (w - 1) & 1, s_abort)) break;
+                const int slot = i % nslots, w = i / window;
+                if (!tc::mbar_wait(&produced[slot], (uint32_t)((i / nslots) & 1), s_abort)) break;
+                if (i % window == 0 && w > 0 && !tc::mbar_wait(acc_free, (uint32_t)((w - 1) & 1), s_abort)) break;
                 tc::fence_after_sync();
-                const uint32_t bh = tc::smem_u32(s_b + (2 * b) * bbuf_bytes);
-                const uint32_t bl = tc::smem_u32(s_b + (2 * b + 1) * bbuf_bytes);
-                for (int m = 0; m < nmt; m++) {
-                    const uint32_t a0 = tmem + kTcABase + (uint32_t)((b * kTcMaxMT + m) * 32);
-                    const int r0 = s_meta[4 + m], nr = s_meta[8 + m];
-                    for (int r = r0; r < r0 + nr; r++) {
-                        const int4 run = s_runs[r];
-                        const uint32_t idesc = tc::idesc_bf16(128, run.y);
-                        const uint32_t d = tmem + (uint32_t)run.z;
-#pragma unroll
-                        for (int ks = 0; ks < kTcChunk / 16; ks++) {
-                            const uint32_t boff = (uint32_t)(run.x / 8) * kSBO + (uint32_t)ks * 2 * kLBO;
-                            const uint64_t dh = tc::smem_desc(bh + boff, kLBO, kSBO);
-                            const uint64_t dl = tc::smem_desc(bl + boff, kLBO, kSBO);
-                            const uint32_t ahi = a0 + ks * 8, alo = a0 + 16 + ks * 8;
-                            tc::mma_ts(d, ahi, dh, idesc, (i % window == 0 && ks == 0) ? 0u : 1u);
-                            tc::mma_ts(d, ahi, dl, idesc, 1u);
-                            tc::mma_ts(d, alo, dh, idesc, 1u);
-                        }
-                    }
+                const uint32_t abase = tmem + (uint32_t)a0 + (uint32_t)slot * slot_cols;
+                const uint32_t bh = tc::smem_u32(s_b + (2 * slot) * bbuf_bytes);
+                const uint32_t bl = tc::smem_u32(s_b + (2 * slot + 1) * bbuf_bytes);
+                const bool wstart = (i % window) == 0;
+                for (int e = 0; e < nmma; e++) {
+                    const TcMma mm = s_mma[e];
+                    const uint32_t baddr = ((mm.idesc_flags & 1u) ? bl : bh) + mm.b_off;
+                    const uint64_t desc = (uint64_t)(((baddr >> 4) & 0x3FFFu) | ((kLBO >> 4) << 16)) |
+                                          ((uint64_t)desc_hi << 32);
+                    const uint32_t acc = (wstart && (mm.idesc_flags & 2u)) ? 0u : 1u;
+                    tc::mma_ts(tmem + mm.d_col, abase + mm.a_col, desc, mm.idesc_flags & ~3u, acc);
                 }
-                tc::mma_commit(&mma_done[b]);
+                tc::mma_commit(&mma_done[slot]);
                 if (i % window == window - 1 || i == nch - 1) tc::mma_commit(acc_ready);
-                const int jn = i + kTcStages;
-                if (jn < nch) {
-                    const int s = i % kTcStages;
-                    if (!tc::mbar_wait(&empty[s], (i / kTcStages) & 1, s_abort)) break;
-                    tc::mbar_arrive_expect_tx(&full[s], stage_tx);
-                    tc::tma_load_2d(s_d + s * stage_bytes, &fmap, (int)((cta.c0 + jn) * kTcChunk), 0, &full[s]);
-                    last_issued[s] = jn;
+                if (issued < nch) {
+                    const int st = issued % kTcStages;
+                    // the stage held chunk issued - kTcStages, released by the producers before produced[]
+                    if (!tc::mbar_wait(&empty[st], (uint32_t)(((issued - kTcStages) / kTcStages) & 1), s_abort)) break;
+                    tc::mbar_arrive_expect_tx(&full[st], stage_tx);
+                    tc::tma_load_2d(s_d + st * stage_bytes, &fmap, 0, (int)((cta.c0 + issued) * nshell), &full[st]);
+                    issued++;
                 }
             }
             // drain: every MMA issued by this thread, and every TMA load it started
             tc::mma_commit(drain);
             volatile int no_abort = 0;
             tc::mbar_wait(drain, 0, &no_abort);
-            for (int s = 0; s < kTcStages; s++)
-                if (last_issued[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)((last_issued[s] / kTcStages) & 1), &no_abort);
+            for (int st = 0; st < kTcStages && st < issued; st++) {
+                const int last = st + kTcStages * ((issued - 1 - st) / kTcStages);
+                tc::mbar_wait(&full[st], (uint32_t)((last / kTcStages) & 1), &no_abort);
+            }
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------- producers
-        const int q = warp & 3, h = warp >> 2;
+        const int q = warp & 3, h = warp >> 2;  // lane quadrant, 8-cell slice of the chunk
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int row = 32 * q + lane;
+        short2 rf[kTcMaxMT];
+#pragma unroll
+        for (int m = 0; m < kTcMaxMT; m++) rf[m] = s_rowf[m * 128 + row];
         for (int i = 0; i < nch; i++) {
-            const int s = i % kTcStages, b = i & 1, w = i / window;
-            if (!tc::mbar_wait_warp(&full[s], (i / kTcStages) & 1, s_abort)) break;
-            if (i >= 2 && !tc::mbar_wait_warp(&mma_done[b], ((i >> 1) - 1) & 1, s_abort)) break;
-            const uint8_t* D = s_d + s * stage_bytes;
+            const int st = i % kTcStages, slot = i % nslots, w = i / window;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((i / kTcStages) & 1), s_abort)) break;
+            if (i >= nslots && !tc::mbar_wait_warp(&mma_done[slot], (uint32_t)((i / nslots - 1) & 1), s_abort)) break;
+            const uint8_t* D = s_d + st * stage_bytes;
+            // A operand first (the longer job): all loads of this lane's rows, then the products
+            float4 xa[kTcMaxMT][2], xb[kTcMaxMT][2];
+#pragma unroll
+            for (int m = 0; m < kTcMaxMT; m++) {
+                if (m < nmt && rf[m].x >= 0) {
+                    const float4* r1 = (const float4*)(D + rf[m].x * 128);
+                    xa[m][0] = r1[(2 * h) ^ (rf[m].x & 7)];
+                    xa[m][1] = r1[(2 * h + 1) ^ (rf[m].x & 7)];
+                    if (RA == 2) {
+                        const float4* r2 = (const float4*)(D + rf[m].y * 128);
+                        xb[m][0] = r2[(2 * h) ^ (rf[m].y & 7)];
+                        xb[m][1] = r2[(2 * h + 1) ^ (rf[m].y & 7)];
+                    }
+                } else {
+                    xa[m][0] = xa[m][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    xb[m][0] = xb[m][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            const uint32_t abase = tmem + lane_base + (uint32_t)a0 + (uint32_t)slot * slot_cols;
+#pragma unroll
+            for (int m = 0; m < kTcMaxMT; m++) {
+                if (m >= nmt) break;
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const float4 a = xa[m][j];
+                    if (RA == 2) {
+                        const float4 c = xb[m][j];
+                        tc::split2_prod(a.x, c.x, a.y, c.y, hi[2 * j], lo[2 * j]);
+                        tc::split2_prod(a.z, c.z, a.w, c.w, hi[2 * j + 1], lo[2 * j + 1]);
+                    } else {
+                        tc::split2(a.x, a.y, hi[2 * j], lo[2 * j]);
+                        tc::split2(a.z, a.w, hi[2 * j + 1], lo[2 * j + 1]);
+                    }
+                }
+                tc::tmem_st4(abase + (uint32_t)(m * 32 + h * 4), hi);
+                tc::tmem_st4(abase + (uint32_t)(m * 32 + 16 + h * 4), lo);
+            }
             // B operand: (column n, 8-cell group kg) -> one 16-byte core-matrix row of hi and of lo
-            uint8_t* Bh = s_b + (2 * b) * bbuf_bytes;
-            uint8_t* Bl = s_b + (2 * b + 1) * bbuf_bytes;
+            uint8_t* Bh = s_b + (2 * slot) * bbuf_bytes;
+            uint8_t* Bl = s_b + (2 * slot + 1) * bbuf_bytes;
             for (int it = tid; it < ncol * (kTcChunk / 8); it += kTcProducers) {
                 const int kg = it / ncol, n = it - (it / ncol) * ncol;
                 const short2 f = s_colf[n];
-                float v[8];
+                uint4 hi, lo;
                 if (f.x >= 0) {
                     const float4* r1 = (const float4*)(D + f.x * 128);
-                    float4 x0 = r1[(2 * kg) ^ (f.x & 7)], x1 = r1[(2 * kg + 1) ^ (f.x & 7)];
-                    v[0] = x0.x, v[1] = x0.y, v[2] = x0.z, v[3] = x0.w, v[4] = x1.x, v[5] = x1.y, v[6] = x1.z,
-                    v[7] = x1.w;
+                    const float4 x0 = r1[(2 * kg) ^ (f.x & 7)], x1 = r1[(2 * kg + 1) ^ (f.x & 7)];
                     if (CA == 2) {
                         const float4* r2 = (const float4*)(D + f.y * 128);
-                        float4 y0 = r2[(2 * kg) ^ (f.y & 7)], y1 = r2[(2 * kg + 1) ^ (f.y & 7)];
-                        float u[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-                        uint4 hi, lo;
-                        tc::split2_prod(v[0], u[0], v[1], u[1], hi.x, lo.x);
-                        tc::split2_prod(v[2], u[2], v[3], u[3], hi.y, lo.y);
-                        tc::split2_prod(v[4], u[4], v[5], u[5], hi.z, lo.z);
-                        tc::split2_prod(v[6], u[6], v[7], u[7], hi.w, lo.w);
-                        const uint32_t off = (uint32_t)(n / 8) * kSBO + (uint32_t)kg * kLBO + (uint32_t)(n % 8) * 16;
-                        *(uint4*)(Bh + off) = hi;
-                        *(uint4*)(Bl + off) = lo;
-                        continue;
+                        const float4 y0 = r2[(2 * kg) ^ (f.y & 7)], y1 = r2[(2 * kg + 1) ^ (f.y & 7)];
+                        tc::split2_prod(x0.x, y0.x, x0.y, y0.y, hi.x, lo.x);
+                        tc::split2_prod(x0.z, y0.z, x0.w, y0.w, hi.y, lo.y);
+                        tc::split2_prod(x1.x, y1.x, x1.y, y1.y, hi.z, lo.z);
+                        tc::split2_prod(x1.z, y1.z, x1.w, y1.w, hi.w, lo.w);
+                    } else {
+                        tc::split2(x0.x, x0.y, hi.x, lo.x);
+                        tc::split2(x0.z, x0.w, hi.y, lo.y);
+                        tc::split2(x1.x, x1.y, hi.z, lo.z);
+                        tc::split2(x1.z, x1.w, hi.w, lo.w);
                     }
                 } else {
-#pragma unroll
-                    for (int j = 0; j < 8; j++) v[j] = 0.f;
+                    hi = make_uint4(0u, 0u, 0u, 0u);
+                    lo = hi;
                 }
-                uint4 hi, lo;
-                tc::split2(v[0], v[1], hi.x, lo.x);
-                tc::split2(v[2], v[3], hi.y, lo.y);
-                tc::split2(v[4], v[5], hi.z, lo.z);
-                tc::split2(v[6], v[7], hi.w, lo.w);
                 const uint32_t off = (uint32_t)(n / 8) * kSBO + (uint32_t)kg * kLBO + (uint32_t)(n % 8) * 16;
                 *(uint4*)(Bh + off) = hi;
                 *(uint4*)(Bl + off) = lo;
-            }
-            // A operand: this lane's row, cells 16h .. 16h+15, for every M tile
-            for (int m = 0; m < nmt; m++) {
-                const short2 f = s_rowf[m * 128 + row];
-                uint32_t hi[8], lo[8];
-                if (f.x >= 0) {
-                    const float4* r1 = (const float4*)(D + f.x * 128);
-                    const float4* r2 = (const float4*)(D + (RA == 2 ? f.y : f.x) * 128);
-#pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const float4 a = r1[(4 * h + j) ^ (f.x & 7)];
-                        if (RA == 2) {
-                            const float4 c = r2[(4 * h + j) ^ (f.y & 7)];
-                            tc::split2_prod(a.x, c.x, a.y, c.y, hi[2 * j], lo[2 * j]);
-                            tc::split2_prod(a.z, c.z, a.w, c.w, hi[2 * j + 1], lo[2 * j + 1]);
-                        } else {
-                            tc::split2(a.x, a.y, hi[2 * j], lo[2 * j]);
-                            tc::split2(a.z, a.w, hi[2 * j + 1], lo[2 * j + 1]);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; j++) hi[j] = lo[j] = 0u;
-                }
-                const uint32_t a0 = tmem + lane_base + kTcABase + (uint32_t)((b * kTcMaxMT + m) * 32);
-                tc::tmem_st8(a0 + h * 8, hi);
-                tc::tmem_st8(a0 + 16 + h * 8, lo);
             }
             tc::fence_proxy_async_smem();
             tc::tmem_st_wait();
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) {
-                tc::mbar_arrive(&empty[s]);
-                tc::mbar_arrive(&produced[b]);
+                tc::mbar_arrive(&empty[st]);
+                tc::mbar_arrive(&produced[slot]);
             }
             // drain the accumulators at the end of a window
             if (i % window == window - 1 || i == nch - 1) {
-                if (!tc::mbar_wait_warp(acc_ready, w & 1, s_abort)) break;
+                if (!tc::mbar_wait_warp(acc_ready, (uint32_t)(w & 1), s_abort)) break;
                 tc::fence_after_sync();
-                for (int g = h; g < acc_cols / 16; g += 2) {
+                for (int g = h; g < acc_cols / 16; g += 4) {
                     uint32_t v[16];
                     tc::tmem_ld16(tmem + lane_base + (uint32_t)(g * 16), v);
                     tc::tmem_ld_wait();
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     double* out = partial + (size_t)blockIdx.x * (kTcAccMax * 128);
     for (int i = tid; i < acc_cols * 128; i += kTcThreads) out[i] = (double)s_acc[i];
-    if (warp == 8) {
+    if (warp == kTcProducers / 32) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
     }
@@ -400,7 +423,8 @@ struct TcState {
     int ngroups = 0;
     int nshell = 0;
     int stage_bytes = 0, bbuf_bytes = 0, smem_bytes = 0;
-    int window = 16;
+    int window = 64;
+    int slot_cap = 2, acc_max = 256;
     int ra = 2, ca = 1;
     void *d_ctas = nullptr, *d_groups = nullptr, *d_mtiles = nullptr, *d_runs = nullptr, *d_rowf = nullptr,
          *d_colf = nullptr, *d_binmap = nullptr;
@@ -422,9 +446,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-static size_t tc_smem_bytes(int stage_bytes, int bbuf_bytes) {
-    return 1024 + (size_t)kTcStages * stage_bytes + 4 * (size_t)bbuf_bytes + (size_t)kTcAccMax * 128 * 4 +
-           kTcMaxMT * 128 * 4 + kTcMaxCols * 4 + kTcMaxRuns * 16 + 16 * 8 + 64 + 64;
+static size_t tc_smem_bytes(int stage_bytes, int bbuf_bytes, int slots, int acc_max) {
+    return 1024 + (size_t)kTcStages * stage_bytes + 2 * (size_t)slots * bbuf_bytes + (size_t)acc_max * 128 * 4 +
+           kTcMaxMT * 128 * 4 + kTcMaxCols * 4 + kTcMaxMma * sizeof(TcMma) + (2 * kTcStages + 11) * 8 + 64;
 }
 
 // Build the groups: rows sorted by column span, 128-row M tiles, 16-column blocks.
@@ -638,11 +662,12 @@ poly_status ps_tc_prepare(PsPlan* p) {
     if ((s = ps_alloc(p, (void**)&t->d_partial, t->ctas.size() * (size_t)kTcAccMax * 128 * 8))) return s;
     if ((s = ps_alloc(p, (void**)&t->d_err, 16))) return s;
     if (cudaMemset(t->d_err, 0, 16)) return POLY_ERR_CUDA;
-    // tensor map over the fields [nshell][ncell] fp32: box 32 cells x all shells, 128-byte swizzle
+    // tensor map over the cell-tiled fields [ncell/32 * nshell rows][32 cells] fp32: one box = one 32-cell
+    // chunk of every shell (a contiguous block), 128-byte swizzle
     auto enc = get_encode();
     if (!enc) return POLY_ERR_UNSUPPORTED;
-    cuuint64_t gdim[2] = {(cuuint64_t)ncell, (cuuint64_t)p->nshell};
-    cuuint64_t gstride[1] = {(cuuint64_t)ncell * 4};
+    cuuint64_t gdim[2] = {(cuuint64_t)kTcChunk, (cuuint64_t)(ncell / kTcChunk) * (cuuint64_t)p->nshell};
+    cuuint64_t gstride[1] = {(cuuint64_t)kTcChunk * 4};
     cuuint32_t box[2] = {(cuuint32_t)kTcChunk, (cuuint32_t)p->nshell};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&t->fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->d_fields, gdim, gstride, box, estr,
@@ -650,10 +675,20 @@ poly_status ps_tc_prepare(PsPlan* p) {
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return POLY_ERR_CUDA;
     t->stage_bytes = (p->nshell * 128 + 1023) / 1024 * 1024;
-    int maxcol = 16;
-    for (auto& g : groups) maxcol = std::max(maxcol, g.ncol);
+    int maxcol = 16, maxacc = 16;
+    for (auto& g : groups) {
+        maxcol = std::max(maxcol, g.ncol);
+        maxacc = std::max(maxacc, g.acc_cols);
+        int nm = 0;
+        for (int m = 0; m < g.nmt; m++) nm += 6 * mtiles[g.mt_off + m].nrun;
+        if (nm > kTcMaxMma) return POLY_ERR_UNSUPPORTED;
+    }
     t->bbuf_bytes = maxcol * kTcChunk * 2;
-    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes);
+    t->acc_max = maxacc;
+    t->slot_cap = 4;  // A/B slots: as many as shared memory allows (the kernel also bounds them by TMEM)
+    while (t->slot_cap > 2 && tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc) > 227 * 1024)
+        t->slot_cap--;
+    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc);
     if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
     const char* w = getenv("POLY_TC_WINDOW");
     if (w && atoi(w) > 0) t->window = atoi(w);
@@ -668,7 +703,7 @@ poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {
         cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t->smem_bytes);
         if (e2) return e2;
         kern<<<(unsigned)t->ctas.size(), kTcThreads, t->smem_bytes, st>>>(
-            t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->window, (const TcCta*)t->d_ctas,
+            t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->slot_cap, t->acc_max, t->window, (const TcCta*)t->d_ctas,
             (const TcGroup*)t->d_groups, (const TcMTile*)t->d_mtiles, (const int4*)t->d_runs,
             (const short2*)t->d_rowf, (const short2*)t->d_colf, t->d_partial, t->d_err);
         return cudaGetLastError();

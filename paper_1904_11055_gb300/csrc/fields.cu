@@ -9,10 +9,10 @@ cudaError_t ps_forward_f64(int n, const void* delta, int K, const void* tw_fwd, 
                            cudaStream_t st);
 cudaError_t ps_inverse_f32(int n, int unity, const void* fhat, const void* lines, const int* line_off, int s0, int ns,
                            int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride, void* spill,
-                           void* xpre, int max_lines, cudaStream_t st);
+                           void* xpre, int max_lines, int tile_ns, cudaStream_t st);
 cudaError_t ps_inverse_f64(int n, int unity, const void* fhat, const void* lines, const int* line_off, int s0, int ns,
                            int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride, void* spill,
-                           void* xpre, int max_lines, cudaStream_t st);
+                           void* xpre, int max_lines, int tile_ns, cudaStream_t st);
 size_t ps_plane_smem_f32(int n, int K, int spill);
 size_t ps_plane_smem_f64(int n, int K, int spill);
 
@@ -47,9 +47,9 @@ cudaError_t ps_forward(int n, int is_double, const void* delta, int K, const voi
 
 cudaError_t ps_inverse(int n, int is_double, int unity, const void* fhat, const void* lines, const int* line_off, int s0,
                        int ns, int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride, void* spill,
-                       void* xpre, int max_lines, cudaStream_t st) {
+                       void* xpre, int max_lines, int tile_ns, cudaStream_t st) {
     return is_double ? ps_inverse_f64(n, unity, fhat, lines, line_off, s0, ns, K, x0, nx, tw_inv, out, out_stride,
-                                      spill, xpre, max_lines, st)
+                                      spill, xpre, max_lines, tile_ns, st)
                      : ps_inverse_f32(n, unity, fhat, lines, line_off, s0, ns, K, x0, nx, tw_inv, out, out_stride,
-                                      spill, xpre, max_lines, st);
+                                      spill, xpre, max_lines, tile_ns, st);
 }

@@ -217,28 +217,41 @@ struct HalfPairReader {  // Z(kz) built from rows y1, y2 of Hb (kz lines)
     }
 };
 
+// Output layout of the shell fields: natural [s][x][y][z] (tile_ns == 0), or
+// cell-tiled [cell / 32][s][cell % 32] over tile_ns shells, so that one 32-cell
+// chunk of every shell is one contiguous block (what the contractions stream).
 template <typename T>
 struct RowPairWriter {  // final stage: real part -> row y1, imaginary part -> row y2
-    T* plane;
-    int y0, n;
+    T* plane;       // natural layout: this plane's first cell
+    T* base;        // tiled layout: the whole field array
+    int y0, n, x, s, tile_ns;
+    PS_DEV size_t at(int y, int z) const {
+        const size_t cell = ((size_t)x * n + y) * n + z;
+        return (cell >> 5) * (size_t)tile_ns * 32 + (size_t)s * 32 + (cell & 31);
+    }
     PS_DEV void write(int l, int pos, Cx<T> v) const {
         const int y1 = y0 + 2 * l, y2 = y1 + 1;
-        plane[(size_t)y1 * n + pos] = v.re;
-        if (y2 < n) plane[(size_t)y2 * n + pos] = v.im;
+        if (tile_ns > 0) {
+            base[at(y1, pos)] = v.re;
+            if (y2 < n) base[at(y2, pos)] = v.im;
+        } else {
+            plane[(size_t)y1 * n + pos] = v.re;
+            if (y2 < n) plane[(size_t)y2 * n + pos] = v.im;
+        }
     }
 };
 
-template <typename T, int N, bool SPILL, bool UNITY, bool XPRE>
-__global__ void __launch_bounds__(kPlaneThreads) inv_plane_kernel(
+template <typename T, int N, bool SPILL, bool UNITY, bool XPRE, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) inv_plane_kernel(
     const Cx<T>* __restrict__ fhat, const short4* __restrict__ lines, const int* __restrict__ line_off, int s0,
     int K, int x0, const Cx<double>* __restrict__ g_tw, T* __restrict__ out, size_t out_shell_stride,
-    Cx<T>* __restrict__ spill, const Cx<T>* __restrict__ xpre) {
+    Cx<T>* __restrict__ spill, const Cx<T>* __restrict__ xpre, int tile_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ls = line_stride<T>(N);
     constexpr int LPW = fft_lpw(N);
     Cx<T>* s_tw = reinterpret_cast<Cx<T>*>(smem_raw);
     Cx<T>* s_z = s_tw + N;
-    Cx<T>* s_h = s_z + (size_t)kPlaneWarps * LPW * ls;
+    Cx<T>* s_h = s_z + (size_t)WARPS * LPW * ls;
     const int x = x0 + blockIdx.x;
     const int s = s0 + blockIdx.y;
     Cx<T>* Hb = SPILL ? spill + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (size_t)(K + 1) * ls : s_h;
@@ -299,7 +312,7 @@ __global__ void __launch_bounds__(kPlaneThreads) inv_plane_kernel(
     }
     __syncthreads();
     // DFT along y of the K+1 kz lines
-    for (int g = warp * LPW; g <= K; g += kPlaneWarps * LPW) {
+    for (int g = warp * LPW; g <= K; g += WARPS * LPW) {
         SmemLines<T> hb{Hb + (size_t)g * ls, ls};
         warp_fft_inplace<T, N, +1>(hb, min(LPW, K + 1 - g), s_tw, lane);
     }
@@ -308,10 +321,10 @@ __global__ void __launch_bounds__(kPlaneThreads) inv_plane_kernel(
     T* plane = out + (size_t)blockIdx.y * out_shell_stride + (size_t)blockIdx.x * N * N;
     SmemLines<T> zb{s_z + (size_t)warp * LPW * ls, ls};
     const int npairs = (N + 1) / 2;
-    for (int p0 = warp * LPW; p0 < npairs; p0 += kPlaneWarps * LPW) {
+    for (int p0 = warp * LPW; p0 < npairs; p0 += WARPS * LPW) {
         const int nl = min(LPW, npairs - p0);
         HalfPairReader<T> rd{Hb, ls, K, N, 2 * p0};
-        RowPairWriter<T> wr{plane, 2 * p0, N};
+        RowPairWriter<T> wr{plane, out, 2 * p0, N, x, s, tile_ns};
         warp_fft<T, N, +1>(zb, nl, s_tw, lane, rd, wr);
     }
 }
@@ -320,9 +333,9 @@ __global__ void __launch_bounds__(kPlaneThreads) inv_plane_kernel(
 // host launchers
 // ------------------------------------------------------------------------
 template <typename T, int N>
-static size_t plane_smem_n(int K, bool spill) {
+static size_t plane_smem_n(int K, bool spill, int warps = kPlaneWarps) {
     const int ls = line_stride<T>(N);
-    size_t e = N + (size_t)kPlaneWarps * fft_lpw(N) * ls + (spill ? 0 : (size_t)(K + 1) * ls);
+    size_t e = N + (size_t)warps * fft_lpw(N) * ls + (spill ? 0 : (size_t)(K + 1) * ls);
     return e * sizeof(Cx<T>);
 }
 
@@ -361,7 +374,7 @@ static cudaError_t forward_n(const T* delta, int K, const Cx<double>* tw_fwd, Cx
 template <typename T, int N, bool UNITY>
 static cudaError_t inverse_n(const Cx<T>* fhat, const short4* lines, const int* line_off, int s0, int ns, int K,
                              int x0, int nx, const Cx<double>* tw_inv, T* out, size_t out_stride, Cx<T>* spill,
-                             Cx<T>* xpre, int max_lines, cudaStream_t st) {
+                             Cx<T>* xpre, int max_lines, int tile_ns, cudaStream_t st) {
     bool spill_on = plane_smem_n<T, N>(K, false) > kMaxSmem;
     if (spill_on && !spill) return cudaErrorInvalidValue;
     size_t sm = plane_smem_n<T, N>(K, spill_on);
@@ -375,17 +388,24 @@ static cudaError_t inverse_n(const Cx<T>* fhat, const short4* lines, const int* 
         kx<<<dim3((max_lines + 31) / 32, ns), 256, smx, st>>>(fhat, lines, line_off, s0, K, tw_inv, xpre);
         if ((e = cudaGetLastError())) return e;
     }
-#define PS_LAUNCH_INV(SP, PRE)                                                                                   \
+#define PS_LAUNCH_INV(SP, PRE, W)                                                                                \
     {                                                                                                             \
-        auto k = inv_plane_kernel<T, N, SP, UNITY, PRE>;                                                          \
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;        \
-        k<<<grid, kPlaneThreads, sm, st>>>(fhat, lines, line_off, s0, K, x0, tw_inv, out, out_stride,             \
-                                           SP ? spill : nullptr, xpre);                                           \
+        auto k = inv_plane_kernel<T, N, SP, UNITY, PRE, W>;                                                       \
+        const size_t smw = plane_smem_n<T, N>(K, SP, W);                                                          \
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw))) return e;       \
+        k<<<grid, W * 32, smw, st>>>(fhat, lines, line_off, s0, K, x0, tw_inv, out, out_stride,                   \
+                                     SP ? spill : nullptr, xpre, tile_ns);                                        \
     }
+    // 16 warps per block for FP32 when the plane still fits in shared memory (latency hiding), else 8
+    const bool wide = sizeof(T) == 4 && !spill_on && plane_smem_n<T, N>(K, false, 16) <= kMaxSmem;
     if (spill_on) {
-        if (pre) PS_LAUNCH_INV(true, true) else PS_LAUNCH_INV(true, false)
+        if (pre) PS_LAUNCH_INV(true, true, 8) else PS_LAUNCH_INV(true, false, 8)
+    } else if (wide) {
+        if constexpr (sizeof(T) == 4) {
+            if (pre) PS_LAUNCH_INV(false, true, 16) else PS_LAUNCH_INV(false, false, 16)
+        }
     } else {
-        if (pre) PS_LAUNCH_INV(false, true) else PS_LAUNCH_INV(false, false)
+        if (pre) PS_LAUNCH_INV(false, true, 8) else PS_LAUNCH_INV(false, false, 8)
     }
 #undef PS_LAUNCH_INV
     return cudaGetLastError();

@@ -14,9 +14,11 @@ cudaError_t ps_forward(int n, int is_double, const void* delta, int K, const voi
 // shells s0..s0+ns-1, planes x0..x0+nx-1 -> out[(s-s0)*out_stride + (x-x0)*N*N + y*N + z].
 // xpre != NULL (and not unity): first run the x pass into xpre (sum over shells of lines * N complex values;
 // max_lines = the largest line count of the shells), then scatter; otherwise gather along x in the plane kernel.
+// tile_ns > 0: write the cell-tiled layout out[(cell/32) * tile_ns * 32 + s * 32 + cell % 32] (absolute shell s,
+// x0 must be 0) instead of the natural one.
 cudaError_t ps_inverse(int n, int is_double, int unity, const void* fhat, const void* lines, const int* line_off,
                        int s0, int ns, int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride,
-                       void* spill, void* xpre, int max_lines, cudaStream_t st);
+                       void* spill, void* xpre, int max_lines, int tile_ns, cudaStream_t st);
 
 // ---- contract_cc.cu -----------------------------------------------------------
 // One GEMM tile of the CUDA-core contraction: up to 64 rows x 64 cols, each row
@@ -31,8 +33,9 @@ constexpr int kCcTM = 64, kCcTN = 64, kCcMaxFields = 128;
 inline int ps_cc_chunk(int is_double) { return is_double ? 16 : 32; }
 
 // partial[(split * ntiles + tile) * 64 * 64 + r * 64 + c] = sum over the split's cells
+// fields: natural [s][cell] with stride field_stride (tile_ns == 0) or cell-tiled over tile_ns shells
 cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
-                           int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
+                           int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
                            const short2* rowf, const short2* colf, int nsplit, int64_t chunks_per_split,
                            double* partial, cudaStream_t st);
 // S[b] = sum_split partial[split * slot_stride + slot[b]]

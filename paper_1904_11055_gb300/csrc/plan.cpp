@@ -305,7 +305,7 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
         for (int s0 = 0; s0 < p->nshell && !rc; s0 += sb) {
             const int ns = std::min(sb, p->nshell - s0);
             if ((e = ps_inverse(N, 1, 1, nullptr, p->d_lines, p->d_line_off, s0, ns, p->K, 0, h + 1, p->d_tw_inv,
-                                d_planes, plane_elems, d_spill, nullptr, 0, st))) {
+                                d_planes, plane_elems, d_spill, nullptr, 0, 0, st))) {
                 rc = cuda_error(e, "counting fields");
                 break;
             }
@@ -316,7 +316,7 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
             }
         }
         if (rc) break;
-        if ((e = ps_contract_cc(1, 1, 0, d_iota, (size_t)nw, nw, d_wgt, (const PsTile*)p->d_cc_tiles,
+        if ((e = ps_contract_cc(1, 1, 0, d_iota, (size_t)nw, 0, nw, d_wgt, (const PsTile*)p->d_cc_tiles,
                                 (int)t.tiles.size(), (const int*)p->d_cc_field_ids, (const short2*)p->d_cc_rowf,
                                 (const short2*)p->d_cc_colf, nsplit, cps, (double*)d_part, st)) ||
             (e = ps_reduce_slots((double*)d_part, nsplit, slot_stride, (const int64_t*)p->d_cc_slot, p->nbins,
@@ -502,7 +502,7 @@ poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st) {
     if (!ps_xpre_fits(p, 0, p->nshell)) return set_error(POLY_ERR_ARG, "x-pass buffer too small");
     if ((e = ps_inverse(p->N, p->is_double, 0, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, 0, p->N,
                         p->d_tw_inv, p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, p->d_xpre,
-                        p->max_lines, st)))
+                        p->max_lines, p->nshell, st)))
         return cuda_error(e, "shell fields");
     p->launches += 2;  // x pass + plane kernel
     mark(p, 2, st);
@@ -513,7 +513,7 @@ poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st) {
     cudaError_t e;
     if (p->prec == POLY_SPLIT_BF16 && !absval) return ps_tc_sums(p, st);
     const size_t n3 = (size_t)p->N * p->N * p->N;
-    if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->d_fields, n3, (int64_t)n3, nullptr,
+    if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->d_fields, n3, p->nshell, (int64_t)n3, nullptr,
                             (const PsTile*)p->d_cc_tiles, (int)p->cc.tiles.size(), (const int*)p->d_cc_field_ids,
                             (const short2*)p->d_cc_rowf, (const short2*)p->d_cc_colf, p->cc_nsplit, p->cc_cps,
                             p->d_partial, st)))
