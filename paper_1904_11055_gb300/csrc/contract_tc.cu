@@ -10,12 +10,19 @@
 // (round-to-nearest adds), and the per-block sums are reduced in FP64 across
 // blocks in a fixed order.
 //
-// Block layout: 16 producer warps + 1 control warp.  The control thread streams
-// 32-cell chunks of all shell fields (one contiguous block of the cell-tiled
-// field layout) into shared memory with TMA (128-byte swizzle) and issues the
-// MMAs; the producers write the pair products of their TMEM lanes (A operand,
-// M = 128 rows per tile) with tcgen05.st and the column factors (B operand)
-// into shared memory in the K-major core-matrix layout.
+// Block layout: 16 producer warps in two teams, 4 issuer warps, 1 load warp.
+// The load warp streams 32-cell chunks of all shell fields (one contiguous block
+// of the cell-tiled field layout) into shared memory with TMA (128-byte swizzle).
+// Team t produces chunks t, t + 2, ... into A/B slot t, so that one team's
+// barrier waits overlap the other team's work.  Producer warp w of a team owns
+// TMEM lane quadrant w % 4 of M tiles 2 (w / 4) and 2 (w / 4) + 1: each lane forms
+// the 32 products of its row in each of the two tiles and writes their hi and lo
+// parts with 16-column tcgen05.st.  The rows of a warp are a block of 8
+// consecutive k1 x 4 consecutive k2, so its shared-memory reads of the factors
+// touch at most 12 distinct rows of the chunk (broadcast loads).  The team then
+// writes the column factors (B operand) into shared memory in the K-major
+// core-matrix layout.  Issuer warp m issues the MMAs of M tile m (operands in
+// registers; one elected lane issues and commits).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -35,14 +42,17 @@
 namespace ps {
 
 constexpr int kTcChunk = 32;         // cells per chunk (K of one pipeline step)
-constexpr int kTcStages = 6;         // TMA stages
-constexpr int kTcProducers = 512;    // 16 warps: 4 per TMEM lane quadrant, each owning 8 cells of a chunk
-constexpr int kTcThreads = kTcProducers + 32;
+constexpr int kTcStages = 6;         // TMA stages (even: each team cycles through its own three)
 constexpr int kTcMaxMT = 4;          // M tiles per block
+constexpr int kTcTeamWarps = 8;      // producer warps per team: 4 lane quadrants x 2 pairs of M tiles
+constexpr int kTcProducers = 2 * kTcTeamWarps * 32;
+constexpr int kTcIssuers = kTcMaxMT;  // one MMA-issuing warp per M tile
+constexpr int kTcThreads = kTcProducers + 32 * kTcIssuers + 32;  // + the load warp
 constexpr int kTcAccMax = 256;       // accumulator columns per block
-constexpr int kTcABase = 256;        // first TMEM column of the A slots
-constexpr int kTcMaxRuns = 64;       // N runs per block
+constexpr int kTcABase = 256;        // first TMEM column of the A operand in the self-test
+constexpr int kTcMaxRunsMt = 4;      // N runs per M tile
 constexpr int kTcMaxCols = 256;      // local B columns per block
+constexpr int kTcRowBlock1 = 8, kTcRowBlock2 = 4;  // pair rows of one producer warp: 8 k1 x 4 k2
 constexpr uint32_t kLBO = 128, kSBO = 512;  // B layout: K-adjacent core matrices, 8-row groups (K = 32)
 
 struct TcMTile {
@@ -62,95 +72,96 @@ struct TcCta {  // one block: a group and a chunk range
     long long c0, c1;
 };
 
-// ---------------------------------------------------------------------------------
-// One MMA of a chunk, precomputed per block: accumulator column, A column within
-// the slot, B byte offset within the slot's buffer, instruction descriptor, and
-// flags (bit 0: B = lo part, bit 1: first product of a K-step pair (resets at a window start)).
-struct TcMma {
-    uint32_t d_col, a_col, b_off, idesc_flags;
+// Window bookkeeping without divisions: the accumulators are drained after the
+// last chunk of each window of `window` chunks and after the block's last chunk.
+struct TcWindow {
+    int end, index;  // last chunk of the current window, window number
+    __device__ TcWindow(int i0, int window) : end((i0 / window + 1) * window - 1), index(i0 / window) {}
+    __device__ void advance_to(int i, int window) {
+        while (i > end) {
+            end += window;
+            index++;
+        }
+    }
 };
-constexpr int kTcMaxMma = 256;
+
+template <int RA>
+__device__ __forceinline__ void tc_row_products(const uint8_t* D, int k1, int k2, uint32_t* hi, uint32_t* lo) {
+    // the 32 products of one row for a chunk; column j holds cells 2j, 2j+1
+    const float4* r1 = (const float4*)(D + k1 * 128);
+    const float4* r2 = (const float4*)(D + k2 * 128);
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const float4 x = r1[c ^ (k1 & 7)];
+        if (RA == 2) {
+            const float4 y = r2[c ^ (k2 & 7)];
+            tc::split2_prod(x.x, y.x, x.y, y.y, hi[2 * c], lo[2 * c]);
+            tc::split2_prod(x.z, y.z, x.w, y.w, hi[2 * c + 1], lo[2 * c + 1]);
+        } else {
+            tc::split2(x.x, x.y, hi[2 * c], lo[2 * c]);
+            tc::split2(x.z, x.w, hi[2 * c + 1], lo[2 * c + 1]);
+        }
+    }
+}
 
 template <int RA, int CA>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_contract_kernel(const __grid_constant__ CUtensorMap fmap, int nshell, int stage_bytes, int bbuf_bytes,
-                       int slot_cap, int acc_max, int window, const TcCta* __restrict__ ctas,
-                       const TcGroup* __restrict__ groups, const TcMTile* __restrict__ mtiles,
-                       const int4* __restrict__ runs, const short2* __restrict__ rowf,
-                       const short2* __restrict__ colf, double* __restrict__ partial, int* __restrict__ err) {
+                       int acc_max, int window, const TcCta* __restrict__ ctas, const TcGroup* __restrict__ groups,
+                       const TcMTile* __restrict__ mtiles, const int4* __restrict__ runs,
+                       const short2* __restrict__ rowf, const short2* __restrict__ colf, double* __restrict__ partial,
+                       int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* s_d = base;                                        // kTcStages x stage_bytes (1024-aligned)
     uint8_t* s_b = s_d + kTcStages * stage_bytes;               // [slot][hi, lo] x bbuf_bytes
-    float* s_acc = (float*)(s_b + 2 * slot_cap * bbuf_bytes);   // [acc_max cols][128 rows]
+    float* s_acc = (float*)(s_b + 4 * bbuf_bytes);              // [acc_max cols][128 rows]
     short2* s_rowf = (short2*)(s_acc + (size_t)acc_max * 128);  // [kTcMaxMT][128]
     short2* s_colf = s_rowf + kTcMaxMT * 128;                   // [kTcMaxCols]
-    TcMma* s_mma = (TcMma*)(s_colf + kTcMaxCols);               // [kTcMaxMma]
-    uint64_t* bars = (uint64_t*)(s_mma + kTcMaxMma);
+    uint64_t* bars = (uint64_t*)(s_colf + kTcMaxCols);
     uint64_t* full = bars;                                      // [kTcStages]
     uint64_t* empty = full + kTcStages;                         // [kTcStages]
-    uint64_t* produced = empty + kTcStages;                     // [4]
-    uint64_t* mma_done = produced + 4;                          // [4]
-    uint64_t* acc_ready = mma_done + 4;
+    uint64_t* produced = empty + kTcStages;                     // [2]
+    uint64_t* mma_done = produced + 2;                          // [2]
+    uint64_t* acc_ready = mma_done + 2;
     uint64_t* acc_free = acc_ready + 1;
     uint64_t* drain = acc_free + 1;
     uint32_t* s_tmem = (uint32_t*)(drain + 1);
     volatile int* s_abort = (volatile int*)(s_tmem + 1);
-    int* s_meta = (int*)(s_tmem + 2);  // nmma, nslots, a0
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TcCta cta = ctas[blockIdx.x];
     const TcGroup grp = groups[cta.group];
     const int nch = (int)(cta.c1 - cta.c0);
     const int nmt = grp.nmt, ncol = grp.ncol, acc_cols = grp.acc_cols;
+    constexpr int kProdWarps = kTcProducers / 32;
+    constexpr int kLoadWarp = kProdWarps + kTcIssuers;
+    // TMEM columns: accumulators [0, a0), then slot t of team t: nmt x 32 columns (hi 16 + lo 16 per M tile)
+    const int a0 = (acc_cols + 31) / 32 * 32;
+    const uint32_t slot_cols = (uint32_t)(nmt * 32);
 
     if (tid == 0) {
-        // TMEM columns: accumulators [0, acc_cols), then the A slots of nmt x 32 columns each
-        const int a0 = (acc_cols + 31) / 32 * 32;
-        int nslots = (512 - a0) / (nmt * 32);
-        nslots = nslots < slot_cap ? nslots : slot_cap;
-        nslots = nslots > 4 ? 4 : nslots;
         for (int st = 0; st < kTcStages; st++) {
             tc::mbar_init(&full[st], 1);
-            tc::mbar_init(&empty[st], kTcProducers / 32);
+            tc::mbar_init(&empty[st], kTcTeamWarps);
         }
-        for (int b = 0; b < 4; b++) {
-            tc::mbar_init(&produced[b], kTcProducers / 32);
-            tc::mbar_init(&mma_done[b], 1);
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&produced[b], kTcTeamWarps);
+            tc::mbar_init(&mma_done[b], nmt);  // one commit per issuer
         }
-        tc::mbar_init(acc_ready, 1);
-        tc::mbar_init(acc_free, kTcProducers / 32);
-        tc::mbar_init(drain, 1);
+        tc::mbar_init(acc_ready, nmt);
+        tc::mbar_init(acc_free, kTcTeamWarps);  // the team that owns a window's last chunk drains it
+        tc::mbar_init(drain, nmt);
         tc::mbar_fence_init();
         *s_abort = 0;
-        int nm = 0;
-        for (int m = 0; m < nmt; m++) {
-            const TcMTile mt = mtiles[grp.mt_off + m];
-            for (int r = 0; r < mt.nrun; r++) {
-                const int4 run = runs[mt.run_off + r];  // n0, nn, acc col
-                const uint32_t idesc = tc::idesc_bf16(128, run.y);
-                for (int ks = 0; ks < kTcChunk / 16; ks++) {
-                    const uint32_t boff = (uint32_t)(run.x / 8) * kSBO + (uint32_t)ks * 2 * kLBO;
-                    const uint32_t acol = (uint32_t)(m * 32 + ks * 8);
-                    if (nm + 3 <= kTcMaxMma) {
-                        s_mma[nm++] = TcMma{(uint32_t)run.z, acol, boff, idesc | (ks == 0 ? 2u : 0u)};  // hi x hi
-                        s_mma[nm++] = TcMma{(uint32_t)run.z, acol, boff, idesc | 1u};                    // hi x lo
-                        s_mma[nm++] = TcMma{(uint32_t)run.z, acol + 16, boff, idesc};                   // lo x hi
-                    }
-                }
-            }
-        }
-        s_meta[0] = nm;
-        s_meta[1] = nslots;
-        s_meta[2] = a0;
     }
     for (int i = tid; i < kTcMaxMT * 128; i += kTcThreads) {
         const int m = i >> 7;
-        s_rowf[i] = m < nmt ? rowf[mtiles[grp.mt_off + m].row_off + (i & 127)] : make_short2(-1, -1);
+        s_rowf[i] = m < nmt ? rowf[mtiles[grp.mt_off + m].row_off + (i & 127)] : make_short2(0, 0);
     }
     for (int i = tid; i < kTcMaxCols; i += kTcThreads) s_colf[i] = i < ncol ? colf[grp.col_off + i] : make_short2(-1, -1);
     for (int i = tid; i < acc_cols * 128; i += kTcThreads) s_acc[i] = 0.f;
-    if (warp == kTcProducers / 32) {
+    if (warp == kProdWarps) {
         tc::tmem_alloc(s_tmem, 512);
         tc::tmem_relinquish();
     }
@@ -158,122 +169,148 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *s_tmem;
-    const int nmma = s_meta[0], nslots = s_meta[1], a0 = s_meta[2];
     const uint32_t stage_tx = (uint32_t)nshell * kTcChunk * 4;
-    const uint32_t slot_cols = (uint32_t)(nmt * 32);
 
-    if (warp == kTcProducers / 32) {
-        // ------------------------------------------------------------- control thread
-        if (lane == 0 && nch > 0) {
+    if (warp == kLoadWarp) {
+        // ------------------------------------------------------------- TMA loads
+        const bool el = tc::elect_one();
+        const int pre = kTcStages < nch ? kTcStages : nch;
+        if (el && nch > 0) {
             tc::prefetch_tensormap(&fmap);
-            int issued = 0;
-            for (; issued < kTcStages && issued < nch; issued++) {
-                tc::mbar_arrive_expect_tx(&full[issued], stage_tx);
-                tc::tma_load_2d(s_d + issued * stage_bytes, &fmap, 0, (int)((cta.c0 + issued) * nshell), &full[issued]);
-            }
-            const uint32_t desc_hi = (kSBO >> 4) | (1u << 14);  // stride byte offset, sm_100 descriptor version
-            for (int i = 0; i < nch; i++) {
-                const int slot = i % nslots, w = i / window;
-                if (!tc::mbar_wait(&produced[slot], (uint32_t)((i / nslots) & 1), s_abort)) break;
-                if (i % window == 0 && w > 0 && !tc::mbar_wait(acc_free, (uint32_t)((w - 1) & 1), s_abort)) break;
-                tc::fence_after_sync();
-                const uint32_t abase = tmem + (uint32_t)a0 + (uint32_t)slot * slot_cols;
-                const uint32_t bh = tc::smem_u32(s_b + (2 * slot) * bbuf_bytes);
-                const uint32_t bl = tc::smem_u32(s_b + (2 * slot + 1) * bbuf_bytes);
-                const bool wstart = (i % window) == 0;
-                for (int e = 0; e < nmma; e++) {
-                    const TcMma mm = s_mma[e];
-                    const uint32_t baddr = ((mm.idesc_flags & 1u) ? bl : bh) + mm.b_off;
-                    const uint64_t desc = (uint64_t)(((baddr >> 4) & 0x3FFFu) | ((kLBO >> 4) << 16)) |
-                                          ((uint64_t)desc_hi << 32);
-                    const uint32_t acc = (wstart && (mm.idesc_flags & 2u)) ? 0u : 1u;
-                    tc::mma_ts(tmem + mm.d_col, abase + mm.a_col, desc, mm.idesc_flags & ~3u, acc);
-                }
-                tc::mma_commit(&mma_done[slot]);
-                if (i % window == window - 1 || i == nch - 1) tc::mma_commit(acc_ready);
-                if (issued < nch) {
-                    const int st = issued % kTcStages;
-                    // the stage held chunk issued - kTcStages, released by the producers before produced[]
-                    if (!tc::mbar_wait(&empty[st], (uint32_t)(((issued - kTcStages) / kTcStages) & 1), s_abort)) break;
-                    tc::mbar_arrive_expect_tx(&full[st], stage_tx);
-                    tc::tma_load_2d(s_d + st * stage_bytes, &fmap, 0, (int)((cta.c0 + issued) * nshell), &full[st]);
-                    issued++;
-                }
-            }
-            // drain: every MMA issued by this thread, and every TMA load it started
-            tc::mma_commit(drain);
-            volatile int no_abort = 0;
-            tc::mbar_wait(drain, 0, &no_abort);
-            for (int st = 0; st < kTcStages && st < issued; st++) {
-                const int last = st + kTcStages * ((issued - 1 - st) / kTcStages);
-                tc::mbar_wait(&full[st], (uint32_t)((last / kTcStages) & 1), &no_abort);
+            for (int c = 0; c < pre; c++) {
+                tc::mbar_arrive_expect_tx(&full[c], stage_tx);
+                tc::tma_load_2d(s_d + c * stage_bytes, &fmap, 0, (int)((cta.c0 + c) * nshell), &full[c]);
             }
         }
         __syncwarp();
+        int st = 0, c = pre;
+        uint32_t ph = 0;  // phase of empty[st] that frees the stage for chunk c
+        for (; c < nch; c++) {
+            // the stage held chunk c - kTcStages; its team released it before produced[]
+            if (!tc::mbar_wait_warp(&empty[st], ph, s_abort)) break;
+            if (el) {
+                tc::mbar_arrive_expect_tx(&full[st], stage_tx);
+                tc::tma_load_2d(s_d + st * stage_bytes, &fmap, 0, (int)((cta.c0 + c) * nshell), &full[st]);
+            }
+            __syncwarp();
+            if (++st == kTcStages) {
+                st = 0;
+                ph ^= 1u;
+            }
+        }
+        // every load started (chunks 0 .. c - 1) must land before the block exits
+        if (el) {
+            volatile int no_abort = 0;
+            for (int s2 = 0; s2 < kTcStages && s2 < c; s2++) {
+                const int last = s2 + kTcStages * ((c - 1 - s2) / kTcStages);
+                tc::mbar_wait(&full[s2], (uint32_t)((last / kTcStages) & 1), &no_abort);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= kProdWarps) {
+        // ------------------------------------------------------------- MMA issuers
+        const int m = warp - kProdWarps;
+        if (m < nmt) {
+            uint32_t r_d[kTcMaxRunsMt], r_b[kTcMaxRunsMt], r_id[kTcMaxRunsMt];
+            const TcMTile mt = mtiles[grp.mt_off + m];
+            const int nrun = mt.nrun;
+#pragma unroll
+            for (int r = 0; r < kTcMaxRunsMt; r++) {
+                const int4 run = r < nrun ? runs[mt.run_off + r] : make_int4(0, 16, 0, 0);  // n0, nn, acc col
+                r_d[r] = tmem + (uint32_t)run.z;
+                r_b[r] = (uint32_t)(run.x / 8) * kSBO;
+                r_id[r] = tc::idesc_bf16(128, run.y);
+            }
+            const bool el = tc::elect_one();
+            // 64-bit descriptor = start address | LBO | (SBO, sm_100 descriptor version) << 32
+            const uint64_t desc_k = ((uint64_t)((kSBO >> 4) | (1u << 14)) << 32) | (uint64_t)((kLBO >> 4) << 16);
+            TcWindow win(0, window);
+            for (int i = 0; i < nch; i++) {
+                const int slot = i & 1;
+                win.advance_to(i, window);
+                const bool wstart = i == win.end - window + 1;
+                if (!tc::mbar_wait_warp(&produced[slot], (uint32_t)((i >> 1) & 1), s_abort)) break;
+                if (wstart && win.index > 0 && !tc::mbar_wait_warp(acc_free, (uint32_t)((win.index - 1) & 1), s_abort))
+                    break;
+                tc::fence_after_sync();
+                if (el) {
+                    const uint32_t a = tmem + (uint32_t)a0 + (uint32_t)slot * slot_cols + (uint32_t)(m * 32);
+                    const uint32_t bh = tc::smem_u32(s_b + (2 * slot) * bbuf_bytes);
+                    const uint32_t bl = tc::smem_u32(s_b + (2 * slot + 1) * bbuf_bytes);
+                    const uint32_t first = wstart ? 0u : 1u;
+#pragma unroll
+                    for (int r = 0; r < kTcMaxRunsMt; r++) {
+                        if (r < nrun) {
+#pragma unroll
+                            for (int ks = 0; ks < kTcChunk / 16; ks++) {
+                                const uint32_t bo = r_b[r] + (uint32_t)ks * 2 * kLBO;
+                                const uint64_t dh = desc_k | (uint64_t)(((bh + bo) >> 4) & 0x3FFFu);
+                                const uint64_t dl = desc_k | (uint64_t)(((bl + bo) >> 4) & 0x3FFFu);
+                                const uint32_t ak = a + (uint32_t)(ks * 8);
+                                tc::mma_ts(r_d[r], ak, dh, r_id[r], ks == 0 ? first : 1u);  // hi x hi
+                                tc::mma_ts(r_d[r], ak, dl, r_id[r], 1u);                    // hi x lo
+                                tc::mma_ts(r_d[r], ak + 16, dh, r_id[r], 1u);               // lo x hi
+                            }
+                        }
+                    }
+                    tc::mma_commit(&mma_done[slot]);
+                    if (i == win.end || i == nch - 1) tc::mma_commit(acc_ready);
+                }
+                __syncwarp();
+            }
+            // every MMA this issuer started completes before the columns are freed
+            if (el && nch > 0) tc::mma_commit(drain);
+            __syncwarp();
+        }
     } else {
         // ------------------------------------------------------------- producers
-        const int q = warp & 3, h = warp >> 2;  // lane quadrant, 8-cell slice of the chunk
+        const int team = warp / kTcTeamWarps, tw = warp % kTcTeamWarps;
+        const int q = tw & 3, mp = tw >> 2;  // lane quadrant, pair of M tiles (2 mp, 2 mp + 1)
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int row = 32 * q + lane;
-        short2 rf[kTcMaxMT];
-#pragma unroll
-        for (int m = 0; m < kTcMaxMT; m++) rf[m] = s_rowf[m * 128 + row];
-        for (int i = 0; i < nch; i++) {
-            const int st = i % kTcStages, slot = i % nslots, w = i / window;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((i / kTcStages) & 1), s_abort)) break;
-            if (i >= nslots && !tc::mbar_wait_warp(&mma_done[slot], (uint32_t)((i / nslots - 1) & 1), s_abort)) break;
-            const uint8_t* D = s_d + st * stage_bytes;
-            // A operand first (the longer job): all loads of this lane's rows, then the products
-            float4 xa[kTcMaxMT][2], xb[kTcMaxMT][2];
-#pragma unroll
-            for (int m = 0; m < kTcMaxMT; m++) {
-                if (m < nmt && rf[m].x >= 0) {
-                    const float4* r1 = (const float4*)(D + rf[m].x * 128);
-                    xa[m][0] = r1[(2 * h) ^ (rf[m].x & 7)];
-                    xa[m][1] = r1[(2 * h + 1) ^ (rf[m].x & 7)];
-                    if (RA == 2) {
-                        const float4* r2 = (const float4*)(D + rf[m].y * 128);
-                        xb[m][0] = r2[(2 * h) ^ (rf[m].y & 7)];
-                        xb[m][1] = r2[(2 * h + 1) ^ (rf[m].y & 7)];
-                    }
-                } else {
-                    xa[m][0] = xa[m][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    xb[m][0] = xb[m][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+        const int ma = 2 * mp, mb = 2 * mp + 1;
+        const short2 fa = s_rowf[ma * 128 + row], fb = s_rowf[mb * 128 + row];  // in-range shells
+        const int ttid = tid % (kTcTeamWarps * 32);
+        // slot `team`; stages team, team + 2, team + 4 in turn
+        const uint32_t abase = tmem + lane_base + (uint32_t)a0 + (uint32_t)team * slot_cols;
+        uint8_t* Bh = s_b + (2 * team) * bbuf_bytes;
+        uint8_t* Bl = s_b + (2 * team + 1) * bbuf_bytes;
+        int st = team;
+        uint32_t ph_full = 0, ph_md = 0;
+        TcWindow win(team, window);
+        for (int i = team; i < nch; i += 2) {
+            if (!tc::mbar_wait_warp(&full[st], ph_full, s_abort)) break;
+            if (i >= 2) {
+                // the MMAs of this team's previous chunk have read the slot
+                if (!tc::mbar_wait_warp(&mma_done[team], ph_md, s_abort)) break;
+                ph_md ^= 1u;
             }
-            const uint32_t abase = tmem + lane_base + (uint32_t)a0 + (uint32_t)slot * slot_cols;
-#pragma unroll
-            for (int m = 0; m < kTcMaxMT; m++) {
-                if (m >= nmt) break;
-                uint32_t hi[4], lo[4];
-#pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const float4 a = xa[m][j];
-                    if (RA == 2) {
-                        const float4 c = xb[m][j];
-                        tc::split2_prod(a.x, c.x, a.y, c.y, hi[2 * j], lo[2 * j]);
-                        tc::split2_prod(a.z, c.z, a.w, c.w, hi[2 * j + 1], lo[2 * j + 1]);
-                    } else {
-                        tc::split2(a.x, a.y, hi[2 * j], lo[2 * j]);
-                        tc::split2(a.z, a.w, hi[2 * j + 1], lo[2 * j + 1]);
-                    }
+            tc::fence_after_sync();
+            const uint8_t* D = s_d + st * stage_bytes;
+            {
+                uint32_t hi[16], lo[16];
+                if (ma < nmt) {
+                    tc_row_products<RA>(D, fa.x, RA == 2 ? fa.y : 0, hi, lo);
+                    tc::tmem_st16(abase + (uint32_t)(ma * 32), hi);
+                    tc::tmem_st16(abase + (uint32_t)(ma * 32 + 16), lo);
                 }
-                tc::tmem_st4(abase + (uint32_t)(m * 32 + h * 4), hi);
-                tc::tmem_st4(abase + (uint32_t)(m * 32 + 16 + h * 4), lo);
+                if (mb < nmt) {
+                    tc_row_products<RA>(D, fb.x, RA == 2 ? fb.y : 0, hi, lo);
+                    tc::tmem_st16(abase + (uint32_t)(mb * 32), hi);
+                    tc::tmem_st16(abase + (uint32_t)(mb * 32 + 16), lo);
+                }
             }
             // B operand: (column n, 8-cell group kg) -> one 16-byte core-matrix row of hi and of lo
-            uint8_t* Bh = s_b + (2 * slot) * bbuf_bytes;
-            uint8_t* Bl = s_b + (2 * slot + 1) * bbuf_bytes;
-            for (int it = tid; it < ncol * (kTcChunk / 8); it += kTcProducers) {
+            for (int it = ttid; it < ncol * (kTcChunk / 8); it += kTcTeamWarps * 32) {
                 const int kg = it / ncol, n = it - (it / ncol) * ncol;
                 const short2 f = s_colf[n];
                 uint4 hi, lo;
                 if (f.x >= 0) {
-                    const float4* r1 = (const float4*)(D + f.x * 128);
-                    const float4 x0 = r1[(2 * kg) ^ (f.x & 7)], x1 = r1[(2 * kg + 1) ^ (f.x & 7)];
+                    const float4* c1 = (const float4*)(D + f.x * 128);
+                    const float4 x0 = c1[(2 * kg) ^ (f.x & 7)], x1 = c1[(2 * kg + 1) ^ (f.x & 7)];
                     if (CA == 2) {
-                        const float4* r2 = (const float4*)(D + f.y * 128);
-                        const float4 y0 = r2[(2 * kg) ^ (f.y & 7)], y1 = r2[(2 * kg + 1) ^ (f.y & 7)];
+                        const float4* c2 = (const float4*)(D + f.y * 128);
+                        const float4 y0 = c2[(2 * kg) ^ (f.y & 7)], y1 = c2[(2 * kg + 1) ^ (f.y & 7)];
                         tc::split2_prod(x0.x, y0.x, x0.y, y0.y, hi.x, lo.x);
                         tc::split2_prod(x0.z, y0.z, x0.w, y0.w, hi.y, lo.y);
                         tc::split2_prod(x1.x, y1.x, x1.y, y1.y, hi.z, lo.z);
@@ -298,13 +335,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             __syncwarp();
             if (lane == 0) {
                 tc::mbar_arrive(&empty[st]);
-                tc::mbar_arrive(&produced[slot]);
+                tc::mbar_arrive(&produced[team]);
             }
-            // drain the accumulators at the end of a window
-            if (i % window == window - 1 || i == nch - 1) {
-                if (!tc::mbar_wait_warp(acc_ready, (uint32_t)(w & 1), s_abort)) break;
+            st += 2;
+            if (st >= kTcStages) {
+                st -= kTcStages;
+                ph_full ^= 1u;
+            }
+            // drain the accumulators after the last chunk of a window
+            win.advance_to(i, window);
+            if (i == win.end || i == nch - 1) {
+                if (!tc::mbar_wait_warp(acc_ready, (uint32_t)(win.index & 1), s_abort)) break;
                 tc::fence_after_sync();
-                for (int g = h; g < acc_cols / 16; g += 4) {
+                for (int g = mp; g < acc_cols / 16; g += 2) {
                     uint32_t v[16];
                     tc::tmem_ld16(tmem + lane_base + (uint32_t)(g * 16), v);
                     tc::tmem_ld_wait();
@@ -321,7 +364,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     double* out = partial + (size_t)blockIdx.x * (kTcAccMax * 128);
     for (int i = tid; i < acc_cols * 128; i += kTcThreads) out[i] = (double)s_acc[i];
-    if (warp == kTcProducers / 32) {
+    if (warp == kProdWarps) {
+        // every issuer committed its MMAs to `drain`; wait for them before freeing the columns
+        volatile int no_abort2 = 0;
+        if (nch > 0 && lane == 0) tc::mbar_wait(drain, 0, &no_abort2);
+        __syncwarp();
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
     }
@@ -424,7 +471,7 @@ struct TcState {
     int nshell = 0;
     int stage_bytes = 0, bbuf_bytes = 0, smem_bytes = 0;
     int window = 64;
-    int slot_cap = 2, acc_max = 256;
+    int acc_max = 256;
     int ra = 2, ca = 1;
     void *d_ctas = nullptr, *d_groups = nullptr, *d_mtiles = nullptr, *d_runs = nullptr, *d_rowf = nullptr,
          *d_colf = nullptr, *d_binmap = nullptr;
@@ -448,10 +495,35 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 static size_t tc_smem_bytes(int stage_bytes, int bbuf_bytes, int slots, int acc_max) {
     return 1024 + (size_t)kTcStages * stage_bytes + 2 * (size_t)slots * bbuf_bytes + (size_t)acc_max * 128 * 4 +
-           kTcMaxMT * 128 * 4 + kTcMaxCols * 4 + kTcMaxMma * sizeof(TcMma) + (2 * kTcStages + 11) * 8 + 64;
+           kTcMaxMT * 128 * 4 + kTcMaxCols * 4 + (2 * kTcStages + 11) * 8 + 64;
 }
 
-// Build the groups: rows sorted by column span, 128-row M tiles, 16-column blocks.
+// Sorted 16-column blocks of one M tile -> runs (first block, block count), at most
+// kTcMaxRunsMt of them: the narrowest gaps are filled (their sums are computed and unused).
+static std::vector<std::pair<int, int>> tc_runs(const std::set<int>& blocks) {
+    std::vector<std::pair<int, int>> rr;
+    for (int b : blocks) {
+        if (!rr.empty() && rr.back().first + rr.back().second == b) rr.back().second++;
+        else rr.push_back({b, 1});
+    }
+    while ((int)rr.size() > kTcMaxRunsMt) {
+        size_t best = 0;
+        int gap = 1 << 30;
+        for (size_t k = 0; k + 1 < rr.size(); k++) {
+            const int g = rr[k + 1].first - (rr[k].first + rr[k].second);
+            if (g < gap) {
+                gap = g;
+                best = k;
+            }
+        }
+        rr[best].second = rr[best + 1].first + rr[best + 1].second - rr[best].first;
+        rr.erase(rr.begin() + (long)best + 1);
+    }
+    return rr;
+}
+
+// Build the groups: 32-row blocks of rows sorted by column span, 128-row M tiles,
+// 16-column blocks.
 poly_status ps_tc_prepare(PsPlan* p) {
     if (p->is_double) return POLY_ERR_UNSUPPORTED;
     TcState* t = new (std::nothrow) TcState();
@@ -461,7 +533,8 @@ poly_status ps_tc_prepare(PsPlan* p) {
     t->ra = n >= 3 ? 2 : 1;
     t->ca = n - t->ra;
     t->nshell = p->nshell;
-    auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], t->ra == 2 ? b[1] : -1); };
+    const bool ra2 = t->ra == 2;
+    auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra2 ? b[1] : -1); };
     auto ckey = [&](const int32_t* b) { return std::make_pair(b[t->ra], t->ca == 2 ? b[t->ra + 1] : -1); };
     std::map<std::pair<int, int>, std::set<std::pair<int, int>>> rows;
     std::set<std::pair<int, int>> allcols;
@@ -472,26 +545,58 @@ poly_status ps_tc_prepare(PsPlan* p) {
     std::map<std::pair<int, int>, int> gcol;
     for (auto& c : allcols) gcol[c] = (int)gcol.size();
     struct Row {
-        std::pair<int, int> key;
-        std::vector<int> cols;  // global column indices, sorted
+        bool valid;
+        std::pair<int, int> key;  // shells (from 1) of the row factors; in range also for padding rows
+        std::vector<int> cols;    // global column indices, sorted (empty for padding rows)
     };
-    std::vector<Row> rl;
+    // A producer warp takes 32 rows: pair rows by 8 consecutive k1 x 4 consecutive k2,
+    // single-field rows by 32 consecutive k1.  Lanes without a row repeat an in-range
+    // neighbour (their accumulator rows are never read), so the warp's factor reads stay
+    // within the block's 8 + 4 (or 32) shells.
+    const int ns = p->nshell;
+    std::map<std::pair<int, int>, std::vector<Row>> blocks;
     for (auto& kv : rows) {
-        Row r{kv.first, {}};
+        const int k1 = kv.first.first, k2 = kv.first.second;
+        const std::pair<int, int> bk =
+            ra2 ? std::make_pair((k1 - 1) / kTcRowBlock1, (k2 - 1) / kTcRowBlock2) : std::make_pair((k1 - 1) / 32, 0);
+        auto it = blocks.find(bk);
+        if (it == blocks.end()) {
+            std::vector<Row> blk(32);
+            for (int l = 0; l < 32; l++) {
+                blk[l].valid = false;
+                blk[l].key = ra2 ? std::make_pair(std::min(ns, bk.first * kTcRowBlock1 + l / kTcRowBlock2 + 1),
+                                                  std::min(ns, bk.second * kTcRowBlock2 + l % kTcRowBlock2 + 1))
+                                 : std::make_pair(std::min(ns, bk.first * 32 + l + 1), -1);
+            }
+            it = blocks.emplace(bk, std::move(blk)).first;
+        }
+        const int l = ra2 ? ((k1 - 1) % kTcRowBlock1) * kTcRowBlock2 + (k2 - 1) % kTcRowBlock2 : (k1 - 1) % 32;
+        Row& r = it->second[l];
+        r.valid = true;
+        r.key = kv.first;
         for (auto& c : kv.second) r.cols.push_back(gcol[c]);
         std::sort(r.cols.begin(), r.cols.end());
-        rl.push_back(r);
     }
-    std::stable_sort(rl.begin(), rl.end(), [](const Row& a, const Row& b) {
-        return std::make_pair(a.cols.front(), a.cols.back()) < std::make_pair(b.cols.front(), b.cols.back());
-    });
-    const int nmt_total = (int)((rl.size() + 127) / 128);
+    std::vector<std::pair<std::pair<int, int>, const std::vector<Row>*>> bl;  // (column span, block)
+    for (auto& kv : blocks) {
+        int lo = 1 << 30, hi = -1;
+        for (const Row& r : kv.second)
+            if (r.valid) {
+                lo = std::min(lo, r.cols.front());
+                hi = std::max(hi, r.cols.back());
+            }
+        bl.push_back({{lo, hi}, &kv.second});
+    }
+    std::stable_sort(bl.begin(), bl.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    std::vector<Row> rl;
+    for (auto& b : bl) rl.insert(rl.end(), b.second->begin(), b.second->end());
+    while (rl.size() % 128) rl.push_back(Row{false, {1, ra2 ? 1 : -1}, {}});
+    const int nmt_total = (int)(rl.size() / 128);
     // group consecutive M tiles; a group is valid when its local column list (<= 256)
     // and its accumulator columns (<= 256) fit
     auto mt_cols = [&](int m) {
         std::set<int> s;
-        for (size_t r = (size_t)m * 128; r < std::min(rl.size(), (size_t)(m + 1) * 128); r++)
-            s.insert(rl[r].cols.begin(), rl[r].cols.end());
+        for (size_t r = (size_t)m * 128; r < (size_t)(m + 1) * 128; r++) s.insert(rl[r].cols.begin(), rl[r].cols.end());
         return s;
     };
     struct GroupPlan {
@@ -513,9 +618,9 @@ poly_status ps_tc_prepare(PsPlan* p) {
         for (size_t i = 0; i < g.local.size(); i++) lidx[g.local[i]] = (int)i;
         g.acc = 0;
         for (int m = m0; m < m1; m++) {
-            std::set<int> blocks;
-            for (int c : mt_cols(m)) blocks.insert(lidx[c] / 16);
-            g.acc += 16 * (int)blocks.size();
+            std::set<int> cb;
+            for (int c : mt_cols(m)) cb.insert(lidx[c] / 16);
+            for (auto& rr : tc_runs(cb)) g.acc += 16 * rr.second;
         }
         return g.acc <= kTcAccMax && (m1 - m0) <= kTcMaxMT;
     };
@@ -569,29 +674,22 @@ poly_status ps_tc_prepare(PsPlan* p) {
             TcMTile M{};
             M.row_off = (int)rowf.size();
             M.run_off = (int)runs.size();
-            const size_t r0 = (size_t)m * 128, r1 = std::min(rl.size(), r0 + 128);
-            for (size_t r = r0; r < r0 + 128; r++) {
-                short2 f = make_short2(-1, -1);
-                if (r < r1) {
-                    f.x = (short)(rl[r].key.first - 1);
-                    f.y = (short)(rl[r].key.second > 0 ? rl[r].key.second - 1 : -1);
-                }
+            const size_t r0 = (size_t)m * 128, r1 = r0 + 128;
+            for (size_t r = r0; r < r1; r++) {
+                short2 f;
+                f.x = (short)(rl[r].key.first - 1);
+                f.y = (short)(rl[r].key.second > 0 ? rl[r].key.second - 1 : -1);
                 rowf.push_back(f);
             }
-            std::set<int> blocks;
+            std::set<int> cb;
             for (size_t r = r0; r < r1; r++)
-                for (int c : rl[r].cols) blocks.insert(lidx[c] / 16);
-            // merge consecutive blocks into runs
-            std::vector<int> bl(blocks.begin(), blocks.end());
+                for (int c : rl[r].cols) cb.insert(lidx[c] / 16);
             std::map<int, std::pair<int, int>> block_acc;  // block -> (run n0, acc col of run start)
-            for (size_t k = 0; k < bl.size();) {
-                size_t e = k;
-                while (e + 1 < bl.size() && bl[e + 1] == bl[e] + 1 && (int)(e + 2 - k) * 16 <= 256) e++;
-                const int n0 = bl[k] * 16, nn = (int)(e - k + 1) * 16;
+            for (auto& rr : tc_runs(cb)) {
+                const int n0 = rr.first * 16, nn = rr.second * 16;
                 runs.push_back(make_int4(n0, nn, acc, m - gp.m0));
-                for (size_t q = k; q <= e; q++) block_acc[bl[q]] = {n0, acc};
+                for (int q = rr.first; q < rr.first + rr.second; q++) block_acc[q] = {n0, acc};
                 acc += nn;
-                k = e + 1;
             }
             M.nrun = (int)runs.size() - M.run_off;
             for (size_t r = r0; r < r1; r++)
@@ -606,8 +704,10 @@ poly_status ps_tc_prepare(PsPlan* p) {
         }
         G.acc_cols = acc;
         groups.push_back(G);
-        gwork.push_back((double)acc);
-        work_cells += acc;
+        // per-chunk cost: tensor pipe (3 MMAs x K/16 per 16 accumulator columns) or producers, whichever is longer
+        const double wk = std::max(3.0 * acc, 160.0 * G.nmt + 100.0);
+        gwork.push_back(wk);
+        work_cells += wk;
         t->executed_flops_per_cell += 3.0 * 2.0 * 128.0 * acc;
     }
     // blocks: split each group's chunks in proportion to its work
@@ -653,12 +753,6 @@ poly_status ps_tc_prepare(PsPlan* p) {
         (s = up(&t->d_colf, colf.data(), colf.size() * sizeof(short2))) ||
         (s = up(&t->d_binmap, binmap.data(), std::max<size_t>(1, binmap.size()) * sizeof(int4))))
         return s;
-    for (auto& g : groups)
-        if (g.nmt > 0 && (int)runs.size() > 0) {
-            int nr = 0;
-            for (int m = 0; m < g.nmt; m++) nr += mtiles[g.mt_off + m].nrun;
-            if (nr > kTcMaxRuns) return POLY_ERR_UNSUPPORTED;
-        }
     if ((s = ps_alloc(p, (void**)&t->d_partial, t->ctas.size() * (size_t)kTcAccMax * 128 * 8))) return s;
     if ((s = ps_alloc(p, (void**)&t->d_err, 16))) return s;
     if (cudaMemset(t->d_err, 0, 16)) return POLY_ERR_CUDA;
@@ -679,16 +773,10 @@ poly_status ps_tc_prepare(PsPlan* p) {
     for (auto& g : groups) {
         maxcol = std::max(maxcol, g.ncol);
         maxacc = std::max(maxacc, g.acc_cols);
-        int nm = 0;
-        for (int m = 0; m < g.nmt; m++) nm += 6 * mtiles[g.mt_off + m].nrun;
-        if (nm > kTcMaxMma) return POLY_ERR_UNSUPPORTED;
     }
     t->bbuf_bytes = maxcol * kTcChunk * 2;
     t->acc_max = maxacc;
-    t->slot_cap = 4;  // A/B slots: as many as shared memory allows (the kernel also bounds them by TMEM)
-    while (t->slot_cap > 2 && tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc) > 227 * 1024)
-        t->slot_cap--;
-    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc);
+    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, 2, maxacc);
     if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
     const char* w = getenv("POLY_TC_WINDOW");
     if (w && atoi(w) > 0) t->window = atoi(w);
@@ -703,7 +791,7 @@ poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {
         cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t->smem_bytes);
         if (e2) return e2;
         kern<<<(unsigned)t->ctas.size(), kTcThreads, t->smem_bytes, st>>>(
-            t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->slot_cap, t->acc_max, t->window, (const TcCta*)t->d_ctas,
+            t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->acc_max, t->window, (const TcCta*)t->d_ctas,
             (const TcGroup*)t->d_groups, (const TcMTile*)t->d_mtiles, (const int4*)t->d_runs,
             (const short2*)t->d_rowf, (const short2*)t->d_colf, t->d_partial, t->d_err);
         return cudaGetLastError();

@@ -42,6 +42,15 @@ PS_DEV void tmem_st4(uint32_t taddr, const uint32_t* v) {
                  "r"(v[2]), "r"(v[3])
                  : "memory");
 }
+// 32 lanes x 16 columns of 32 bits: this thread's lane, columns taddr.col .. +15
+PS_DEV void tmem_st16(uint32_t taddr, const uint32_t* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
 PS_DEV void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 32 lanes x 16 columns of 32 bits: this thread's lane, columns taddr.col .. +15
@@ -55,6 +64,14 @@ PS_DEV void tmem_ld16(uint32_t taddr, uint32_t* v) {
         : "memory");
 }
 PS_DEV void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Elects one lane of a converged warp.  A tcgen05.commit tracks only the MMAs of
+// the thread that executes it, so callers elect once and keep the result.
+PS_DEV bool elect_one() {
+    uint32_t p;
+    asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}\n" : "=r"(p));
+    return p != 0;
+}
 
 // ---- descriptors ------------------------------------------------------------
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
