@@ -10,9 +10,9 @@
 // (round-to-nearest adds), and the per-block sums are reduced in FP64 across
 // blocks in a fixed order.
 //
-// Block layout: 16 producer warps in two teams, 4 issuer warps, 1 load warp.
-// The load warp streams 32-cell chunks of all shell fields (one contiguous block
-// of the cell-tiled field layout) into shared memory with TMA (128-byte swizzle).
+// Block layout: 16 producer warps in two teams and 4 issuer warps.  Issuer 0
+// also streams 32-cell chunks of all shell fields (one contiguous block of the
+// cell-tiled field layout) into shared memory with TMA (128-byte swizzle).
 // Team t produces chunks t, t + 2, ... into A/B slot t, so that one team's
 // barrier waits overlap the other team's work.  Producer warp w of a team owns
 // TMEM lane quadrant w % 4 of M tiles 2 (w / 4) and 2 (w / 4) + 1: each lane forms
@@ -47,7 +47,7 @@ constexpr int kTcMaxMT = 4;          // M tiles per block
 constexpr int kTcTeamWarps = 8;      // producer warps per team: 4 lane quadrants x 2 pairs of M tiles
 constexpr int kTcProducers = 2 * kTcTeamWarps * 32;
 constexpr int kTcIssuers = kTcMaxMT;  // one MMA-issuing warp per M tile
-constexpr int kTcThreads = kTcProducers + 32 * kTcIssuers + 32;  // + the load warp
+constexpr int kTcThreads = kTcProducers + 32 * kTcIssuers;
 constexpr int kTcAccMax = 256;       // accumulator columns per block
 constexpr int kTcABase = 256;        // first TMEM column of the A operand in the self-test
 constexpr int kTcMaxRunsMt = 4;      // N runs per M tile
@@ -85,18 +85,59 @@ struct TcWindow {
     }
 };
 
+// One B item: 8 cells of column factor(s) -> hi and lo 16-byte core-matrix rows.
+// key1 < 0 marks a padding column (zeros).
+template <int CA>
+__device__ __forceinline__ void tc_b_item(uint32_t D, int key1, int key2, uint32_t dst_hi, uint32_t dst_lo) {
+    uint32_t h[4] = {0u, 0u, 0u, 0u}, l[4] = {0u, 0u, 0u, 0u};
+    if (key1 >= 0) {
+        float4 x0, x1;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(x0.x), "=f"(x0.y), "=f"(x0.z), "=f"(x0.w) : "r"(D + (uint32_t)key1));
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(x1.x), "=f"(x1.y), "=f"(x1.z), "=f"(x1.w) : "r"(D + ((uint32_t)key1 ^ 16u)));
+        if (CA == 2) {
+            float4 y0, y1;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(y0.x), "=f"(y0.y), "=f"(y0.z), "=f"(y0.w) : "r"(D + (uint32_t)key2));
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(y1.x), "=f"(y1.y), "=f"(y1.z), "=f"(y1.w) : "r"(D + ((uint32_t)key2 ^ 16u)));
+            tc::split2_prod_x2(x0.x, y0.x, x0.y, y0.y, h[0], l[0]);
+            tc::split2_prod_x2(x0.z, y0.z, x0.w, y0.w, h[1], l[1]);
+            tc::split2_prod_x2(x1.x, y1.x, x1.y, y1.y, h[2], l[2]);
+            tc::split2_prod_x2(x1.z, y1.z, x1.w, y1.w, h[3], l[3]);
+        } else {
+            tc::split2(x0.x, x0.y, h[0], l[0]);
+            tc::split2(x0.z, x0.w, h[1], l[1]);
+            tc::split2(x1.x, x1.y, h[2], l[2]);
+            tc::split2(x1.z, x1.w, h[3], l[3]);
+        }
+    }
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst_hi), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3])
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst_lo), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3])
+                 : "memory");
+}
+
+// Shared-memory byte offset of 16-byte chunk c of staged shell row k (128-byte
+// swizzle): k * 128 + ((c ^ (k & 7)) * 16) = row_key(k) ^ (c * 16).
+__device__ __forceinline__ uint32_t tc_row_key(int k) { return (uint32_t)(k * 128) ^ (uint32_t)((k & 7) * 16); }
+
 template <int RA>
-__device__ __forceinline__ void tc_row_products(const uint8_t* D, int k1, int k2, uint32_t* hi, uint32_t* lo) {
+__device__ __forceinline__ void tc_row_products(uint32_t D, uint32_t key1, uint32_t key2, uint32_t* hi, uint32_t* lo) {
     // the 32 products of one row for a chunk; column j holds cells 2j, 2j+1
-    const float4* r1 = (const float4*)(D + k1 * 128);
-    const float4* r2 = (const float4*)(D + k2 * 128);
 #pragma unroll
     for (int c = 0; c < 8; c++) {
-        const float4 x = r1[c ^ (k1 & 7)];
+        float4 x, y;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w)
+                     : "r"(D + (key1 ^ (uint32_t)(c * 16))));
         if (RA == 2) {
-            const float4 y = r2[c ^ (k2 & 7)];
-            tc::split2_prod(x.x, y.x, x.y, y.y, hi[2 * c], lo[2 * c]);
-            tc::split2_prod(x.z, y.z, x.w, y.w, hi[2 * c + 1], lo[2 * c + 1]);
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
+                         : "r"(D + (key2 ^ (uint32_t)(c * 16))));
+            tc::split2_prod_x2(x.x, y.x, x.y, y.y, hi[2 * c], lo[2 * c]);
+            tc::split2_prod_x2(x.z, y.z, x.w, y.w, hi[2 * c + 1], lo[2 * c + 1]);
         } else {
             tc::split2(x.x, x.y, hi[2 * c], lo[2 * c]);
             tc::split2(x.z, x.w, hi[2 * c + 1], lo[2 * c + 1]);
@@ -135,7 +176,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int nch = (int)(cta.c1 - cta.c0);
     const int nmt = grp.nmt, ncol = grp.ncol, acc_cols = grp.acc_cols;
     constexpr int kProdWarps = kTcProducers / 32;
-    constexpr int kLoadWarp = kProdWarps + kTcIssuers;
     // TMEM columns: accumulators [0, a0), then slot t of team t: nmt x 32 columns (hi 16 + lo 16 per M tile)
     const int a0 = (acc_cols + 31) / 32 * 32;
     const uint32_t slot_cols = (uint32_t)(nmt * 32);
@@ -171,45 +211,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tmem = *s_tmem;
     const uint32_t stage_tx = (uint32_t)nshell * kTcChunk * 4;
 
-    if (warp == kLoadWarp) {
-        // ------------------------------------------------------------- TMA loads
+    if (warp >= kProdWarps) {
+        // ------------------------------------------------------------- MMA issuers (issuer 0 also loads)
+        const int m = warp - kProdWarps;
         const bool el = tc::elect_one();
         const int pre = kTcStages < nch ? kTcStages : nch;
-        if (el && nch > 0) {
-            tc::prefetch_tensormap(&fmap);
-            for (int c = 0; c < pre; c++) {
-                tc::mbar_arrive_expect_tx(&full[c], stage_tx);
-                tc::tma_load_2d(s_d + c * stage_bytes, &fmap, 0, (int)((cta.c0 + c) * nshell), &full[c]);
-            }
-        }
-        __syncwarp();
-        int st = 0, c = pre;
-        uint32_t ph = 0;  // phase of empty[st] that frees the stage for chunk c
-        for (; c < nch; c++) {
-            // the stage held chunk c - kTcStages; its team released it before produced[]
-            if (!tc::mbar_wait_warp(&empty[st], ph, s_abort)) break;
-            if (el) {
-                tc::mbar_arrive_expect_tx(&full[st], stage_tx);
-                tc::tma_load_2d(s_d + st * stage_bytes, &fmap, 0, (int)((cta.c0 + c) * nshell), &full[st]);
+        int c = pre;  // next chunk to load
+        if (m == 0) {
+            if (el && nch > 0) {
+                tc::prefetch_tensormap(&fmap);
+                for (int c0 = 0; c0 < pre; c0++) {
+                    tc::mbar_arrive_expect_tx(&full[c0], stage_tx);
+                    tc::tma_load_2d(s_d + c0 * stage_bytes, &fmap, 0, (int)((cta.c0 + c0) * nshell), &full[c0]);
+                }
             }
             __syncwarp();
-            if (++st == kTcStages) {
-                st = 0;
-                ph ^= 1u;
-            }
         }
-        // every load started (chunks 0 .. c - 1) must land before the block exits
-        if (el) {
-            volatile int no_abort = 0;
-            for (int s2 = 0; s2 < kTcStages && s2 < c; s2++) {
-                const int last = s2 + kTcStages * ((c - 1 - s2) / kTcStages);
-                tc::mbar_wait(&full[s2], (uint32_t)((last / kTcStages) & 1), &no_abort);
-            }
-        }
-        __syncwarp();
-    } else if (warp >= kProdWarps) {
-        // ------------------------------------------------------------- MMA issuers
-        const int m = warp - kProdWarps;
         if (m < nmt) {
             uint32_t r_d[kTcMaxRunsMt], r_b[kTcMaxRunsMt], r_id[kTcMaxRunsMt];
             const TcMTile mt = mtiles[grp.mt_off + m];
@@ -221,10 +238,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 r_b[r] = (uint32_t)(run.x / 8) * kSBO;
                 r_id[r] = tc::idesc_bf16(128, run.y);
             }
-            const bool el = tc::elect_one();
             // 64-bit descriptor = start address | LBO | (SBO, sm_100 descriptor version) << 32
             const uint64_t desc_k = ((uint64_t)((kSBO >> 4) | (1u << 14)) << 32) | (uint64_t)((kLBO >> 4) << 16);
             TcWindow win(0, window);
+            int lst = 0;
+            uint32_t lph = 0;  // stage and phase of empty[] that frees the stage for chunk c
             for (int i = 0; i < nch; i++) {
                 const int slot = i & 1;
                 win.advance_to(i, window);
@@ -257,11 +275,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (i == win.end || i == nch - 1) tc::mma_commit(acc_ready);
                 }
                 __syncwarp();
+                if (m == 0 && c < nch) {
+                    // the stage held chunk c - kTcStages = i, released by its team before produced[]
+                    if (!tc::mbar_wait_warp(&empty[lst], lph, s_abort)) break;
+                    if (el) {
+                        tc::mbar_arrive_expect_tx(&full[lst], stage_tx);
+                        tc::tma_load_2d(s_d + lst * stage_bytes, &fmap, 0, (int)((cta.c0 + c) * nshell), &full[lst]);
+                    }
+                    __syncwarp();
+                    c++;
+                    if (++lst == kTcStages) {
+                        lst = 0;
+                        lph ^= 1u;
+                    }
+                }
             }
             // every MMA this issuer started completes before the columns are freed
             if (el && nch > 0) tc::mma_commit(drain);
             __syncwarp();
         }
+        if (m == 0 && el) {
+            // every load started (chunks 0 .. c - 1) lands before the block exits
+            volatile int no_abort = 0;
+            for (int s2 = 0; s2 < kTcStages && s2 < c; s2++) {
+                const int last = s2 + kTcStages * ((c - 1 - s2) / kTcStages);
+                tc::mbar_wait(&full[s2], (uint32_t)((last / kTcStages) & 1), &no_abort);
+            }
+        }
+        __syncwarp();
     } else {
         // ------------------------------------------------------------- producers
         const int team = warp / kTcTeamWarps, tw = warp % kTcTeamWarps;
@@ -270,11 +311,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int row = 32 * q + lane;
         const int ma = 2 * mp, mb = 2 * mp + 1;
         const short2 fa = s_rowf[ma * 128 + row], fb = s_rowf[mb * 128 + row];  // in-range shells
+        const uint32_t ka1 = tc_row_key(fa.x), ka2 = tc_row_key(RA == 2 ? fa.y : 0);
+        const uint32_t kb1 = tc_row_key(fb.x), kb2 = tc_row_key(RA == 2 ? fb.y : 0);
         const int ttid = tid % (kTcTeamWarps * 32);
         // slot `team`; stages team, team + 2, team + 4 in turn
         const uint32_t abase = tmem + lane_base + (uint32_t)a0 + (uint32_t)team * slot_cols;
-        uint8_t* Bh = s_b + (2 * team) * bbuf_bytes;
-        uint8_t* Bl = s_b + (2 * team + 1) * bbuf_bytes;
+        const uint32_t Bh = tc::smem_u32(s_b + (2 * team) * bbuf_bytes);
+        const uint32_t Bl = tc::smem_u32(s_b + (2 * team + 1) * bbuf_bytes);
+        const uint32_t sd0 = tc::smem_u32(s_d);
+        // this thread's first B item (column n, 8-cell group kg), fixed for every chunk
+        const int nbitems = ncol * (kTcChunk / 8);
+        int b_key1 = -1, b_key2 = 0;
+        uint32_t b_off = 0;
+        if (ttid < nbitems) {
+            const int kg = ttid / ncol, n = ttid - kg * ncol;
+            const short2 f = s_colf[n];
+            if (f.x >= 0) {
+                b_key1 = (int)(tc_row_key(f.x) ^ (uint32_t)(2 * kg * 16));
+                b_key2 = (int)(tc_row_key(CA == 2 ? f.y : 0) ^ (uint32_t)(2 * kg * 16));
+            }
+            b_off = (uint32_t)(n / 8) * kSBO + (uint32_t)kg * kLBO + (uint32_t)(n % 8) * 16;
+        }
         int st = team;
         uint32_t ph_full = 0, ph_md = 0;
         TcWindow win(team, window);
@@ -286,48 +343,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 ph_md ^= 1u;
             }
             tc::fence_after_sync();
-            const uint8_t* D = s_d + st * stage_bytes;
+            const uint32_t D = sd0 + (uint32_t)(st * stage_bytes);
             {
                 uint32_t hi[16], lo[16];
                 if (ma < nmt) {
-                    tc_row_products<RA>(D, fa.x, RA == 2 ? fa.y : 0, hi, lo);
+                    tc_row_products<RA>(D, ka1, ka2, hi, lo);
                     tc::tmem_st16(abase + (uint32_t)(ma * 32), hi);
                     tc::tmem_st16(abase + (uint32_t)(ma * 32 + 16), lo);
                 }
                 if (mb < nmt) {
-                    tc_row_products<RA>(D, fb.x, RA == 2 ? fb.y : 0, hi, lo);
+                    tc_row_products<RA>(D, kb1, kb2, hi, lo);
                     tc::tmem_st16(abase + (uint32_t)(mb * 32), hi);
                     tc::tmem_st16(abase + (uint32_t)(mb * 32 + 16), lo);
                 }
             }
             // B operand: (column n, 8-cell group kg) -> one 16-byte core-matrix row of hi and of lo
-            for (int it = ttid; it < ncol * (kTcChunk / 8); it += kTcTeamWarps * 32) {
-                const int kg = it / ncol, n = it - (it / ncol) * ncol;
+            if (ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, Bh + b_off, Bl + b_off);
+            for (int it = ttid + kTcTeamWarps * 32; it < nbitems; it += kTcTeamWarps * 32) {
+                const int kg = it / ncol, n = it - kg * ncol;
                 const short2 f = s_colf[n];
-                uint4 hi, lo;
-                if (f.x >= 0) {
-                    const float4* c1 = (const float4*)(D + f.x * 128);
-                    const float4 x0 = c1[(2 * kg) ^ (f.x & 7)], x1 = c1[(2 * kg + 1) ^ (f.x & 7)];
-                    if (CA == 2) {
-                        const float4* c2 = (const float4*)(D + f.y * 128);
-                        const float4 y0 = c2[(2 * kg) ^ (f.y & 7)], y1 = c2[(2 * kg + 1) ^ (f.y & 7)];
-                        tc::split2_prod(x0.x, y0.x, x0.y, y0.y, hi.x, lo.x);
-                        tc::split2_prod(x0.z, y0.z, x0.w, y0.w, hi.y, lo.y);
-                        tc::split2_prod(x1.x, y1.x, x1.y, y1.y, hi.z, lo.z);
-                        tc::split2_prod(x1.z, y1.z, x1.w, y1.w, hi.w, lo.w);
-                    } else {
-                        tc::split2(x0.x, x0.y, hi.x, lo.x);
-                        tc::split2(x0.z, x0.w, hi.y, lo.y);
-                        tc::split2(x1.x, x1.y, hi.z, lo.z);
-                        tc::split2(x1.z, x1.w, hi.w, lo.w);
-                    }
-                } else {
-                    hi = make_uint4(0u, 0u, 0u, 0u);
-                    lo = hi;
-                }
                 const uint32_t off = (uint32_t)(n / 8) * kSBO + (uint32_t)kg * kLBO + (uint32_t)(n % 8) * 16;
-                *(uint4*)(Bh + off) = hi;
-                *(uint4*)(Bl + off) = lo;
+                tc_b_item<CA>(D, f.x >= 0 ? (int)(tc_row_key(f.x) ^ (uint32_t)(2 * kg * 16)) : -1,
+                              (int)(tc_row_key(CA == 2 && f.x >= 0 ? f.y : 0) ^ (uint32_t)(2 * kg * 16)), Bh + off,
+                              Bl + off);
             }
             tc::fence_proxy_async_smem();
             tc::tmem_st_wait();

@@ -189,5 +189,30 @@ PS_DEV void split2_prod(float x0, float y0, float x1, float y1, uint32_t& hi, ui
     lo = *reinterpret_cast<uint32_t*>(&l);
 }
 
+// The same for two products at once with packed FP32 pairs (sm_100 family):
+// (x0 y0, x1 y1) -> hi = RN_bf16 pair, lo = RN_bf16 pair of the exact residuals.
+PS_DEV void split2_prod_x2(float x0, float y0, float x1, float y1, uint32_t& hi, uint32_t& lo) {
+    asm("{\n\t"
+        ".reg .b64 xa, ya, pa, na, ra;\n\t"
+        ".reg .f32 p0, p1, r0, r1;\n\t"
+        ".reg .b32 h, n0, n1;\n\t"
+        "mov.b64 xa, {%2, %3};\n\t"
+        "mov.b64 ya, {%4, %5};\n\t"
+        "mul.rn.f32x2 pa, xa, ya;\n\t"
+        "mov.b64 {p0, p1}, pa;\n\t"
+        "cvt.rn.bf16x2.f32 h, p1, p0;\n\t"
+        "xor.b32 n1, h, 0x80008000;\n\t"
+        "shl.b32 n0, n1, 16;\n\t"
+        "and.b32 n1, n1, 0xffff0000;\n\t"
+        "mov.b64 na, {n0, n1};\n\t"
+        "fma.rn.f32x2 ra, xa, ya, na;\n\t"
+        "mov.b64 {r0, r1}, ra;\n\t"
+        "cvt.rn.bf16x2.f32 %1, r1, r0;\n\t"
+        "mov.b32 %0, h;\n\t"
+        "}"
+        : "=r"(hi), "=r"(lo)
+        : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
+}
+
 }  // namespace tc
 }  // namespace ps
