@@ -277,7 +277,7 @@ def run_ours(args):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             achieved = useful_flops / (stage["ms_contract"] * 1e-3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": traffic_for("contract_tc", ["contract_tc.cu"]), "kernel": "tc_contract",
+                    "traffic": traffic_for("contract_tc", ["contract_tc.cu", "tc.cuh"]), "kernel": "tc_contract",
                     "peak_source": f"bf16 dense sustained, {peak_src}"}
         else:
             mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -292,7 +292,7 @@ def run_ours(args):
         fields_roof = {"bound": "hbm", "achieved": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9,
                        "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                       "traffic": traffic_for("inv_plane", ["fields.cu", "fft.cuh"]), "kernel": "inv_plane_kernel",
+                       "traffic": traffic_for("inv_plane", ["fields_impl.cuh", "fields_f32.cu", "fft.cuh"]), "kernel": "inv_plane_kernel",
                        "peak_source": peak_src}
         results[prec] = {"value": value, "ms_per_step": total_ms / args.steps, "roofline": roof,
                          "fields_roofline": fields_roof, "stage_ms": stage, "gpu_launches": launches,

@@ -344,21 +344,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             tc::fence_after_sync();
             const uint32_t D = sd0 + (uint32_t)(st * stage_bytes);
-            {
+            // A operand of the first M tile, then this thread's B item (column n, 8-cell group kg ->
+            // one 16-byte core-matrix row of hi and of lo), then the second M tile: the stores of
+            // one row drain while the next registers are formed
+            if (ma < nmt) {
                 uint32_t hi[16], lo[16];
-                if (ma < nmt) {
-                    tc_row_products<RA>(D, ka1, ka2, hi, lo);
-                    tc::tmem_st16(abase + (uint32_t)(ma * 32), hi);
-                    tc::tmem_st16(abase + (uint32_t)(ma * 32 + 16), lo);
-                }
-                if (mb < nmt) {
-                    tc_row_products<RA>(D, kb1, kb2, hi, lo);
-                    tc::tmem_st16(abase + (uint32_t)(mb * 32), hi);
-                    tc::tmem_st16(abase + (uint32_t)(mb * 32 + 16), lo);
-                }
+                tc_row_products<RA>(D, ka1, ka2, hi, lo);
+                tc::tmem_st16(abase + (uint32_t)(ma * 32), hi);
+                tc::tmem_st16(abase + (uint32_t)(ma * 32 + 16), lo);
             }
-            // B operand: (column n, 8-cell group kg) -> one 16-byte core-matrix row of hi and of lo
             if (ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, Bh + b_off, Bl + b_off);
+            if (mb < nmt) {
+                uint32_t hi[16], lo[16];
+                tc_row_products<RA>(D, kb1, kb2, hi, lo);
+                tc::tmem_st16(abase + (uint32_t)(mb * 32), hi);
+                tc::tmem_st16(abase + (uint32_t)(mb * 32 + 16), lo);
+            }
             for (int it = ttid + kTcTeamWarps * 32; it < nbitems; it += kTcTeamWarps * 32) {
                 const int kg = it / ncol, n = it - kg * ncol;
                 const short2 f = s_colf[n];
