@@ -15,13 +15,14 @@
 // cell-tiled field layout) into shared memory with TMA (128-byte swizzle).
 // Team t produces chunks t, t + 2, ... into A/B slot t, so that one team's
 // barrier waits overlap the other team's work.  Producer warp w of a team owns
-// TMEM lane quadrant w % 4 of M tiles 2 (w / 4) and 2 (w / 4) + 1: each lane forms
-// the 32 products of its row in each of the two tiles and writes their hi and lo
-// parts with 16-column tcgen05.st.  The rows of a warp are a block of 8
-// consecutive k1 x 4 consecutive k2, so its shared-memory reads of the factors
-// touch at most 12 distinct rows of the chunk (broadcast loads).  The team then
-// writes the column factors (B operand) into shared memory in the K-major
-// core-matrix layout.  Issuer warp m issues the MMAs of M tile m (operands in
+// TMEM lane quadrant w % 4 and the 16-cell half w / 4 of a chunk: in every M tile
+// of the block, each lane forms the 16 products of its row in its half and
+// writes their hi and lo parts with one 16-column tcgen05.st (per M tile the A
+// slot holds [hi | lo] of cells 0-15, then [hi | lo] of cells 16-31), so the
+// work per chunk is proportional to the number of M tiles.  The rows of a warp
+// come from 8 consecutive k1 and a few consecutive k2, so its shared-memory reads
+// of the factors are bank-conflict-free broadcasts.  The team then writes the
+// column factors (B operand) into shared memory in the K-major core-matrix layout.  Issuer warp m issues the MMAs of M tile m (operands in
 // registers; one elected lane issues and commits).
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -52,7 +53,7 @@ constexpr int kTcAccMax = 256;       // accumulator columns per block
 constexpr int kTcABase = 256;        // first TMEM column of the A operand in the self-test
 constexpr int kTcMaxRunsMt = 4;      // N runs per M tile
 constexpr int kTcMaxCols = 256;      // local B columns per block
-constexpr int kTcRowBlock1 = 8, kTcRowBlock2 = 4;  // pair rows of one producer warp: 8 k1 x 4 k2
+constexpr int kTcRowOctet = 8;       // pair rows of one producer warp come from 8 consecutive k1
 constexpr uint32_t kLBO = 128, kSBO = 512;  // B layout: K-adjacent core matrices, 8-row groups (K = 32)
 
 struct TcMTile {
@@ -124,23 +125,25 @@ __device__ __forceinline__ void tc_b_item(uint32_t D, int key1, int key2, uint32
 __device__ __forceinline__ uint32_t tc_row_key(int k) { return (uint32_t)(k * 128) ^ (uint32_t)((k & 7) * 16); }
 
 template <int RA>
-__device__ __forceinline__ void tc_row_products(uint32_t D, uint32_t key1, uint32_t key2, uint32_t* hi, uint32_t* lo) {
-    // the 32 products of one row for a chunk; column j holds cells 2j, 2j+1
+__device__ __forceinline__ void tc_row_products(uint32_t D, uint32_t key1, uint32_t key2, int half, uint32_t* v) {
+    // the 16 products of one row in cells [16 half, 16 half + 16) of a chunk: v[0..7] = hi,
+    // v[8..15] = lo, column j of each holding cells 16 half + 2j, 16 half + 2j + 1
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
+    for (int c4 = 0; c4 < 4; c4++) {
+        const uint32_t c = (uint32_t)(4 * half + c4);
         float4 x, y;
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w)
-                     : "r"(D + (key1 ^ (uint32_t)(c * 16))));
+                     : "r"(D + (key1 ^ (c * 16u))));
         if (RA == 2) {
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
-                         : "r"(D + (key2 ^ (uint32_t)(c * 16))));
-            tc::split2_prod_x2(x.x, y.x, x.y, y.y, hi[2 * c], lo[2 * c]);
-            tc::split2_prod_x2(x.z, y.z, x.w, y.w, hi[2 * c + 1], lo[2 * c + 1]);
+                         : "r"(D + (key2 ^ (c * 16u))));
+            tc::split2_prod_x2(x.x, y.x, x.y, y.y, v[2 * c4], v[8 + 2 * c4]);
+            tc::split2_prod_x2(x.z, y.z, x.w, y.w, v[2 * c4 + 1], v[8 + 2 * c4 + 1]);
         } else {
-            tc::split2(x.x, x.y, hi[2 * c], lo[2 * c]);
-            tc::split2(x.z, x.w, hi[2 * c + 1], lo[2 * c + 1]);
+            tc::split2(x.x, x.y, v[2 * c4], v[8 + 2 * c4]);
+            tc::split2(x.z, x.w, v[2 * c4 + 1], v[8 + 2 * c4 + 1]);
         }
     }
 }
@@ -264,10 +267,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 const uint32_t bo = r_b[r] + (uint32_t)ks * 2 * kLBO;
                                 const uint64_t dh = desc_k | (uint64_t)(((bh + bo) >> 4) & 0x3FFFu);
                                 const uint64_t dl = desc_k | (uint64_t)(((bl + bo) >> 4) & 0x3FFFu);
-                                const uint32_t ak = a + (uint32_t)(ks * 8);
+                                const uint32_t ak = a + (uint32_t)(ks * 16);  // hi; lo at + 8
                                 tc::mma_ts(r_d[r], ak, dh, r_id[r], ks == 0 ? first : 1u);  // hi x hi
                                 tc::mma_ts(r_d[r], ak, dl, r_id[r], 1u);                    // hi x lo
-                                tc::mma_ts(r_d[r], ak + 16, dh, r_id[r], 1u);               // lo x hi
+                                tc::mma_ts(r_d[r], ak + 8, dh, r_id[r], 1u);                // lo x hi
                             }
                         }
                     }
@@ -306,16 +309,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else {
         // ------------------------------------------------------------- producers
         const int team = warp / kTcTeamWarps, tw = warp % kTcTeamWarps;
-        const int q = tw & 3, mp = tw >> 2;  // lane quadrant, pair of M tiles (2 mp, 2 mp + 1)
+        const int q = tw & 3, half = tw >> 2;  // lane quadrant, 16-cell half of the chunk
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int row = 32 * q + lane;
-        const int ma = 2 * mp, mb = 2 * mp + 1;
-        const short2 fa = s_rowf[ma * 128 + row], fb = s_rowf[mb * 128 + row];  // in-range shells
-        const uint32_t ka1 = tc_row_key(fa.x), ka2 = tc_row_key(RA == 2 ? fa.y : 0);
-        const uint32_t kb1 = tc_row_key(fb.x), kb2 = tc_row_key(RA == 2 ? fb.y : 0);
+        uint32_t key1[kTcMaxMT], key2[kTcMaxMT];  // this lane's row factors in each M tile (in-range shells)
+#pragma unroll
+        for (int m = 0; m < kTcMaxMT; m++) {
+            const short2 f = s_rowf[m * 128 + row];
+            key1[m] = tc_row_key(f.x);
+            key2[m] = tc_row_key(RA == 2 ? f.y : 0);
+        }
         const int ttid = tid % (kTcTeamWarps * 32);
         // slot `team`; stages team, team + 2, team + 4 in turn
-        const uint32_t abase = tmem + lane_base + (uint32_t)a0 + (uint32_t)team * slot_cols;
+        const uint32_t abase = tmem + lane_base + (uint32_t)a0 + (uint32_t)team * slot_cols + (uint32_t)(16 * half);
         const uint32_t Bh = tc::smem_u32(s_b + (2 * team) * bbuf_bytes);
         const uint32_t Bl = tc::smem_u32(s_b + (2 * team + 1) * bbuf_bytes);
         const uint32_t sd0 = tc::smem_u32(s_d);
@@ -344,21 +350,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             tc::fence_after_sync();
             const uint32_t D = sd0 + (uint32_t)(st * stage_bytes);
-            // A operand of the first M tile, then this thread's B item (column n, 8-cell group kg ->
-            // one 16-byte core-matrix row of hi and of lo), then the second M tile: the stores of
-            // one row drain while the next registers are formed
-            if (ma < nmt) {
-                uint32_t hi[16], lo[16];
-                tc_row_products<RA>(D, ka1, ka2, hi, lo);
-                tc::tmem_st16(abase + (uint32_t)(ma * 32), hi);
-                tc::tmem_st16(abase + (uint32_t)(ma * 32 + 16), lo);
-            }
-            if (ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, Bh + b_off, Bl + b_off);
-            if (mb < nmt) {
-                uint32_t hi[16], lo[16];
-                tc_row_products<RA>(D, kb1, kb2, hi, lo);
-                tc::tmem_st16(abase + (uint32_t)(mb * 32), hi);
-                tc::tmem_st16(abase + (uint32_t)(mb * 32 + 16), lo);
+            // A operand: this lane's row in each M tile, cells [16 half, 16 half + 16), hi and lo in one
+            // 16-column store; the B item (column n, 8-cell group kg -> one 16-byte core-matrix row of
+            // hi and of lo) after the first tile, while its stores drain
+#pragma unroll
+            for (int m = 0; m < kTcMaxMT; m++) {
+                if (m < nmt) {
+                    uint32_t v[16];
+                    tc_row_products<RA>(D, key1[m], key2[m], half, v);
+                    tc::tmem_st16(abase + (uint32_t)(m * 32), v);
+                }
+                if (m == 0 && ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, Bh + b_off, Bl + b_off);
             }
             for (int it = ttid + kTcTeamWarps * 32; it < nbitems; it += kTcTeamWarps * 32) {
                 const int kg = it / ncol, n = it - kg * ncol;
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (i == win.end || i == nch - 1) {
                 if (!tc::mbar_wait_warp(acc_ready, (uint32_t)(win.index & 1), s_abort)) break;
                 tc::fence_after_sync();
-                for (int g = mp; g < acc_cols / 16; g += 2) {
+                for (int g = half; g < acc_cols / 16; g += 2) {
                     uint32_t v[16];
                     tc::tmem_ld16(tmem + lane_base + (uint32_t)(g * 16), v);
                     tc::tmem_ld_wait();
@@ -588,43 +590,50 @@ poly_status ps_tc_prepare(PsPlan* p) {
         std::pair<int, int> key;  // shells (from 1) of the row factors; in range also for padding rows
         std::vector<int> cols;    // global column indices, sorted (empty for padding rows)
     };
-    // A producer warp takes 32 rows: pair rows by 8 consecutive k1 x 4 consecutive k2,
-    // single-field rows by 32 consecutive k1.  Lanes without a row repeat an in-range
-    // neighbour (their accumulator rows are never read), so the warp's factor reads stay
-    // within the block's 8 + 4 (or 32) shells.
+    // A producer warp takes 32 rows.  Pair rows: the rows of one octet of 8
+    // consecutive k1, sorted by (k2, k1) and cut in 32s, so that a warp's rows
+    // use at most 8 consecutive k1 and a few consecutive k2 (the factor reads are
+    // bank-conflict-free broadcasts).  Single-field rows: 32 consecutive k1.
+    // Lanes without a row repeat the block's first row (their accumulator rows are
+    // never read).
     const int ns = p->nshell;
-    std::map<std::pair<int, int>, std::vector<Row>> blocks;
+    std::map<int, std::vector<std::pair<std::pair<int, int>, const std::set<std::pair<int, int>>*>>> octets;
     for (auto& kv : rows) {
-        const int k1 = kv.first.first, k2 = kv.first.second;
-        const std::pair<int, int> bk =
-            ra2 ? std::make_pair((k1 - 1) / kTcRowBlock1, (k2 - 1) / kTcRowBlock2) : std::make_pair((k1 - 1) / 32, 0);
-        auto it = blocks.find(bk);
-        if (it == blocks.end()) {
-            std::vector<Row> blk(32);
-            for (int l = 0; l < 32; l++) {
-                blk[l].valid = false;
-                blk[l].key = ra2 ? std::make_pair(std::min(ns, bk.first * kTcRowBlock1 + l / kTcRowBlock2 + 1),
-                                                  std::min(ns, bk.second * kTcRowBlock2 + l % kTcRowBlock2 + 1))
-                                 : std::make_pair(std::min(ns, bk.first * 32 + l + 1), -1);
-            }
-            it = blocks.emplace(bk, std::move(blk)).first;
-        }
-        const int l = ra2 ? ((k1 - 1) % kTcRowBlock1) * kTcRowBlock2 + (k2 - 1) % kTcRowBlock2 : (k1 - 1) % 32;
-        Row& r = it->second[l];
-        r.valid = true;
-        r.key = kv.first;
-        for (auto& c : kv.second) r.cols.push_back(gcol[c]);
-        std::sort(r.cols.begin(), r.cols.end());
+        const int k1 = kv.first.first;
+        octets[ra2 ? (k1 - 1) / kTcRowOctet : (k1 - 1) / 32].push_back({kv.first, &kv.second});
     }
+    std::vector<std::vector<Row>> blocks;
+    for (auto& ov : octets) {
+        auto& lst = ov.second;
+        std::sort(lst.begin(), lst.end(), [](const auto& x, const auto& y) {
+            return std::make_pair(x.first.second, x.first.first) < std::make_pair(y.first.second, y.first.first);
+        });
+        for (size_t t = 0; t < lst.size(); t += 32) {
+            std::vector<Row> blk(32);
+            for (size_t l = 0; l < 32; l++) {
+                if (t + l < lst.size()) {
+                    Row& r = blk[l];
+                    r.valid = true;
+                    r.key = lst[t + l].first;
+                    for (auto& c : *lst[t + l].second) r.cols.push_back(gcol[c]);
+                    std::sort(r.cols.begin(), r.cols.end());
+                } else {
+                    blk[l] = Row{false, lst[t].first, {}};
+                }
+            }
+            blocks.push_back(std::move(blk));
+        }
+    }
+    (void)ns;
     std::vector<std::pair<std::pair<int, int>, const std::vector<Row>*>> bl;  // (column span, block)
-    for (auto& kv : blocks) {
+    for (auto& blk : blocks) {
         int lo = 1 << 30, hi = -1;
-        for (const Row& r : kv.second)
+        for (const Row& r : blk)
             if (r.valid) {
                 lo = std::min(lo, r.cols.front());
                 hi = std::max(hi, r.cols.back());
             }
-        bl.push_back({{lo, hi}, &kv.second});
+        bl.push_back({{lo, hi}, &blk});
     }
     std::stable_sort(bl.begin(), bl.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
     std::vector<Row> rl;
@@ -663,6 +672,8 @@ poly_status ps_tc_prepare(PsPlan* p) {
         }
         return g.acc <= kTcAccMax && (m1 - m0) <= kTcMaxMT;
     };
+    // groups: the fewest that fit, with the M tiles spread evenly over them (each group
+    // pays a fixed per-chunk cost for loading and synchronisation)
     std::vector<GroupPlan> gplans;
     int ngroups = (nmt_total + kTcMaxMT - 1) / kTcMaxMT;
     while (true) {
@@ -743,8 +754,9 @@ poly_status ps_tc_prepare(PsPlan* p) {
         }
         G.acc_cols = acc;
         groups.push_back(G);
-        // per-chunk cost: tensor pipe (3 MMAs x K/16 per 16 accumulator columns) or producers, whichever is longer
-        const double wk = std::max(3.0 * acc, 160.0 * G.nmt + 100.0);
+        // per-chunk cost in cycles: tensor pipe (3 MMAs x K/16 per 16 accumulator columns) or the
+        // producers (a fixed loading and synchronisation cost plus a share per M tile), whichever is longer
+        const double wk = std::max(3.0 * acc, 550.0 + 360.0 * G.nmt);
         gwork.push_back(wk);
         work_cells += wk;
         t->executed_flops_per_cell += 3.0 * 2.0 * 128.0 * acc;
