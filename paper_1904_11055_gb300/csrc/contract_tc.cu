@@ -13,8 +13,10 @@
 // Block layout: 16 producer warps in two teams and 4 issuer warps.  Issuer 0
 // also streams 32-cell chunks of all shell fields (one contiguous block of the
 // cell-tiled field layout) into shared memory with TMA (128-byte swizzle).
-// Team t produces chunks t, t + 2, ... into A/B slot t, so that one team's
-// barrier waits overlap the other team's work.  Producer warp w of a team owns
+// Team t produces chunks t, t + 2, ..., so that one team's barrier waits overlap
+// the other team's work; chunk i goes to A/B slot i mod nslots (3 slots when
+// tensor memory holds them, else 2), so a team reuses a slot only after the
+// MMAs of an earlier chunk than its previous one.  Producer warp w of a team owns
 // TMEM lane quadrant w % 4 and the 16-cell half w / 4 of a chunk: in every M tile
 // of the block, each lane forms the 16 products of its row in its half and
 // writes their hi and lo parts with one 16-column tcgen05.st (per M tile the A
@@ -52,6 +54,7 @@ constexpr int kTcThreads = kTcProducers + 32 * kTcIssuers;
 constexpr int kTcAccMax = 256;       // accumulator columns per block
 constexpr int kTcABase = 256;        // first TMEM column of the A operand in the self-test
 constexpr int kTcMaxRunsMt = 4;      // N runs per M tile
+constexpr int kTcMaxSlots = 3;       // A/B slots
 constexpr int kTcMaxCols = 256;      // local B columns per block
 constexpr int kTcRowOctet = 8;       // pair rows of one producer warp come from 8 consecutive k1
 constexpr uint32_t kLBO = 128, kSBO = 512;  // B layout: K-adjacent core matrices, 8-row groups (K = 32)
@@ -151,7 +154,7 @@ __device__ __forceinline__ void tc_row_products(uint32_t D, uint32_t key1, uint3
 template <int RA, int CA>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_contract_kernel(const __grid_constant__ CUtensorMap fmap, int nshell, int stage_bytes, int bbuf_bytes,
-                       int acc_max, int window, const TcCta* __restrict__ ctas, const TcGroup* __restrict__ groups,
+                       int slot_cap, int acc_max, int window, const TcCta* __restrict__ ctas, const TcGroup* __restrict__ groups,
                        const TcMTile* __restrict__ mtiles, const int4* __restrict__ runs,
                        const short2* __restrict__ rowf, const short2* __restrict__ colf, double* __restrict__ partial,
                        int* __restrict__ err) {
@@ -159,15 +162,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* s_d = base;                                        // kTcStages x stage_bytes (1024-aligned)
     uint8_t* s_b = s_d + kTcStages * stage_bytes;               // [slot][hi, lo] x bbuf_bytes
-    float* s_acc = (float*)(s_b + 4 * bbuf_bytes);              // [acc_max cols][128 rows]
+    float* s_acc = (float*)(s_b + 2 * slot_cap * bbuf_bytes);   // [acc_max cols][128 rows]
     short2* s_rowf = (short2*)(s_acc + (size_t)acc_max * 128);  // [kTcMaxMT][128]
     short2* s_colf = s_rowf + kTcMaxMT * 128;                   // [kTcMaxCols]
     uint64_t* bars = (uint64_t*)(s_colf + kTcMaxCols);
     uint64_t* full = bars;                                      // [kTcStages]
     uint64_t* empty = full + kTcStages;                         // [kTcStages]
-    uint64_t* produced = empty + kTcStages;                     // [2]
-    uint64_t* mma_done = produced + 2;                          // [2]
-    uint64_t* acc_ready = mma_done + 2;
+    uint64_t* produced = empty + kTcStages;                     // [kTcMaxSlots]
+    uint64_t* mma_done = produced + kTcMaxSlots;                // [kTcMaxSlots]
+    uint64_t* acc_ready = mma_done + kTcMaxSlots;
     uint64_t* acc_free = acc_ready + 1;
     uint64_t* drain = acc_free + 1;
     uint32_t* s_tmem = (uint32_t*)(drain + 1);
@@ -179,17 +182,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int nch = (int)(cta.c1 - cta.c0);
     const int nmt = grp.nmt, ncol = grp.ncol, acc_cols = grp.acc_cols;
     constexpr int kProdWarps = kTcProducers / 32;
-    // TMEM columns: accumulators [0, a0), then slot t of team t: nmt x 32 columns (hi 16 + lo 16 per M tile)
+    // TMEM columns: accumulators [0, a0), then the A slots of nmt x 32 columns (hi 16 + lo 16 per M tile)
     const int a0 = (acc_cols + 31) / 32 * 32;
     const uint32_t slot_cols = (uint32_t)(nmt * 32);
+    int nslots = (512 - a0) / (int)slot_cols;
+    nslots = nslots < slot_cap ? nslots : slot_cap;  // >= 2: a0 <= 256 and nmt <= 4
 
     if (tid == 0) {
         for (int st = 0; st < kTcStages; st++) {
             tc::mbar_init(&full[st], 1);
             tc::mbar_init(&empty[st], kTcTeamWarps);
         }
-        for (int b = 0; b < 2; b++) {
-            tc::mbar_init(&produced[b], kTcTeamWarps);
+        for (int b = 0; b < kTcMaxSlots; b++) {
+            tc::mbar_init(&produced[b], kTcTeamWarps);  // one team writes a slot per chunk
             tc::mbar_init(&mma_done[b], nmt);  // one commit per issuer
         }
         tc::mbar_init(acc_ready, nmt);
@@ -246,11 +251,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             TcWindow win(0, window);
             int lst = 0;
             uint32_t lph = 0;  // stage and phase of empty[] that frees the stage for chunk c
+            int slot = 0;
+            uint32_t ph = 0;  // phase of produced[slot] for chunk i
             for (int i = 0; i < nch; i++) {
-                const int slot = i & 1;
                 win.advance_to(i, window);
                 const bool wstart = i == win.end - window + 1;
-                if (!tc::mbar_wait_warp(&produced[slot], (uint32_t)((i >> 1) & 1), s_abort)) break;
+                if (!tc::mbar_wait_warp(&produced[slot], ph, s_abort)) break;
                 if (wstart && win.index > 0 && !tc::mbar_wait_warp(acc_free, (uint32_t)((win.index - 1) & 1), s_abort))
                     break;
                 tc::fence_after_sync();
@@ -292,6 +298,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         lph ^= 1u;
                     }
                 }
+                if (++slot == nslots) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
             }
             // every MMA this issuer started completes before the columns are freed
             if (el && nch > 0) tc::mma_commit(drain);
@@ -320,10 +330,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             key2[m] = tc_row_key(RA == 2 ? f.y : 0);
         }
         const int ttid = tid % (kTcTeamWarps * 32);
-        // slot `team`; stages team, team + 2, team + 4 in turn
-        const uint32_t abase = tmem + lane_base + (uint32_t)a0 + (uint32_t)team * slot_cols + (uint32_t)(16 * half);
-        const uint32_t Bh = tc::smem_u32(s_b + (2 * team) * bbuf_bytes);
-        const uint32_t Bl = tc::smem_u32(s_b + (2 * team + 1) * bbuf_bytes);
+        // stages team, team + 2, team + 4 in turn; slots i mod nslots
+        const uint32_t abase0 = tmem + lane_base + (uint32_t)a0 + (uint32_t)(16 * half);
+        const uint32_t Bbase = tc::smem_u32(s_b);
         const uint32_t sd0 = tc::smem_u32(s_d);
         // this thread's first B item (column n, 8-cell group kg), fixed for every chunk
         const int nbitems = ncol * (kTcChunk / 8);
@@ -339,15 +348,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             b_off = (uint32_t)(n / 8) * kSBO + (uint32_t)kg * kLBO + (uint32_t)(n % 8) * 16;
         }
         int st = team;
-        uint32_t ph_full = 0, ph_md = 0;
+        uint32_t ph_full = 0;
         TcWindow win(team, window);
         for (int i = team; i < nch; i += 2) {
             if (!tc::mbar_wait_warp(&full[st], ph_full, s_abort)) break;
-            if (i >= 2) {
-                // the MMAs of this team's previous chunk have read the slot
-                if (!tc::mbar_wait_warp(&mma_done[team], ph_md, s_abort)) break;
-                ph_md ^= 1u;
+            const int slot = i % nslots, use = i / nslots;  // slot and its use count
+            if (use > 0) {
+                // the MMAs of chunk i - nslots have read the slot
+                if (!tc::mbar_wait_warp(&mma_done[slot], (uint32_t)((use - 1) & 1), s_abort)) break;
             }
+            const uint32_t abase = abase0 + (uint32_t)slot * slot_cols;
+            const uint32_t Bh = Bbase + (uint32_t)(2 * slot * bbuf_bytes);
+            const uint32_t Bl = Bh + (uint32_t)bbuf_bytes;
             tc::fence_after_sync();
             const uint32_t D = sd0 + (uint32_t)(st * stage_bytes);
             // A operand: this lane's row in each M tile, cells [16 half, 16 half + 16), hi and lo in one
@@ -376,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             __syncwarp();
             if (lane == 0) {
                 tc::mbar_arrive(&empty[st]);
-                tc::mbar_arrive(&produced[team]);
+                tc::mbar_arrive(&produced[slot]);
             }
             st += 2;
             if (st >= kTcStages) {
@@ -512,7 +524,7 @@ struct TcState {
     int nshell = 0;
     int stage_bytes = 0, bbuf_bytes = 0, smem_bytes = 0;
     int window = 64;
-    int acc_max = 256;
+    int acc_max = 256, slot_cap = 2;
     int ra = 2, ca = 1;
     void *d_ctas = nullptr, *d_groups = nullptr, *d_mtiles = nullptr, *d_runs = nullptr, *d_rowf = nullptr,
          *d_colf = nullptr, *d_binmap = nullptr;
@@ -536,7 +548,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 static size_t tc_smem_bytes(int stage_bytes, int bbuf_bytes, int slots, int acc_max) {
     return 1024 + (size_t)kTcStages * stage_bytes + 2 * (size_t)slots * bbuf_bytes + (size_t)acc_max * 128 * 4 +
-           kTcMaxMT * 128 * 4 + kTcMaxCols * 4 + (2 * kTcStages + 11) * 8 + 64;
+           kTcMaxMT * 128 * 4 + kTcMaxCols * 4 + (2 * kTcStages + 2 * kTcMaxSlots + 3) * 8 + 64;
 }
 
 // Sorted 16-column blocks of one M tile -> runs (first block, block count), at most
@@ -827,7 +839,10 @@ poly_status ps_tc_prepare(PsPlan* p) {
     }
     t->bbuf_bytes = maxcol * kTcChunk * 2;
     t->acc_max = maxacc;
-    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, 2, maxacc);
+    t->slot_cap = kTcMaxSlots;  // B slots: as many as shared memory holds (the kernel also bounds them by TMEM)
+    while (t->slot_cap > 2 && tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc) > 227 * 1024)
+        t->slot_cap--;
+    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc);
     if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
     const char* w = getenv("POLY_TC_WINDOW");
     if (w && atoi(w) > 0) t->window = atoi(w);
@@ -842,7 +857,7 @@ poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {
         cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t->smem_bytes);
         if (e2) return e2;
         kern<<<(unsigned)t->ctas.size(), kTcThreads, t->smem_bytes, st>>>(
-            t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->acc_max, t->window, (const TcCta*)t->d_ctas,
+            t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->slot_cap, t->acc_max, t->window, (const TcCta*)t->d_ctas,
             (const TcGroup*)t->d_groups, (const TcMTile*)t->d_mtiles, (const int4*)t->d_runs,
             (const short2*)t->d_rowf, (const short2*)t->d_colf, t->d_partial, t->d_err);
         return cudaGetLastError();
