@@ -256,11 +256,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1) inv_plane_kernel(
     const int s = s0 + blockIdx.y;
     Cx<T>* Hb = SPILL ? spill + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (size_t)(K + 1) * ls : s_h;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int s_kzmax;
+    const int lb = line_off[s], le = line_off[s + 1];
+    // the shell's largest kz: kz lines above it stay zero through the y pass and are skipped
+    if (threadIdx.x == 0) s_kzmax = 0;
     load_twiddles(s_tw, g_tw, N);
-    for (int e = threadIdx.x; e < (K + 1) * ls; e += blockDim.x) Hb[e] = cx<T>(0, 0);
+    __syncthreads();
+    {
+        int kzm = 0;
+        for (int li = lb + threadIdx.x; li < le; li += blockDim.x) kzm = max(kzm, (int)lines[li].y);
+        if (kzm > 0) atomicMax(&s_kzmax, kzm);
+    }
+    __syncthreads();
+    const int Ks = s_kzmax;
+    for (int e = threadIdx.x; e < (Ks + 1) * ls; e += blockDim.x) Hb[e] = cx<T>(0, 0);
     __syncthreads();
 
-    const int lb = line_off[s], le = line_off[s + 1];
     if (XPRE) {
         // the x pass already transformed each line: scatter this plane's values
         const Cx<T>* Tx = xpre + (size_t)lb * N + (size_t)x * (le - lb);
@@ -311,10 +322,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) inv_plane_kernel(
         Hb[(size_t)kz * ls + pad_idx<T>((ky + N) % N)] = cx<T>(sr, si);
     }
     __syncthreads();
-    // DFT along y of the K+1 kz lines
-    for (int g = warp * LPW; g <= K; g += WARPS * LPW) {
+    // DFT along y of the Ks + 1 kz lines
+    for (int g = warp * LPW; g <= Ks; g += WARPS * LPW) {
         SmemLines<T> hb{Hb + (size_t)g * ls, ls};
-        warp_fft_inplace<T, N, +1>(hb, min(LPW, K + 1 - g), s_tw, lane);
+        warp_fft_inplace<T, N, +1>(hb, min(LPW, Ks + 1 - g), s_tw, lane);
     }
     __syncthreads();
     // real transform along z, two rows per complex line, written straight to global
@@ -323,7 +334,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) inv_plane_kernel(
     const int npairs = (N + 1) / 2;
     for (int p0 = warp * LPW; p0 < npairs; p0 += WARPS * LPW) {
         const int nl = min(LPW, npairs - p0);
-        HalfPairReader<T> rd{Hb, ls, K, N, 2 * p0};
+        HalfPairReader<T> rd{Hb, ls, Ks, N, 2 * p0};
         RowPairWriter<T> wr{plane, out, 2 * p0, N, x, s, tile_ns};
         warp_fft<T, N, +1>(zb, nl, s_tw, lane, rd, wr);
     }

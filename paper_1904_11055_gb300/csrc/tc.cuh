@@ -135,6 +135,17 @@ PS_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Non-blocking test of phase `parity` (acquire when it returns true).
+PS_DEV bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, "
+        "p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Wait for phase `parity` of `bar`, giving up after the clock budget or when
 // another thread has raised *abort.  Returns false on give-up.
 PS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
