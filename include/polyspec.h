@@ -118,13 +118,41 @@ poly_status poly_estimate_host(poly_plan plan, const void* delta_x_host, double*
 poly_status poly_backward(poly_plan plan, const void* delta_x, const double* dL_dB, void* dL_ddelta, void* stream);
 
 /*
- * Estimate `count` fields, possibly of different plans (e.g. different grid
- * sizes), in one stream-ordered batch: fields[i] is a device pointer for
- * plans[i] and outs[i] a device array of plans[i]'s nbins doubles.  Results
- * are bit-identical to calling poly_estimate on each field.
+ * Estimate `count` fields, possibly of different plans (e.g. mock catalogues
+ * on different grid sizes), in one stream-ordered batch: fields[i] is a device
+ * pointer for plans[i] and outs[i] a device array of plans[i]'s nbins doubles.
+ * Results are bit-identical to calling poly_estimate on each field.
+ *
+ * The first call with a given (plans, fields, outs) list captures all the
+ * launches into one CUDA graph, which later calls with the same list replay
+ * with a single launch (the library keeps the 8 most recently used graphs).
+ * Fields of one plan run in order on one branch of the graph (they share the
+ * plan's workspace); different plans run on parallel branches.  A cached graph
+ * reads the fields and writes the outputs at the addresses it was captured
+ * with, so keep those buffers alive (or pass a new list); destroying or
+ * retuning a plan drops the graphs that use it.  Calls with the same list
+ * from several host threads at once are not supported.
  */
 poly_status poly_estimate_batched(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
                                   void* stream);
+
+/*
+ * Autotuner for the plan's contraction shape (no counterpart in the paper).
+ * For a POLY_SPLIT_BF16 plan it times the tensor-core contraction on the
+ * shell fields of delta_x (device, N^3 float) for each candidate shape:
+ * at most 2, 3 or 4 M tiles per CTA group, and a CTA budget of 1/2, 1 or 2
+ * times the SM count.  The plan keeps the fastest.  config_out receives an
+ * opaque code for it (give it to poly_plan_set_config to restore the choice
+ * without timing, e.g. from a cache on disk) and ms_out the contraction time
+ * it measured.  Other precisions have nothing to tune: config 0, 0 ms.
+ * Synchronises `stream`.  Results after tuning differ from the untuned plan
+ * only in the order of the final FP64 sums (last bits); repeated estimates of
+ * one tuned plan are bit-identical.
+ */
+poly_status poly_plan_tune(poly_plan plan, const void* delta_x, int* config_out, double* ms_out, void* stream);
+
+/* Apply a configuration code from poly_plan_tune (0: keep the current one). */
+poly_status poly_plan_set_config(poly_plan plan, int config);
 
 /* Wait for the plan's work on `stream` and report device-side errors. */
 poly_status poly_plan_sync(poly_plan plan, void* stream);

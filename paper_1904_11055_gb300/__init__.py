@@ -31,7 +31,7 @@ POLY_ALLOW_ALIAS = 0x2
 ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_plan_counts", "poly_estimate",
                "poly_estimate_host", "poly_backward", "poly_estimate_batched", "poly_plan_sync", "poly_plan_destroy",
                "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
-               "poly_plan_stats", "poly_estimate_noalloc")
+               "poly_plan_stats", "poly_estimate_noalloc", "poly_plan_tune", "poly_plan_set_config")
 
 
 class poly_stats(ctypes.Structure):
@@ -73,6 +73,8 @@ def load_library():
     L.poly_plan_set_timing.argtypes = [P, i32]
     L.poly_plan_stats.argtypes = [P, ctypes.POINTER(poly_stats)]
     L.poly_estimate_noalloc.argtypes = [i32, f64, i32, P, P, P, P, P]
+    L.poly_plan_tune.argtypes = [P, P, ctypes.POINTER(i32), ctypes.POINTER(f64), P]
+    L.poly_plan_set_config.argtypes = [P, i32]
     L.poly_debug_fail_alloc_after.argtypes = [i32]
     L.poly_debug_fail_alloc_after.restype = None
     for name in ABI_SYMBOLS:
@@ -138,6 +140,17 @@ def poly_estimate_batched(plans, field_ptrs, out_ptrs, stream: int | None) -> No
 
 def poly_plan_sync(plan: int, stream: int | None = None) -> None:
     _check(load_library().poly_plan_sync(plan, stream), "poly_plan_sync")
+
+
+def poly_plan_tune(plan: int, delta_ptr: int, stream: int | None = None) -> tuple[int, float]:
+    cfg, ms = ctypes.c_int(), ctypes.c_double()
+    _check(load_library().poly_plan_tune(plan, delta_ptr, ctypes.byref(cfg), ctypes.byref(ms), stream),
+           "poly_plan_tune")
+    return cfg.value, ms.value
+
+
+def poly_plan_set_config(plan: int, config: int) -> None:
+    _check(load_library().poly_plan_set_config(plan, int(config)), "poly_plan_set_config")
 
 
 def poly_plan_destroy(plan: int) -> None:
@@ -229,6 +242,21 @@ class Plan:
     def sync(self, stream=None):
         poly_plan_sync(self.handle, _stream_handle(stream))
 
+    def tune(self, delta, stream=None) -> tuple[int, float]:
+        """Time the contraction shapes on this field's shells; keep the fastest (returns code, ms)."""
+        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
+        return poly_plan_tune(self.handle, delta.data_ptr(), _stream_handle(stream))
+
+    def set_config(self, config: int) -> None:
+        poly_plan_set_config(self.handle, config)
+
+    def signature(self) -> str:
+        """Key for a tuning cache: everything the contraction shape depends on, plus the GPU model."""
+        import torch
+
+        e = ",".join(f"{v:.17g}" for v in self.edges)
+        return f"{torch.cuda.get_device_name()}|N={self.N}|n={self.order}|p={self.prec}|f={self.flags}|e={e}"
+
     def close(self):
         if getattr(self, "handle", None):
             poly_plan_destroy(self.handle)
@@ -250,6 +278,26 @@ def estimate_batched(plans, fields, outs=None, stream=None):
     poly_estimate_batched([p.handle for p in plans], [f.data_ptr() for f in fields], [o.data_ptr() for o in outs],
                           _stream_handle(stream))
     return outs
+
+
+def autotune(plan: Plan, delta, cache_path: str | None = None) -> int:
+    """Tune plan on delta, or restore the choice recorded for the same signature in cache_path (JSON)."""
+    import json
+
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    key = plan.signature()
+    if key in cache:
+        plan.set_config(int(cache[key]["config"]))
+        return int(cache[key]["config"])
+    cfg, ms = plan.tune(delta)
+    if cache_path:
+        cache[key] = {"config": cfg, "contract_ms": ms}
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return cfg
 
 
 def _make_function():

@@ -587,6 +587,7 @@ poly_status ps_tc_prepare(PsPlan* p) {
     t->ca = n - t->ra;
     t->nshell = p->nshell;
     const bool ra2 = t->ra == 2;
+    const int max_mt = std::max(1, std::min(kTcMaxMT, p->tc_max_mt));  // M tiles per group (tunable)
     auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra2 ? b[1] : -1); };
     auto ckey = [&](const int32_t* b) { return std::make_pair(b[t->ra], t->ca == 2 ? b[t->ra + 1] : -1); };
     std::map<std::pair<int, int>, std::set<std::pair<int, int>>> rows;
@@ -682,12 +683,12 @@ poly_status ps_tc_prepare(PsPlan* p) {
             for (int c : mt_cols(m)) cb.insert(lidx[c] / 16);
             for (auto& rr : tc_runs(cb)) g.acc += 16 * rr.second;
         }
-        return g.acc <= kTcAccMax && (m1 - m0) <= kTcMaxMT;
+        return g.acc <= kTcAccMax && (m1 - m0) <= max_mt;
     };
     // groups: the fewest that fit, with the M tiles spread evenly over them (each group
     // pays a fixed per-chunk cost for loading and synchronisation)
     std::vector<GroupPlan> gplans;
-    int ngroups = (nmt_total + kTcMaxMT - 1) / kTcMaxMT;
+    int ngroups = (nmt_total + max_mt - 1) / max_mt;
     while (true) {
         gplans.clear();
         bool ok = true;
@@ -776,7 +777,7 @@ poly_status ps_tc_prepare(PsPlan* p) {
     // blocks: split each group's chunks in proportion to its work
     const int64_t ncell = (int64_t)p->N * p->N * p->N;
     const int64_t nchunks = (ncell + kTcChunk - 1) / kTcChunk;
-    const int budget = std::max(p->sms, t->ngroups);
+    const int budget = std::max(p->sms * p->tc_cta_mult / 2, t->ngroups);
     std::vector<int> nsplit(t->ngroups);
     int used = 0;
     for (int g = 0; g < t->ngroups; g++) {
@@ -874,6 +875,11 @@ poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {
 }
 
 void ps_tc_free(PsPlan* p) {
+    if (TcState* t = p->tc) {
+        for (void* d : {t->d_ctas, t->d_groups, t->d_mtiles, t->d_runs, t->d_rowf, t->d_colf, t->d_binmap,
+                        (void*)t->d_partial, (void*)t->d_err})
+            ps_free(p, d);
+    }
     delete p->tc;
     p->tc = nullptr;
 }

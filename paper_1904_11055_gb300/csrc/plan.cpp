@@ -84,6 +84,15 @@ poly_status ps_alloc(PsPlan* p, void** ptr, size_t bytes) {
     return POLY_OK;
 }
 
+void ps_free(PsPlan* p, void* ptr) {
+    if (!ptr) return;
+    auto it = std::find(p->allocations.begin(), p->allocations.end(), ptr);
+    if (it != p->allocations.end()) {
+        cudaFree(ptr);
+        p->allocations.erase(it);
+    }
+}
+
 template <typename V>
 static poly_status upload(PsPlan* p, void** dptr, const std::vector<V>& h) {
     PS_TRY(ps_alloc(p, dptr, h.size() * sizeof(V)));
@@ -356,6 +365,7 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 static void free_plan(PsPlan* p) {
     if (!p) return;
+    ps_batched_forget(p);
     int cur = -1;
     cudaGetDevice(&cur);
     if (p->device >= 0 && cur != p->device) cudaSetDevice(p->device);
@@ -688,6 +698,90 @@ poly_status poly_plan_set_timing(poly_plan p, int enable) {
     p->timing = enable != 0;
     p->ev_recorded = false;
     return POLY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tunable shape of the tensor-core contraction
+// ---------------------------------------------------------------------------
+static poly_status apply_tc_config(PsPlan* p, int max_mt, int cta_mult) {
+    p->tc_max_mt = max_mt;
+    p->tc_cta_mult = cta_mult;
+    ps_batched_forget(p);  // cached graphs hold the old tables
+    ps_tc_free(p);
+    return ps_tc_prepare(p);
+}
+
+static bool decode_config(int config, int* max_mt, int* cta_mult) {
+    *max_mt = config & 15;
+    *cta_mult = (config >> 4) & 15;
+    return *max_mt >= 1 && *max_mt <= 4 && (*cta_mult == 1 || *cta_mult == 2 || *cta_mult == 4) && (config >> 8) == 0;
+}
+
+poly_status poly_plan_tune(poly_plan p, const void* delta_x, int* config_out, double* ms_out, void* stream) {
+    if (!p || !delta_x || !config_out || !ms_out) return set_error(POLY_ERR_ARG, "NULL argument");
+    *config_out = 0;
+    *ms_out = 0;
+    if (p->prec != POLY_SPLIT_BF16) return POLY_OK;  // only the tensor-core contraction has a tunable shape
+    int prev;
+    PS_TRY(enter(p, &prev));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool timing = p->timing;
+    p->timing = false;
+    const int old_mt = p->tc_max_mt, old_mult = p->tc_cta_mult;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    poly_status s = ps_fields(p, delta_x, st);
+    if (!s && (cudaEventCreate(&e0) || cudaEventCreate(&e1))) s = set_error(POLY_ERR_CUDA, "cudaEventCreate");
+    float best = -1.f;
+    int best_mt = old_mt, best_mult = old_mult;
+    for (int mt = 2; mt <= 4 && !s; mt++)
+        for (int mult : {1, 2, 4}) {
+            if (s) break;
+            poly_status a = apply_tc_config(p, mt, mult);
+            if (a == POLY_ERR_UNSUPPORTED) continue;  // this grouping does not fit
+            if (a) {
+                s = a;
+                break;
+            }
+            cudaError_t e = cudaSuccess;
+            if ((s = ps_tc_sums(p, st))) break;  // warm-up
+            if ((e = cudaEventRecord(e0, st))) s = cuda_error(e, "cudaEventRecord");
+            for (int r = 0; r < 3 && !s; r++) s = ps_tc_sums(p, st);
+            if (!s && (e = cudaEventRecord(e1, st))) s = cuda_error(e, "cudaEventRecord");
+            if (!s && (e = cudaEventSynchronize(e1))) s = cuda_error(e, "cudaEventSynchronize");
+            if (!s) s = ps_check_device_error(p);
+            float ms = 0.f;
+            if (!s) cudaEventElapsedTime(&ms, e0, e1);
+            if (!s && (best < 0 || ms < best)) {
+                best = ms;
+                best_mt = mt;
+                best_mult = mult;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    poly_status a = apply_tc_config(p, s ? old_mt : best_mt, s ? old_mult : best_mult);
+    if (!s) s = a;
+    p->timing = timing;
+    if (!s) {
+        *config_out = best_mt | (best_mult << 4);
+        *ms_out = best / 3.0;
+    }
+    leave(p, prev);
+    return s;
+}
+
+poly_status poly_plan_set_config(poly_plan p, int config) {
+    if (!p) return set_error(POLY_ERR_ARG, "NULL plan");
+    if (config == 0) return POLY_OK;
+    int mt, mult;
+    if (!decode_config(config, &mt, &mult)) return set_error(POLY_ERR_ARG, "not a configuration from poly_plan_tune");
+    if (p->prec != POLY_SPLIT_BF16) return POLY_OK;
+    if (mt == p->tc_max_mt && mult == p->tc_cta_mult) return POLY_OK;
+    int prev;
+    PS_TRY(enter(p, &prev));
+    poly_status s = apply_tc_config(p, mt, mult);
+    leave(p, prev);
+    return s;
 }
 
 poly_status poly_plan_stats(poly_plan p, poly_stats* out) {

@@ -65,8 +65,10 @@ struct poly_plan_s {
     void* d_G = nullptr;      // nshell x N^3 real
     void* d_ghat = nullptr;   // union spectrum
     AdjTables* adj = nullptr;
-    // tensor-core contraction
+    // tensor-core contraction: state, and its tunable shape (poly_plan_tune)
     TcState* tc = nullptr;
+    int tc_max_mt = 4;    // largest number of M tiles per CTA group
+    int tc_cta_mult = 2;  // CTA budget = SM count x tc_cta_mult / 2
     // instrumentation
     int64_t launches = 0;
     bool timing = false;
@@ -78,6 +80,7 @@ struct poly_plan_s {
 typedef poly_plan_s PsPlan;
 
 poly_status ps_alloc(PsPlan* p, void** ptr, size_t bytes);
+void ps_free(PsPlan* p, void* ptr);  // frees one allocation made by ps_alloc (NULL: no-op)
 void ps_set_last_error(const std::string& msg);
 // host-side tables (plan.cpp)
 void enumerate_bins(int nshell, const std::vector<double>& edges, int order, bool all_sorted, std::vector<int32_t>& out);
@@ -97,8 +100,10 @@ void ps_tc_free(PsPlan* p);
 double ps_tc_executed_flops(const PsPlan* p);
 poly_status ps_check_device_error(PsPlan* p);
 
-// adjoint.cu / batched
+// adjoint.cu
 void ps_adj_free(PsPlan* p);
 poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, void* dL_ddelta, cudaStream_t st);
+// batched.cpp
 poly_status ps_batched_impl(const poly_plan* plans, const void* const* fields, double* const* outs, int count,
                             cudaStream_t st);
+void ps_batched_forget(const PsPlan* p);  // drop cached graphs that use p

@@ -80,6 +80,17 @@ def test_null_plan_is_rejected(lib):
     lib.poly_plan_destroy(None)
 
 
+def test_tuning_and_batched_entries_reject_null_arguments(lib):
+    import ctypes
+
+    cfg, ms = ctypes.c_int(), ctypes.c_double()
+    assert lib.poly_plan_tune(None, None, ctypes.byref(cfg), ctypes.byref(ms), None) == 1
+    assert lib.poly_plan_set_config(None, 0) == 1
+    assert lib.poly_estimate_batched(None, None, None, 0, None) == 0  # an empty batch is a no-op
+    assert lib.poly_estimate_batched(None, None, None, 2, None) == 1
+    assert lib.poly_estimate_batched(None, None, None, -1, None) == 1
+
+
 def test_binding_wrappers_marshal_without_a_device(lib):
     """Every ABI-named wrapper reaches the library and maps a NULL plan to POLY_ERR_ARG."""
     calls = [
