@@ -28,17 +28,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "bispectrum configs/s at 256³ N_max=64, split-BF16 vs FP32 on GB300 at rel err ≤1e-5"
-N, L, NSHELL, ORDER, SEED = 256, 1000.0, 64, 3, 2
+N, L, NSHELL, ORDER, SEED, WIDTH = 256, 1000.0, 64, 3, 2, 1.0
 WORKLOAD = "bispectrum, 256^3 lognormal field (seed 2), 64 unit shells k_F..64k_F, n=3, 24432 bins"
 
 
-def set_workload(n: int, nshell: int, order: int):
+def set_workload(n: int, nshell: int, order: int, width: float = 1.0):
     """Other sizes (profiling cases, trispectrum); the default is the metric's workload."""
-    global N, NSHELL, ORDER, WORKLOAD
-    if (n, nshell, order) == (N, NSHELL, ORDER):
+    global N, NSHELL, ORDER, WORKLOAD, WIDTH
+    if (n, nshell, order, width) == (N, NSHELL, ORDER, WIDTH):
         return
-    N, NSHELL, ORDER = n, nshell, order
-    WORKLOAD = f"order-{order} polyspectrum, {n}^3 lognormal field (seed 2), {nshell} unit shells (not the metric workload)"
+    N, NSHELL, ORDER, WIDTH = n, nshell, order, width
+    WORKLOAD = (f"order-{order} polyspectrum, {n}^3 lognormal field (seed 2), {nshell} shells of width {width:g} k_F "
+                f"(not the metric workload)")
 SAMPLE_SHELLS = (59, 60, 61, 62, 63, 64)  # CPU baseline sample: the bins among these shells
 
 
@@ -135,7 +136,7 @@ def cpu_baseline(delta_f32):
 
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    edges = fieldgen.unit_edges(NSHELL)
+    edges = fieldgen.unit_edges(NSHELL, WIDTH)
     allb = oracle.enumerate_bins(edges, ORDER)
     sel = np.array([i for i, b in enumerate(allb) if set(b.tolist()) <= set(SAMPLE_SHELLS)])
     t0 = time.perf_counter()
@@ -157,7 +158,7 @@ def run_reference(args):
 
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    edges = fieldgen.unit_edges(NSHELL)
+    edges = fieldgen.unit_edges(NSHELL, WIDTH)
     delta = fieldgen.field("lognormal", N, SEED, np.float32).astype(np.float64)
     allb = oracle.enumerate_bins(edges, ORDER)
     shells = (63, 64)  # per step: the 4 bins among the two outermost shells (keeps K steps within minutes)
@@ -237,7 +238,7 @@ def run_ours(args):
     delta_np = fieldgen.field("lognormal", N, SEED + rank, np.float32)
     d = torch.from_numpy(delta_np).cuda()
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
-    edges = fieldgen.unit_edges(NSHELL)
+    edges = fieldgen.unit_edges(NSHELL, WIDTH)
 
     precisions = [args.precision] if args.precision != "auto" else ["split_bf16", "fp32"]
     results = {}
@@ -416,10 +417,11 @@ def main():
     ap.add_argument("--N", type=int, default=N, help="grid size (default: the metric workload)")
     ap.add_argument("--nshell", type=int, default=NSHELL)
     ap.add_argument("--order", type=int, default=ORDER)
+    ap.add_argument("--width", type=float, default=1.0, help="shell width in k_F (the trispectrum workload: 1.5)")
     ap.add_argument("--workload", default="metric", choices=["metric", "mocks"],
                     help="mocks: 512 mixed-size realisations through poly_estimate_batched")
     args = ap.parse_args()
-    set_workload(args.N, args.nshell, args.order)
+    set_workload(args.N, args.nshell, args.order, args.width)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -65,6 +65,7 @@ def _load():
         L.orc_product_sums.argtypes = [i32, P, P, i32, i64, P, P, P]
         L.orc_estimate.argtypes = [i32, f64, P, i32, P, i32, i64, P, P, P, P, P, P, P]
         L.orc_direct_sample.argtypes = [i32, P, i32, P, i32, i64, P, P, P]
+        L.orc_counts_exact.argtypes = [i32, i32, P, i32, i64, P, P]
         L.orc_gradient.argtypes = [i32, f64, P, i32, P, i32, i64, P, P, P, P]
         _lib = L
     return _lib
@@ -171,6 +172,15 @@ def direct_sample(delta, edges, order: int, bins, N: int | None = None):
     d = np.ascontiguousarray(delta, dtype=np.float64)
     _check(_load().orc_direct_sample(d.shape[0], _p(d), e.size - 1, _p(e), order, nb, _p(b), _p(S), _p(cnt)))
     return S, cnt
+
+
+def counts_exact(N: int, edges, order: int, bins) -> np.ndarray:
+    """Exact polygon counts (n = 2, 3, 4) by integer pair convolutions of the shell indicators."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    b = np.ascontiguousarray(bins, dtype=np.int32)
+    cnt = np.empty(b.shape[0], dtype=np.int64)
+    _check(_load().orc_counts_exact(int(N), e.size - 1, _p(e), int(order), b.shape[0], _p(b), _p(cnt)))
+    return cnt
 
 
 def gradient(delta, L: float, edges, order: int, bins, counts, dLdB) -> np.ndarray:

@@ -383,6 +383,147 @@ int orc_product_sums(int N, const double* fields, const int32_t* slot, int order
 }
 
 /* ------------------------------------------------------------------------- */
+/* exact polygon counts by pair convolutions, n = 2, 3, 4: the plain          */
+/* definition (App. A), the number of n-tuples of grid modes q_t in shell k_t */
+/* with q_1 + ... + q_n = 0 (mod N).  With                                    */
+/*   P_ij(p) = #{(q, q') in S_i x S_j : q + q' = p (mod N)}                   */
+/*           = round(IDFT(DFT(1_Si) DFT(1_Sj))(p) / N^3),                     */
+/* integers of at most |S_i||S_j| (far below 2^52, so the FP64 transforms     */
+/* round to them exactly; each is checked to lie within 1e-3 of one):         */
+/*   n = 2: count = sum_p 1_S1(p) 1_S2(-p)                                    */
+/*   n = 3: count = sum_p P_12(p) 1_S3(-p)                                    */
+/*   n = 4: count = sum_p P_12(p) P_34(-p)                                    */
+/* summed in 64-bit integers.  Shell numbers in `bins` are 1-based.           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int N, ka, kb;
+    const int32_t* smap;
+    const int32_t* pa; /* NULL: the indicator of shell ka */
+    const int32_t* pb; /* NULL: the indicator of shell kb */
+    int64_t part[256];
+} cnt_ctx;
+
+static void count_range(void* vctx, int64_t begin, int64_t end, int tid) {
+    cnt_ctx* c = (cnt_ctx*)vctx;
+    const int N = c->N;
+    int64_t acc = 0;
+    for (int64_t i = begin; i < end; i++) {
+        const int a = (int)(i / ((int64_t)N * N)), b = (int)((i / N) % N), z = (int)(i % N);
+        const int64_t j = ((int64_t)((N - a) % N) * N + (N - b) % N) * N + (N - z) % N; /* -p */
+        const int64_t va = c->pa ? c->pa[i] : (c->smap[i] == c->ka);
+        if (!va) continue;
+        const int64_t vb = c->pb ? c->pb[j] : (c->smap[j] == c->kb);
+        acc += va * vb;
+    }
+    c->part[tid] = acc;
+}
+
+static int64_t count_sum(int N, const int32_t* smap, const int32_t* pa, int ka, const int32_t* pb, int kb) {
+    cnt_ctx c;
+    memset(&c, 0, sizeof c);
+    c.N = N;
+    c.ka = ka;
+    c.kb = kb;
+    c.smap = smap;
+    c.pa = pa;
+    c.pb = pb;
+    par_for((int64_t)N * N * N, count_range, &c);
+    int64_t s = 0;
+    for (int t = 0; t < 256; t++) s += c.part[t];
+    return s;
+}
+
+/* DFT of the indicator of shell k (0-based), interleaved complex */
+static int shell_dft(int N, const int32_t* smap, int k, double* F) {
+    const size_t n3 = (size_t)N * N * N;
+    for (size_t i = 0; i < n3; i++) {
+        F[2 * i] = smap[i] == k ? 1.0 : 0.0;
+        F[2 * i + 1] = 0.0;
+    }
+    return orc_fft3d(F, N, N, N, -1);
+}
+
+static int pair_conv(int N, const double* Fa, const double* Fb, double* work, int32_t* out) {
+    const size_t n3 = (size_t)N * N * N;
+    for (size_t i = 0; i < n3; i++) {
+        const double ar = Fa[2 * i], ai = Fa[2 * i + 1], br = Fb[2 * i], bi = Fb[2 * i + 1];
+        work[2 * i] = ar * br - ai * bi;
+        work[2 * i + 1] = ar * bi + ai * br;
+    }
+    int rc = orc_fft3d(work, N, N, N, +1);
+    if (rc) return rc;
+    for (size_t i = 0; i < n3; i++) {
+        const double v = work[2 * i] / (double)n3, r = nearbyint(v);
+        if (fabs(v - r) > 1e-3 || fabs(work[2 * i + 1] / (double)n3) > 1e-3)
+            return fail(-3, "orc_counts_exact: pair convolution is not an integer");
+        out[i] = (int32_t)r;
+    }
+    return 0;
+}
+
+int orc_counts_exact(int N, int nshell, const double* edges, int order, int64_t nbins, const int32_t* bins,
+                     int64_t* counts) {
+    if (N < 2 || order < 2 || order > 4 || nbins < 0) return fail(-1, "orc_counts_exact: bad args (order 2..4)");
+    const size_t n3 = (size_t)N * N * N;
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    if (!smap) return fail(-2, "orc_counts_exact: out of memory");
+    int rc = orc_shell_map(N, nshell, edges, smap);
+    /* shells whose DFT is needed: the members of every pair (k1, k2) and, for n = 4, (k3, k4) */
+    int* fslot = (int*)malloc(sizeof(int) * (size_t)(nshell + 1));
+    int* pslot = (int*)malloc(sizeof(int) * (size_t)(nshell + 1) * (size_t)(nshell + 1));
+    int nf = 0, np = 0;
+    for (int s = 0; s <= nshell; s++) fslot[s] = -1;
+    for (int64_t i = 0; i < (int64_t)(nshell + 1) * (nshell + 1); i++) pslot[i] = -1;
+    for (int64_t b = 0; b < nbins && !rc; b++) {
+        const int32_t* k = bins + b * order;
+        for (int t = 0; t < order; t++)
+            if (k[t] < 1 || k[t] > nshell) rc = fail(-1, "orc_counts_exact: bin shell out of range");
+        if (rc || order == 2) continue;
+        for (int h = 0; h + 1 < (order == 4 ? 4 : 2); h += 2) {
+            const int a = k[h], c = k[h + 1];
+            if (fslot[a] < 0) fslot[a] = nf++;
+            if (fslot[c] < 0) fslot[c] = nf++;
+            if (pslot[a * (nshell + 1) + c] < 0) pslot[a * (nshell + 1) + c] = np++;
+        }
+    }
+    double* F = NULL;
+    double* work = NULL;
+    int32_t* P = NULL;
+    if (!rc && np > 0) {
+        F = (double*)malloc(sizeof(double) * 2 * n3 * (size_t)nf);
+        work = (double*)malloc(sizeof(double) * 2 * n3);
+        P = (int32_t*)malloc(sizeof(int32_t) * n3 * (size_t)np);
+        if (!F || !work || !P) rc = fail(-2, "orc_counts_exact: out of memory");
+        for (int s = 1; s <= nshell && !rc; s++)
+            if (fslot[s] >= 0) rc = shell_dft(N, smap, s - 1, F + 2 * n3 * (size_t)fslot[s]);
+        for (int a = 1; a <= nshell && !rc; a++)
+            for (int c = 1; c <= nshell && !rc; c++) {
+                const int q = pslot[a * (nshell + 1) + c];
+                if (q >= 0)
+                    rc = pair_conv(N, F + 2 * n3 * (size_t)fslot[a], F + 2 * n3 * (size_t)fslot[c], work,
+                                   P + n3 * (size_t)q);
+            }
+    }
+    for (int64_t b = 0; b < nbins && !rc; b++) {
+        const int32_t* k = bins + b * order;
+        if (order == 2) {
+            counts[b] = count_sum(N, smap, NULL, k[0] - 1, NULL, k[1] - 1);
+        } else {
+            const int32_t* p12 = P + n3 * (size_t)pslot[k[0] * (nshell + 1) + k[1]];
+            if (order == 3) counts[b] = count_sum(N, smap, p12, 0, NULL, k[2] - 1);
+            else counts[b] = count_sum(N, smap, p12, 0, P + n3 * (size_t)pslot[k[2] * (nshell + 1) + k[3]], 0);
+        }
+    }
+    free(smap);
+    free(fslot);
+    free(pslot);
+    free(F);
+    free(work);
+    free(P);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* whole estimator (Eqs. estimator, volume, Vn; App. A):                      */
 /*   count_b = (1/N^3) sum_x prod iota  (an integer: the number of closed     */
 /*             n-gons of grid modes, Eq. Ncalc with V_f = k_F^3)              */
@@ -425,17 +566,38 @@ int orc_estimate(int N, double L, const double* delta, int nshell, const double*
     /* counting fields: the same pipeline on a grid of unity (Sec. 4) */
     if (!rc) rc = orc_shell_fields(N, NULL, smap, nsel, sel, fields, &im2);
     if (!rc) rc = orc_product_sums(N, fields, slot, order, nbins, bins, C, NULL);
+    /* counts: the counting-field sum where FP64 keeps it within 1e-6 of an integer;     */
+    /* otherwise (large counts at n = 4) the exact pair-convolution count of the same bin */
+    int64_t* exact = NULL;
+    if (!rc) {
+        int64_t nbad = 0;
+        for (int64_t b = 0; b < nbins; b++)
+            if (fabs(C[b] / (double)n3 - nearbyint(C[b] / (double)n3)) > 1e-6) nbad++;
+        if (nbad > 0 && order > 4) rc = fail(-3, "orc_estimate: polygon count is not an integer");
+        if (nbad > 0 && !rc) {
+            int32_t* bad = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nbad * order));
+            exact = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbins);
+            if (!bad || !exact) rc = fail(-2, "orc_estimate: out of memory");
+            int64_t j = 0;
+            for (int64_t b = 0; b < nbins && !rc; b++)
+                if (fabs(C[b] / (double)n3 - nearbyint(C[b] / (double)n3)) > 1e-6)
+                    memcpy(bad + (j++) * order, bins + b * order, sizeof(int32_t) * (size_t)order);
+            int64_t* cb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nbad > 0 ? nbad : 1));
+            if (!rc && !cb) rc = fail(-2, "orc_estimate: out of memory");
+            if (!rc) rc = orc_counts_exact(N, nshell, edges, order, nbad, bad, cb);
+            j = 0;
+            for (int64_t b = 0; b < nbins && !rc; b++)
+                exact[b] = fabs(C[b] / (double)n3 - nearbyint(C[b] / (double)n3)) > 1e-6 ? cb[j++] : -1;
+            free(bad);
+            free(cb);
+        }
+    }
     if (!rc) {
         double n3d = (double)n3;
         double norm = pow(L * L * L, order - 1) / pow(n3d, order);
         for (int64_t b = 0; b < nbins; b++) {
             double v = C[b] / n3d;
-            double r = nearbyint(v);
-            if (fabs(v - r) > 1e-6) {
-                rc = fail(-3, "orc_estimate: polygon count is not an integer");
-                break;
-            }
-            int64_t cnt = (int64_t)r;
+            int64_t cnt = (exact && exact[b] >= 0) ? exact[b] : (int64_t)nearbyint(v);
             if (counts) counts[b] = cnt;
             if (S_out) S_out[b] = S[b];
             double den = n3d * (double)cnt;
@@ -445,6 +607,7 @@ int orc_estimate(int N, double L, const double* delta, int nshell, const double*
         }
     }
     if (imag_max) *imag_max = im1 > im2 ? im1 : im2;
+    free(exact);
     free(smap);
     free(slot);
     free(sel);

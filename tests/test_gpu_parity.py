@@ -125,6 +125,29 @@ def test_full_size_256cube_sampled(prec, field256, oracle256):
     assert err.max() <= TOL[prec], err.max()
 
 
+@pytest.fixture(scope="module")
+def oracle256_n4(field256):
+    """Oracle on the quadrilaterals among six shells of the 256^3 trispectrum workload (32 x 1.5 k_F)."""
+    e = fieldgen.unit_edges(32, 1.5)
+    bins = oracle.enumerate_bins(e, 4)
+    shells = {32, 31, 22, 13, 6, 1}
+    idx = np.array([i for i, b in enumerate(bins) if set(b.tolist()) <= shells])
+    return idx, oracle.estimate(field256.astype(np.float64), 1000.0, e, 4, bins=bins[idx])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_full_size_trispectrum_256cube_sampled(prec, field256, oracle256_n4):
+    """256^3 lognormal, 32 shells of width 1.5 k_F (45,135 quadrilaterals): the Gram of pair products."""
+    e = fieldgen.unit_edges(32, 1.5)
+    plan, B = gpu_estimate(field256, 1000.0, e, 4, prec)
+    assert plan.nbins == 45135
+    idx, ref = oracle256_n4
+    assert len(idx) >= 30
+    assert np.array_equal(plan.counts[idx], ref["counts"])
+    err = np.abs(B[idx] - ref["B"]) / (norm(1000.0, 256, 4) * ref["scale"])
+    assert err.max() <= TOL[prec], err.max()
+
+
 # ------------------------------------------------------------------ entry points agree bit for bit
 def test_host_entry_matches_device_entry():
     d = fieldgen.field("lognormal", 32, 5, np.float32)

@@ -101,6 +101,20 @@ def test_counts_match_direct_enumeration(N, order, width, nshell):
     assert np.array_equal(r["counts"], cnt)
 
 
+@pytest.mark.parametrize("N,order,width,nshell", [(16, 3, 1.0, 6), (16, 2, 1.0, 6), (12, 4, 1.0, 4),
+                                                  (12, 4, 1.5, 3), (15, 3, 1.0, 4), (16, 3, 1.5, 5)])
+def test_exact_pair_convolution_counts_match_direct_enumeration(N, order, width, nshell):
+    """The integer pair-convolution counts (used where the FP64 counting-field sum is not within
+    1e-6 of an integer) against brute-force enumeration of the tuples and the counting fields."""
+    e = fieldgen.unit_edges(nshell, width)
+    bins = oracle.enumerate_bins(e, order, oracle.RULE_ALL_SORTED)
+    exact = oracle.counts_exact(N, e, order, bins)
+    _, cnt = oracle.direct_sample(None, e, order, bins, N=N)
+    assert np.array_equal(exact, cnt)
+    r = oracle.estimate(np.zeros((N, N, N)), 1.0, e, order, bins=bins)
+    assert np.array_equal(exact, r["counts"])
+
+
 def test_counts_n2_are_mode_counts():
     N, e = 16, fieldgen.unit_edges(6)
     bins = oracle.enumerate_bins(e, 2, oracle.RULE_ALL_SORTED)
