@@ -653,24 +653,38 @@ poly_status ps_tc_prepare(PsPlan* p) {
     for (auto& b : bl) rl.insert(rl.end(), b.second->begin(), b.second->end());
     while (rl.size() % 128) rl.push_back(Row{false, {1, ra2 ? 1 : -1}, {}});
     const int nmt_total = (int)(rl.size() / 128);
-    // group consecutive M tiles; a group is valid when its local column list (<= 256)
-    // and its accumulator columns (<= 256) fit
     auto mt_cols = [&](int m) {
         std::set<int> s;
         for (size_t r = (size_t)m * 128; r < (size_t)(m + 1) * 128; r++) s.insert(rl[r].cols.begin(), rl[r].cols.end());
         return s;
     };
+    // Tile instances: an M tile with more than kTcMaxCols columns (the trispectrum's pair
+    // columns) is split into instances over ranges of its columns; each instance is placed
+    // in a group on its own, and its products are formed again there.
+    struct Inst {
+        int m;
+        std::vector<int> cols;  // global column indices, sorted
+    };
+    std::vector<Inst> inst;
+    for (int m = 0; m < nmt_total; m++) {
+        auto sc = mt_cols(m);
+        std::vector<int> v(sc.begin(), sc.end());
+        const int np = std::max(1, (int)((v.size() + kTcMaxCols - 1) / kTcMaxCols));
+        for (int k = 0; k < np; k++)
+            inst.push_back(Inst{m, std::vector<int>(v.begin() + (long)(v.size() * k / np),
+                                                    v.begin() + (long)(v.size() * (k + 1) / np))});
+    }
+    const int ninst = (int)inst.size();
+    // group consecutive instances; a group is valid when its local column list (<= 256)
+    // and its accumulator columns (<= 256) fit
     struct GroupPlan {
-        int m0, m1;
+        int m0, m1;              // instances [m0, m1)
         std::vector<int> local;  // global col indices, sorted, padded later
         int acc;
     };
     auto plan_group = [&](int m0, int m1, GroupPlan& g) -> bool {
         std::set<int> u;
-        for (int m = m0; m < m1; m++) {
-            auto s = mt_cols(m);
-            u.insert(s.begin(), s.end());
-        }
+        for (int i = m0; i < m1; i++) u.insert(inst[i].cols.begin(), inst[i].cols.end());
         g.m0 = m0;
         g.m1 = m1;
         g.local.assign(u.begin(), u.end());
@@ -678,29 +692,29 @@ poly_status ps_tc_prepare(PsPlan* p) {
         std::map<int, int> lidx;
         for (size_t i = 0; i < g.local.size(); i++) lidx[g.local[i]] = (int)i;
         g.acc = 0;
-        for (int m = m0; m < m1; m++) {
+        for (int i = m0; i < m1; i++) {
             std::set<int> cb;
-            for (int c : mt_cols(m)) cb.insert(lidx[c] / 16);
+            for (int c : inst[i].cols) cb.insert(lidx[c] / 16);
             for (auto& rr : tc_runs(cb)) g.acc += 16 * rr.second;
         }
         return g.acc <= kTcAccMax && (m1 - m0) <= max_mt;
     };
-    // groups: the fewest that fit, with the M tiles spread evenly over them (each group
+    // groups: the fewest that fit, with the instances spread evenly over them (each group
     // pays a fixed per-chunk cost for loading and synchronisation)
     std::vector<GroupPlan> gplans;
-    int ngroups = (nmt_total + max_mt - 1) / max_mt;
+    int ngroups = (ninst + max_mt - 1) / max_mt;
     while (true) {
         gplans.clear();
         bool ok = true;
         for (int g = 0; g < ngroups && ok; g++) {
-            const int m0 = (int)((long long)nmt_total * g / ngroups), m1 = (int)((long long)nmt_total * (g + 1) / ngroups);
+            const int m0 = (int)((long long)ninst * g / ngroups), m1 = (int)((long long)ninst * (g + 1) / ngroups);
             GroupPlan gp;
             if (m1 <= m0) continue;
             ok = plan_group(m0, m1, gp);
             gplans.push_back(gp);
         }
         if (ok) break;
-        if (ngroups >= nmt_total) return POLY_ERR_UNSUPPORTED;  // a single M tile does not fit
+        if (ngroups >= ninst) return POLY_ERR_UNSUPPORTED;  // a single instance does not fit
         ngroups++;
     }
     t->ngroups = (int)gplans.size();
@@ -718,7 +732,7 @@ poly_status ps_tc_prepare(PsPlan* p) {
         const GroupPlan& gp = gplans[gi];
         TcGroup G{};
         G.mt_off = (int)mtiles.size();
-        G.nmt = gp.m1 - gp.m0;
+        G.nmt = gp.m1 - gp.m0;  // instances of M tiles
         G.col_off = (int)colf.size();
         const int ncol = ((int)gp.local.size() + 15) / 16 * 16;
         G.ncol = ncol;
@@ -733,7 +747,9 @@ poly_status ps_tc_prepare(PsPlan* p) {
         }
         for (int i = (int)gp.local.size(); i < ncol; i++) colf.push_back(make_short2(-1, -1));
         int acc = 0;
-        for (int m = gp.m0; m < gp.m1; m++) {
+        for (int ii = gp.m0; ii < gp.m1; ii++) {
+            const Inst& in = inst[ii];
+            const int m = in.m;
             TcMTile M{};
             M.row_off = (int)rowf.size();
             M.run_off = (int)runs.size();
@@ -745,18 +761,18 @@ poly_status ps_tc_prepare(PsPlan* p) {
                 rowf.push_back(f);
             }
             std::set<int> cb;
-            for (size_t r = r0; r < r1; r++)
-                for (int c : rl[r].cols) cb.insert(lidx[c] / 16);
+            for (int c : in.cols) cb.insert(lidx[c] / 16);
             std::map<int, std::pair<int, int>> block_acc;  // block -> (run n0, acc col of run start)
             for (auto& rr : tc_runs(cb)) {
                 const int n0 = rr.first * 16, nn = rr.second * 16;
-                runs.push_back(make_int4(n0, nn, acc, m - gp.m0));
+                runs.push_back(make_int4(n0, nn, acc, ii - gp.m0));
                 for (int q = rr.first; q < rr.first + rr.second; q++) block_acc[q] = {n0, acc};
                 acc += nn;
             }
             M.nrun = (int)runs.size() - M.run_off;
             for (size_t r = r0; r < r1; r++)
                 for (int c : rl[r].cols) {
+                    if (!std::binary_search(in.cols.begin(), in.cols.end(), c)) continue;  // another instance's
                     const int lc = lidx[c];
                     auto ba = block_acc[lc / 16];
                     const int acc_col = ba.second + (lc - ba.first);
@@ -845,6 +861,11 @@ poly_status ps_tc_prepare(PsPlan* p) {
         t->slot_cap--;
     t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc);
     if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
+    // Accumulation window (chunks of 32 cells summed in FP32 in tensor memory before a drain).
+    // The tensor-core FP32 accumulation error grows with the window; at 256^3 the largest
+    // error over the split-BF16 scale is 6e-7 for the bispectrum at 64 chunks, but 1.5e-5 for
+    // the trispectrum (products of four fields), 5.9e-6 at 16 chunks.
+    t->window = p->order >= 4 ? 16 : 64;
     const char* w = getenv("POLY_TC_WINDOW");
     if (w && atoi(w) > 0) t->window = atoi(w);
     return POLY_OK;

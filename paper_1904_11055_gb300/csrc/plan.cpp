@@ -341,9 +341,12 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
         }
         const double n3 = (double)N * N * N;
         p->counts.resize(p->nbins);
+        // The FP64 sum lands next to the integer count; rounding is exact while its error is
+        // below 0.5.  The largest deviation seen is ~1e-3 (256^3, n = 4, counts ~1e11); a
+        // deviation above 0.05 means the FP64 sum can no longer be trusted to round correctly.
         for (int64_t b = 0; b < p->nbins; b++) {
             const double v = S[b] / n3, r = std::nearbyint(v);
-            if (std::fabs(v - r) > 1e-3 || r < 0) {
+            if (std::fabs(v - r) > 0.05 || r < 0) {
                 char msg[160];
                 snprintf(msg, sizeof msg, "polygon count of bin %lld is not an integer: %.6f", (long long)b, v);
                 rc = set_error(POLY_ERR_COUNT, msg);
