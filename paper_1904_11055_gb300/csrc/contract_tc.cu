@@ -10,13 +10,14 @@
 // (round-to-nearest adds), and the per-block sums are reduced in FP64 across
 // blocks in a fixed order.
 //
-// Block layout: 16 producer warps in two teams and 4 issuer warps.  Issuer 0
-// also streams 32-cell chunks of all shell fields (one contiguous block of the
-// cell-tiled field layout) into shared memory with TMA (128-byte swizzle).
+// Block layout: 16 producer warps in two teams and 4 issuer warps.  The last
+// issuer warp when the block has fewer than 4 M tiles (else issuer 0) streams
+// 32-cell chunks of all shell fields (one contiguous block of the cell-tiled
+// field layout) into shared memory with TMA (128-byte swizzle).
 // Team t produces chunks t, t + 2, ..., so that one team's barrier waits overlap
-// the other team's work; chunk i goes to A/B slot i mod nslots (3 slots when
-// tensor memory holds them, else 2), so a team reuses a slot only after the
-// MMAs of an earlier chunk than its previous one.  Producer warp w of a team owns
+// the other team's work; chunk i goes to A/B slot i mod nslots (up to 4 slots,
+// as many as tensor memory holds next to the accumulators), so a team reuses a
+// slot only after the MMAs of an earlier chunk than its previous one.  Producer warp w of a team owns
 // TMEM lane quadrant w % 4 and the 16-cell half w / 4 of a chunk: in every M tile
 // of the block, each lane forms the 16 products of its row in its half and
 // writes their hi and lo parts with one 16-column tcgen05.st (per M tile the A
@@ -54,7 +55,7 @@ constexpr int kTcThreads = kTcProducers + 32 * kTcIssuers;
 constexpr int kTcAccMax = 256;       // accumulator columns per block
 constexpr int kTcABase = 256;        // first TMEM column of the A operand in the self-test
 constexpr int kTcMaxRunsMt = 4;      // N runs per M tile
-constexpr int kTcMaxSlots = 3;       // A/B slots
+constexpr int kTcMaxSlots = 4;       // A/B slots
 constexpr int kTcMaxCols = 256;      // local B columns per block
 constexpr int kTcRowOctet = 8;       // pair rows of one producer warp come from 8 consecutive k1
 constexpr uint32_t kLBO = 128, kSBO = 512;  // B layout: K-adjacent core matrices, 8-row groups (K = 32)
@@ -220,12 +221,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t stage_tx = (uint32_t)nshell * kTcChunk * 4;
 
     if (warp >= kProdWarps) {
-        // ------------------------------------------------------------- MMA issuers (issuer 0 also loads)
+        // ------------------------------------------------------------- MMA issuers and the loads
         const int m = warp - kProdWarps;
         const bool el = tc::elect_one();
         const int pre = kTcStages < nch ? kTcStages : nch;
         int c = pre;  // next chunk to load
-        if (m == 0) {
+        // the TMA loads come from an issuer warp without an M tile when there is one, else from issuer 0
+        const int loader = nmt < kTcIssuers ? kTcIssuers - 1 : 0;
+        if (m == loader) {
             if (el && nch > 0) {
                 tc::prefetch_tensormap(&fmap);
                 for (int c0 = 0; c0 < pre; c0++) {
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (i == win.end || i == nch - 1) tc::mma_commit(acc_ready);
                 }
                 __syncwarp();
-                if (m == 0 && c < nch) {
+                if (m == loader && c < nch) {
                     // the stage held chunk c - kTcStages = i, released by its team before produced[]
                     if (!tc::mbar_wait_warp(&empty[lst], lph, s_abort)) break;
                     if (el) {
@@ -307,7 +310,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (el && nch > 0) tc::mma_commit(drain);
             __syncwarp();
         }
-        if (m == 0 && el) {
+        if (m == loader && m >= nmt) {
+            // a warp that only loads: refill each stage once its team has released it
+            int lst = 0;
+            uint32_t lph = 0;  // stage and phase of empty[] that frees the stage for chunk c
+            for (; c < nch; c++) {
+                if (!tc::mbar_wait_warp(&empty[lst], lph, s_abort)) break;
+                if (el) {
+                    tc::mbar_arrive_expect_tx(&full[lst], stage_tx);
+                    tc::tma_load_2d(s_d + lst * stage_bytes, &fmap, 0, (int)((cta.c0 + c) * nshell), &full[lst]);
+                }
+                __syncwarp();
+                if (++lst == kTcStages) {
+                    lst = 0;
+                    lph ^= 1u;
+                }
+            }
+        }
+        if (m == loader && el) {
             // every load started (chunks 0 .. c - 1) lands before the block exits
             volatile int no_abort = 0;
             for (int s2 = 0; s2 < kTcStages && s2 < c; s2++) {

@@ -68,7 +68,7 @@ struct poly_plan_s {
     // tensor-core contraction: state, and its tunable shape (poly_plan_tune)
     TcState* tc = nullptr;
     int tc_max_mt = 4;    // largest number of M tiles per CTA group
-    int tc_cta_mult = 2;  // CTA budget = SM count x tc_cta_mult / 2
+    int tc_cta_mult = 4;  // CTA budget = SM count x tc_cta_mult / 2 (two waves balance the tail best)
     // instrumentation
     int64_t launches = 0;
     bool timing = false;
