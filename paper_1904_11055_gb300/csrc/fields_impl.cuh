@@ -8,6 +8,7 @@
 // where K is the largest integer wavevector component inside the outermost shell.
 // Real fields are [x][y][z] with z fastest.
 #pragma once
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -241,11 +242,13 @@ struct RowPairWriter {  // final stage: real part -> row y1, imaginary part -> r
     }
 };
 
-template <typename T, int N, bool SPILL, bool UNITY, bool XPRE, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) inv_plane_kernel(
+// plane_s0: the shell whose plane x = x0 starts at `out` in the natural layout.
+// MINB: blocks per SM the registers must allow (2 for the 8-warp small-shell launches).
+template <typename T, int N, bool SPILL, bool UNITY, bool XPRE, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) inv_plane_kernel(
     const Cx<T>* __restrict__ fhat, const short4* __restrict__ lines, const int* __restrict__ line_off, int s0,
     int K, int x0, const Cx<double>* __restrict__ g_tw, T* __restrict__ out, size_t out_shell_stride,
-    Cx<T>* __restrict__ spill, const Cx<T>* __restrict__ xpre, int tile_ns) {
+    Cx<T>* __restrict__ spill, const Cx<T>* __restrict__ xpre, int tile_ns, int plane_s0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ls = line_stride<T>(N);
     constexpr int LPW = fft_lpw(N);
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) inv_plane_kernel(
     }
     __syncthreads();
     // real transform along z, two rows per complex line, written straight to global
-    T* plane = out + (size_t)blockIdx.y * out_shell_stride + (size_t)blockIdx.x * N * N;
+    T* plane = out + (size_t)(s - plane_s0) * out_shell_stride + (size_t)blockIdx.x * N * N;
     SmemLines<T> zb{s_z + (size_t)warp * LPW * ls, ls};
     const int npairs = (N + 1) / 2;
     for (int p0 = warp * LPW; p0 < npairs; p0 += WARPS * LPW) {
@@ -401,11 +404,11 @@ static cudaError_t inverse_n(const Cx<T>* fhat, const short4* lines, const int* 
     }
 #define PS_LAUNCH_INV(SP, PRE, W)                                                                                \
     {                                                                                                             \
-        auto k = inv_plane_kernel<T, N, SP, UNITY, PRE, W>;                                                       \
+        auto k = inv_plane_kernel<T, N, SP, UNITY, PRE, W, 1>;                                                    \
         const size_t smw = plane_smem_n<T, N>(K, SP, W);                                                          \
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw))) return e;       \
         k<<<grid, W * 32, smw, st>>>(fhat, lines, line_off, s0, K, x0, tw_inv, out, out_stride,                   \
-                                     SP ? spill : nullptr, xpre, tile_ns);                                        \
+                                     SP ? spill : nullptr, xpre, tile_ns, s0);                                    \
     }
     // 16 warps per block for FP32 when the plane still fits in shared memory (latency hiding), else 8
     const bool wide = sizeof(T) == 4 && !spill_on && plane_smem_n<T, N>(K, false, 16) <= kMaxSmem;
@@ -422,5 +425,51 @@ static cudaError_t inverse_n(const Cx<T>* fhat, const short4* lines, const int* 
     return cudaGetLastError();
 }
 
-}  // namespace ps
+// The inverse for the estimate path (FP32, natural or tiled output, x pass in
+// front) in runs of consecutive shells, each launched with the shared memory
+// its own largest kz needs: shells whose plane buffer fits twice per SM run as
+// 8-warp blocks, two per SM, so that one block's transform phases overlap the
+// other's; the rest run as one 16-warp block per SM.  kz_host[s] is shell s's
+// largest kz (host array).
+template <typename T, int N>
+static cudaError_t inverse_ranged_n(const Cx<T>* fhat, const short4* lines, const int* line_off, int s0, int ns, int K,
+                                    const Cx<double>* tw_inv, T* out, size_t out_stride, Cx<T>* xpre, int max_lines,
+                                    int tile_ns, const int* kz_host, cudaStream_t st) {
+    if (plane_smem_n<T, N>(K, false, 16) > kMaxSmem || !xpre)
+        return inverse_n<T, N, false>(fhat, lines, line_off, s0, ns, K, 0, N, tw_inv, out, out_stride, nullptr, xpre,
+                                      max_lines, tile_ns, st);
+    cudaError_t e;
+    const size_t smx = ((size_t)N + 32 * (size_t)(2 * K + 1)) * sizeof(Cx<T>);
+    auto kx = xpass_kernel<T, N>;
+    if ((e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx))) return e;
+    kx<<<dim3((max_lines + 31) / 32, ns), 256, smx, st>>>(fhat, lines, line_off, s0, K, tw_inv, xpre);
+    if ((e = cudaGetLastError())) return e;
+    // largest kz whose 8-warp block fits twice per SM (228 KB per SM, 1 KB reserved per block)
+    constexpr size_t kHalfSm = 228 * 1024 / 2 - 1024;
+    int ksmall = -1;
+    while (ksmall < K && plane_smem_n<T, N>(ksmall + 1, false, 8) <= kHalfSm) ksmall++;
+    for (int r0 = s0; r0 < s0 + ns;) {
+        const bool small = kz_host[r0] <= ksmall;
+        int r1 = r0 + 1, kzm = kz_host[r0];
+        while (r1 < s0 + ns && (kz_host[r1] <= ksmall) == small) kzm = std::max(kzm, kz_host[r1++]);
+        const dim3 grid(N, r1 - r0);
+        if (small) {
+            auto k = inv_plane_kernel<T, N, false, false, true, 8, 2>;
+            const size_t sm = plane_smem_n<T, N>(kzm, false, 8);
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+            k<<<grid, 8 * 32, sm, st>>>(fhat, lines, line_off, r0, K, 0, tw_inv, out, out_stride, nullptr, xpre, tile_ns,
+                                        s0);
+        } else {
+            auto k = inv_plane_kernel<T, N, false, false, true, 16, 1>;
+            const size_t sm = plane_smem_n<T, N>(kzm, false, 16);
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+            k<<<grid, 16 * 32, sm, st>>>(fhat, lines, line_off, r0, K, 0, tw_inv, out, out_stride, nullptr, xpre,
+                                         tile_ns, s0);
+        }
+        if ((e = cudaGetLastError())) return e;
+        r0 = r1;
+    }
+    return cudaSuccess;
+}
 
+}  // namespace ps

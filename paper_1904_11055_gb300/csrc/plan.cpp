@@ -440,6 +440,9 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     std::vector<int> off{0};
     for (int s = 0; s < nshell; s++) {
         build_lines(p, p->edges.data(), s, lines);
+        int kzm = 0;
+        for (size_t l = off.back(); l < lines.size() / 4; l++) kzm = std::max(kzm, (int)lines[4 * l + 1]);
+        p->shell_kz.push_back(kzm);
         off.push_back((int)(lines.size() / 4));
     }
     {
@@ -513,10 +516,14 @@ poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st) {
     p->launches += 2;
     mark(p, 1, st);
     if (!ps_xpre_fits(p, 0, p->nshell)) return set_error(POLY_ERR_ARG, "x-pass buffer too small");
-    if ((e = ps_inverse(p->N, p->is_double, 0, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, 0, p->N,
-                        p->d_tw_inv, p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, p->d_xpre,
-                        p->max_lines, p->nshell, st)))
-        return cuda_error(e, "shell fields");
+    if (p->is_double)
+        e = ps_inverse(p->N, 1, 0, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, 0, p->N, p->d_tw_inv,
+                       p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, p->d_xpre, p->max_lines, p->nshell, st);
+    else
+        e = ps_inverse_ranged_f32(p->N, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, p->d_tw_inv,
+                                  p->d_fields, (size_t)p->N * p->N * p->N, p->d_xpre, p->max_lines, p->nshell,
+                                  p->shell_kz.data(), st);
+    if (e) return cuda_error(e, "shell fields");
     p->launches += 2;  // x pass + plane kernel
     mark(p, 2, st);
     return POLY_OK;
