@@ -98,8 +98,15 @@ __global__ void shell_gather_kernel(const Cx<T>* __restrict__ F, const short4* _
 using namespace ps;
 
 // host -------------------------------------------------------------------------------
+struct AtState;  // adjoint_tc.cu
+poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::vector<short4>& ent, AtState** out);
+cudaError_t ps_at_contract(PsPlan* p, AtState* S, const float* w, cudaStream_t st);
+int ps_at_error(AtState* S);
+void ps_at_free(AtState* S);
+
 struct AdjTables {
     int nent = 0;
+    AtState* at = nullptr;  // tensor-core form of the per-cell contraction (bispectrum, split-BF16)
     void *d_moff = nullptr, *d_ent = nullptr, *d_eoff = nullptr, *d_ebins = nullptr, *d_w = nullptr;
     std::vector<int> line_off;  // host copy of the plan's line offsets
 };
@@ -135,6 +142,13 @@ static poly_status adj_prepare(PsPlan* p, AdjTables& A) {
         eoff.push_back((int)ebins.size());
     }
     A.nent = (int)ent.size();
+    if (n == 3 && p->prec == POLY_SPLIT_BF16) {
+        std::vector<int> ent_m(ent.size());
+        for (int m = 0; m < p->nshell; m++)
+            for (int e = moff[m]; e < moff[m + 1]; e++) ent_m[e] = m;
+        poly_status s = ps_at_prepare(p, ent_m, ent, &A.at);
+        if (s && s != POLY_ERR_UNSUPPORTED) return s;  // unsupported: the CUDA-core kernel below serves
+    }
     const size_t es = p->is_double ? 8 : 4;
     auto up = [&](void** d, const void* h, size_t bytes) -> poly_status {
         poly_status s = ps_alloc(p, d, bytes);
@@ -183,7 +197,9 @@ poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, 
                                                       A.nent, (float*)A.d_w);
     const unsigned gblocks = (unsigned)((ncell + kAdjChunk - 1) / kAdjChunk);
     const size_t smem = (size_t)p->nshell * kAdjChunk * (dbl ? 8 : 4);
-    if (dbl) {
+    if (A.at) {
+        if ((e = ps_at_contract(p, A.at, (const float*)A.d_w, st))) return POLY_ERR_CUDA;
+    } else if (dbl) {
         cudaFuncSetAttribute(adj_g_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         adj_g_kernel<double><<<gblocks, kAdjThreads, smem, st>>>((const double*)p->d_fields, p->nshell, ncell,
                                                                   (const int*)A.d_moff, (const short4*)A.d_ent,
@@ -195,7 +211,7 @@ poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, 
                                                                  (const float*)A.d_w, (float*)p->d_G);
     }
     if ((e = cudaGetLastError())) return POLY_ERR_CUDA;
-    p->launches += 2;
+    p->launches += A.at ? 3 : 2;
     // H = c_n / N^3 * sum_m mask_m forward(G_m)
     const size_t nl = (size_t)(2 * p->K + 1) * (p->K + 1) * (2 * p->K + 1);
     const size_t es = dbl ? 8 : 4;
@@ -228,6 +244,9 @@ poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, 
 }
 
 void ps_adj_free(PsPlan* p) {
+    if (p->adj) ps_at_free(p->adj->at);
     delete p->adj;
     p->adj = nullptr;
 }
+
+int ps_adj_device_error(PsPlan* p) { return p->adj && p->adj->at ? ps_at_error(p->adj->at) : 0; }

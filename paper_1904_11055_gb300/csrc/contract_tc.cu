@@ -926,6 +926,7 @@ void ps_tc_free(PsPlan* p) {
 }
 
 poly_status ps_check_device_error(PsPlan* p) {
+    if (ps_adj_device_error(p)) return POLY_ERR_TIMEOUT;
     if (!p->tc || !p->tc->d_err) return POLY_OK;
     int v = 0;
     if (cudaMemcpy(&v, p->tc->d_err, sizeof(int), cudaMemcpyDeviceToHost)) return POLY_ERR_CUDA;

@@ -372,11 +372,12 @@ static void free_plan(PsPlan* p) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (p->device >= 0 && cur != p->device) cudaSetDevice(p->device);
+    ps_tc_free(p);   // each frees its own buffers through ps_free, which drops them from the list
+    ps_adj_free(p);
     for (void* q : p->allocations) cudaFree(q);
+    p->allocations.clear();
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
-    ps_tc_free(p);
-    ps_adj_free(p);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
 }

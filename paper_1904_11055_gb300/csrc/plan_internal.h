@@ -103,6 +103,7 @@ poly_status ps_check_device_error(PsPlan* p);
 
 // adjoint.cu
 void ps_adj_free(PsPlan* p);
+int ps_adj_device_error(PsPlan* p);  // nonzero: the tensor-core adjoint kernel timed out
 poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, void* dL_ddelta, cudaStream_t st);
 // batched.cpp
 poly_status ps_batched_impl(const poly_plan* plans, const void* const* fields, double* const* outs, int count,

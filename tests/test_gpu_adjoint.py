@@ -4,7 +4,8 @@ Checks: against the FP64 oracle gradient (analytic adjoint, itself pinned by
 central differences in test_oracle_estimator.py); against central finite
 differences of the GPU estimator on 64 random voxels of a 64^3 / 16-shell
 field (FP64 plain method); a full-size 256^3 / 64-shell directional derivative
-(FP64 finite difference of L along a random direction vs <grad_FP32, v>); and
+(FP64 finite difference of L along a random direction vs <grad, v>, for the
+FP32 adjoint and the tensor-core split-BF16 one); and
 the torch.autograd wrapper.
 """
 import os
@@ -39,7 +40,8 @@ def gpu_grad(plan, delta, w):
 
 @pytest.mark.parametrize("N,order,nshell,prec,tol", [(32, 3, 8, "fp64", 1e-9), (32, 3, 8, "fp32", 2e-5),
                                                      (24, 4, 5, "fp64", 1e-9), (24, 2, 9, "fp32", 2e-5),
-                                                     (48, 3, 14, "split_bf16", 2e-5)])
+                                                     (48, 3, 14, "split_bf16", 2e-5),
+                                                     (96, 3, 30, "split_bf16", 2e-5)])
 def test_gradient_matches_oracle(N, order, nshell, prec, tol):
     e = fieldgen.unit_edges(nshell)
     d = fieldgen.field("lognormal", N, 40 + N, np.float32).astype(np.float64)
@@ -75,12 +77,13 @@ def test_gradient_central_differences_64cube():
         assert abs(fd - gv) <= 1e-6 * np.abs(g).max(), (v, fd, gv)
 
 
-def test_gradient_directional_derivative_full_size():
-    """256^3 lognormal, 64 unit shells: <grad, v> from the FP32 adjoint vs an FP64 central difference."""
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_gradient_directional_derivative_full_size(prec):
+    """256^3 lognormal, 64 unit shells: <grad, v> from the FP32 / split-BF16 adjoint vs an FP64 central difference."""
     N, L = 256, 1000.0
     e = fieldgen.unit_edges(64)
     d = fieldgen.field("lognormal", N, 4, np.float32)
-    p32 = ps.Plan(N, L, 3, e, "fp32")
+    p32 = ps.Plan(N, L, 3, e, prec)
     w = np.random.default_rng(5).standard_normal(p32.nbins)
     g = gpu_grad(p32, d.astype(np.float64), w)
     p32.close()

@@ -99,3 +99,17 @@ def test_tuning_reorders_only_the_final_sums(tmp_path):
 def test_tuning_has_nothing_to_do_for_cuda_core_plans():
     plan = ps.Plan(32, 500.0, 3, fieldgen.unit_edges(8), "fp32")
     assert plan.tune(_field("lognormal", 32, 3)) == (0, 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16", "fp64"])
+def test_closing_a_plan_leaves_no_pending_cuda_error(prec):
+    """Teardown frees every buffer once: a stale error would surface at the next kernel launch anywhere."""
+    N, e = 32, fieldgen.unit_edges(8)
+    plan = ps.Plan(N, 500.0, 3, e, prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    d = _field("lognormal", N, 11).to(dt)
+    plan.estimate(d)
+    plan.backward(d, torch.ones(plan.nbins, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    plan.close()
+    assert (torch.ones(8, device="cuda") * 2).sum().item() == 16.0
