@@ -244,7 +244,11 @@ def run_ours(args):
     results = {}
     for prec in precisions:
         try:
+            torch.cuda.synchronize()
+            t_plan = time.perf_counter()
             plan = ps.Plan(N, L, ORDER, edges, prec)
+            torch.cuda.synchronize()
+            plan_ms = (time.perf_counter() - t_plan) * 1e3
         except ps.PolyError as e:
             if e.status == 6:
                 results[prec] = {"unavailable": str(e)}
@@ -295,7 +299,21 @@ def run_ours(args):
                        "frac": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
                        "traffic": traffic_for("inv_plane", ["fields_impl.cuh", "fields_f32.cu", "fft.cuh"]), "kernel": "inv_plane_kernel",
                        "peak_source": peak_src}
+        # the adjoint (dL/d delta for L = sum_b w_b B_b), device-timed, on this rank's field
+        w = torch.from_numpy(np.random.default_rng(5).standard_normal(plan.nbins)).cuda()
+        grad = torch.empty_like(d)
+        plan.backward(d, w, grad)
+        torch.cuda.synchronize()
+        bms = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.backward(d, w, grad)
+            b.record()
+            torch.cuda.synchronize()
+            bms.append(a.elapsed_time(b))
         results[prec] = {"value": value, "ms_per_step": total_ms / args.steps, "roofline": roof,
+                         "plan_ms": plan_ms, "backward_ms": statistics.median(bms),
                          "fields_roofline": fields_roof, "stage_ms": stage, "gpu_launches": launches,
                          "clocks": clk.summary(),
                          "e2e": {"value": plan.nbins * args.steps * world / e2e_s, "unit": "configs/s",
@@ -320,7 +338,12 @@ def run_ours(args):
                    "parallelism": f"replica per GPU x{world}" if world > 1 else "1 GPU"},
         "roofline": h["roofline"], "fields_roofline": h["fields_roofline"], "stage_ms": h["stage_ms"],
         "e2e": h["e2e"], "gpu_launches": h["gpu_launches"], "clocks": h["clocks"],
-        "precisions": {p: ({k: r[k] for k in ("value", "ms_per_step", "roofline", "stage_ms", "e2e")}
+        "plan_ms": {"value": h["plan_ms"], "note": "plan creation with the FP64 counts (the first plan of the "
+                    "process; later plans with the same shells reuse the cached counts); outside the timed step"},
+        "backward_ms": {"value": h["backward_ms"], "note": "poly_backward, dL/d delta of sum_b w_b B_b on the same "
+                        "field, device-timed median of 3"},
+        "precisions": {p: ({k: r[k] for k in ("value", "ms_per_step", "roofline", "stage_ms", "e2e", "plan_ms",
+                                              "backward_ms")}
                            if "value" in r else r) for p, r in results.items()},
     }
     if world == 1 and not args.no_cpu_baseline and (N, NSHELL, ORDER) == (256, 64, 3):
