@@ -297,7 +297,8 @@ def run_ours(args):
         fields_roof = {"bound": "hbm", "achieved": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9,
                        "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                       "traffic": traffic_for("inv_plane", ["fields_impl.cuh", "fields_f32.cu", "fft.cuh"]), "kernel": "inv_plane_kernel",
+                       "traffic": traffic_for("inv_plane", ["fields_impl.cuh", "fields_f32.cu", "fft.cuh"]),
+                       "kernel": "fields stage: xpass_kernel + inv_plane_kernel (8- and 16-warp launches), bytes per step",
                        "peak_source": peak_src}
         # the adjoint (dL/d delta for L = sum_b w_b B_b), device-timed, on this rank's field
         w = torch.from_numpy(np.random.default_rng(5).standard_normal(plan.nbins)).cuda()
