@@ -130,8 +130,9 @@ __global__ void __launch_bounds__(kPlaneThreads) fwd_xlines_kernel(const Cx<T>* 
 // inverse, x pass: for every (shell, line) the masked 1-D inverse transform
 // along x, T[s][x][l] = sum_{kx in the line's runs} F(kx, ky, kz) e^{+2 pi i kx x / N},
 // stored so that a plane's lines are contiguous: T[line_off[s] * N + x * nl_s + l].
-// 32 lines per block; a thread owns one line and every 8th x.
-// ------------------------------------------------------------------------
+// 32 lines per block.  A warp takes one line at a time and its lanes 32
+// consecutive x, so every lane of the warp runs the same kx loop; results pass
+// through a [32 x][32 lines] shared tile so that the stores stay coalesced.
 template <typename T, int N>
 __global__ void __launch_bounds__(256) xpass_kernel(const Cx<T>* __restrict__ fhat, const short4* __restrict__ lines,
                                                     const int* __restrict__ line_off, int s0, int K,
@@ -139,16 +140,19 @@ __global__ void __launch_bounds__(256) xpass_kernel(const Cx<T>* __restrict__ fh
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T>* s_tw = reinterpret_cast<Cx<T>*>(smem_raw);
     const int nk = 2 * K + 1;
-    Cx<T>* s_f = s_tw + N;  // [32][nk]
+    Cx<T>* s_f = s_tw + N;         // [32][nk]: the block's lines, kx in [-K, K]
+    Cx<T>* s_o = s_f + 32 * nk;    // [32 x][33]
+    short4* s_l = reinterpret_cast<short4*>(s_o + 32 * 33);
     const int s = s0 + blockIdx.y;
     const int lb = line_off[s], nls = line_off[s + 1] - lb;
     const int l0 = blockIdx.x * 32;
     if (l0 >= nls) return;
+    const int nl = min(32, nls - l0);
     load_twiddles(s_tw, g_tw, N);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < nl) s_l[threadIdx.x] = lines[lb + l0 + threadIdx.x];
     // stage the run entries of the block's lines (one warp per line)
-    for (int l = warp; l < 32; l += 8) {
-        if (l0 + l >= nls) break;
+    for (int l = warp; l < nl; l += 8) {
         const short4 L = lines[lb + l0 + l];
         const Cx<T>* Fl = fhat + ((size_t)(L.x + K) * (K + 1) + L.y) * nk + K;
         const int an = L.z > 0 ? L.z : 1;
@@ -156,32 +160,44 @@ __global__ void __launch_bounds__(256) xpass_kernel(const Cx<T>* __restrict__ fh
         for (int kx = an + lane; kx <= L.w; kx += 32) s_f[l * nk + K - kx] = Fl[-kx];
     }
     __syncthreads();
-    const int l = lane;
-    if (l0 + l >= nls) return;
-    const short4 L = lines[lb + l0 + l];
-    const int a = L.z, b = L.w, an = a > 0 ? a : 1;
-    const Cx<T>* f = s_f + l * nk + K;
-    Cx<T>* o = out + (size_t)lb * N + l0 + l;
-    for (int x = warp; x < N; x += 8) {
-        T sr = 0, si = 0;
-        int m = (int)(((long long)a * x) % N);
-        for (int kx = a; kx <= b; kx++) {
-            const Cx<T> w = s_tw[m], v = f[kx];
-            sr += v.re * w.re - v.im * w.im;
-            si += v.re * w.im + v.im * w.re;
-            m += x;
-            if (m >= N) m -= N;
+    Cx<T>* o = out + (size_t)lb * N + l0;
+    for (int x0 = 0; x0 < N; x0 += 32) {
+        const int x = x0 + lane;
+        for (int l = warp; l < nl; l += 8) {
+            const short4 L = s_l[l];
+            const int a = L.z, b = L.w, an = a > 0 ? a : 1;
+            const Cx<T>* f = s_f + l * nk + K;
+            T sr = 0, si = 0;
+            if (x < N) {
+                int m = (a * x) % N;
+                for (int kx = a; kx <= b; kx++) {
+                    const Cx<T> w = s_tw[m], v = f[kx];
+                    sr += v.re * w.re - v.im * w.im;
+                    si += v.re * w.im + v.im * w.re;
+                    m += x;
+                    if (m >= N) m -= N;
+                }
+                m = ((N - an) * x) % N;  // -an x mod N
+                for (int kx = an; kx <= b; kx++) {
+                    const Cx<T> w = s_tw[m], v = f[-kx];
+                    sr += v.re * w.re - v.im * w.im;
+                    si += v.re * w.im + v.im * w.re;
+                    m -= x;
+                    if (m < 0) m += N;
+                }
+            }
+            s_o[lane * 33 + l] = cx<T>(sr, si);
         }
-        m = (int)(((long long)(N - an) * x) % N);
-        for (int kx = an; kx <= b; kx++) {
-            const Cx<T> w = s_tw[m], v = f[-kx];
-            sr += v.re * w.re - v.im * w.im;
-            si += v.re * w.im + v.im * w.re;
-            m -= x;
-            if (m < 0) m += N;
-        }
-        o[(size_t)x * nls] = cx<T>(sr, si);
+        __syncthreads();
+        for (int xi = warp; xi < 32 && x0 + xi < N; xi += 8)
+            if (lane < nl) o[(size_t)(x0 + xi) * nls + lane] = s_o[xi * 33 + lane];
+        __syncthreads();
     }
+}
+
+template <typename T, int N>
+static size_t xpass_smem_n(int K) {
+    return ((size_t)N + 32 * (size_t)(2 * K + 1) + 32 * 33) * sizeof(Cx<T>) + 32 * sizeof(short4);
 }
 
 // ------------------------------------------------------------------------
@@ -396,7 +412,7 @@ static cudaError_t inverse_n(const Cx<T>* fhat, const short4* lines, const int* 
     cudaError_t e;
     const bool pre = !UNITY && xpre != nullptr;
     if (pre) {
-        const size_t smx = ((size_t)N + 32 * (size_t)(2 * K + 1)) * sizeof(Cx<T>);
+        const size_t smx = xpass_smem_n<T, N>(K);
         auto kx = xpass_kernel<T, N>;
         if ((e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx))) return e;
         kx<<<dim3((max_lines + 31) / 32, ns), 256, smx, st>>>(fhat, lines, line_off, s0, K, tw_inv, xpre);
@@ -439,7 +455,7 @@ static cudaError_t inverse_ranged_n(const Cx<T>* fhat, const short4* lines, cons
         return inverse_n<T, N, false>(fhat, lines, line_off, s0, ns, K, 0, N, tw_inv, out, out_stride, nullptr, xpre,
                                       max_lines, tile_ns, st);
     cudaError_t e;
-    const size_t smx = ((size_t)N + 32 * (size_t)(2 * K + 1)) * sizeof(Cx<T>);
+    const size_t smx = xpass_smem_n<T, N>(K);
     auto kx = xpass_kernel<T, N>;
     if ((e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx))) return e;
     kx<<<dim3((max_lines + 31) / 32, ns), 256, smx, st>>>(fhat, lines, line_off, s0, K, tw_inv, xpre);
