@@ -221,10 +221,9 @@ def run_ours(args):
     import fieldgen
     import paper_1904_11055_gb300 as ps
     from paper_1904_11055_gb300 import build as psbuild
+    from paper_1904_11055_gb300 import sharding
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = sharding.rank_env()
     torch.cuda.set_device(local)
     dist_ok = world > 1
     if dist_ok:
@@ -235,7 +234,7 @@ def run_ours(args):
         torch.distributed.barrier()
     peaks, peak_src = load_peaks()
 
-    delta_np = fieldgen.field("lognormal", N, SEED + rank, np.float32)
+    delta_np = fieldgen.field("lognormal", N, sharding.field_seed(SEED, rank), np.float32)
     d = torch.from_numpy(delta_np).cuda()
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     edges = fieldgen.unit_edges(NSHELL, WIDTH)
@@ -257,12 +256,9 @@ def run_ours(args):
         step_ms, stage, launches = None, None, None
         with ClockSampler(local) as clk:
             step_ms, stage, launches = time_precision(ps, torch, plan, d, args, flush_buf, dist_ok)
-        total_ms = sum(step_ms)
-        if dist_ok:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = plan.nbins * args.steps * world / (total_ms / 1e3)
+        # every rank estimated its own field K times: units of all ranks over the slowest rank's time
+        value = sharding.job_rate(plan.nbins * args.steps, sum(step_ms) / 1e3)
+        total_ms = sharding.max_over_ranks(sum(step_ms))
         # end to end through the host-buffer entry point (pinned input, H2D + D2H every step)
         pinned = torch.from_numpy(delta_np).pin_memory().numpy()
         out_h = np.empty(plan.nbins)
@@ -272,10 +268,7 @@ def run_ours(args):
         for _ in range(args.steps):
             ps.poly_estimate_host(plan.handle, pinned, out_h, None)
         e2e_s = time.perf_counter() - t0
-        if dist_ok:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_rate = sharding.job_rate(plan.nbins * args.steps, e2e_s)
         n3 = N ** 3
         useful_flops = plan.nbins * n3 * ORDER
         if prec == "split_bf16":
@@ -317,7 +310,7 @@ def run_ours(args):
                          "plan_ms": plan_ms, "backward_ms": statistics.median(bms),
                          "fields_roofline": fields_roof, "stage_ms": stage, "gpu_launches": launches,
                          "clocks": clk.summary(),
-                         "e2e": {"value": plan.nbins * args.steps * world / e2e_s, "unit": "configs/s",
+                         "e2e": {"value": e2e_rate, "unit": "configs/s",
                                  "h2d_bytes_per_step": n3 * 4, "d2h_bytes_per_step": plan.nbins * 8},
                          "nbins": plan.nbins}
         plan.close()
@@ -368,19 +361,23 @@ def run_mocks(args):
     import fieldgen
     import paper_1904_11055_gb300 as ps
 
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:  # one GPU's batch; the other ranks have nothing to add
-        return
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1904_11055_gb300 import sharding
+
+    rank, world, local = sharding.rank_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     e = fieldgen.unit_edges(MOCK_SHELLS)
     plans = {n: ps.Plan(n, L, 3, e, "split_bf16", ps.POLY_ALLOW_ALIAS if 3 * MOCK_SHELLS >= n else 0)
              for n, _ in MOCKS}
     # 8 distinct seeded fields per size, one device buffer per realisation
     host = {n: [fieldgen.field("lognormal", n, 1000 + 8 * k + j, np.float32) for j in range(8)]
             for k, (n, _) in enumerate(MOCKS)}
+    # this rank's share of each grid size's realisations (weak scaling: whole realisations per GPU)
     bplans, fields = [], []
     for n, count in MOCKS:
-        for r in range(count):
+        a, b = sharding.unit_range(count, world, rank)
+        for r in range(a, b):
             bplans.append(plans[n])
             fields.append(torch.from_numpy(host[n][r % 8]).cuda())
     outs = [torch.empty(p.nbins, dtype=torch.float64, device="cuda") for p in bplans]
@@ -412,11 +409,21 @@ def run_mocks(args):
         return statistics.median(ms)
 
     with ClockSampler(torch.cuda.current_device()) as clocks:
+        if world > 1:
+            torch.distributed.barrier()
         t_batch = timed(batched)
         t_seq = timed(sequential)
     identical = all(torch.equal(a, b) for a, b in zip(outs, seq_outs))
-    total = sum(c for _, c in MOCKS)
-    line = {"metric": MOCK_METRIC, "value": total / (t_batch / 1e3), "unit": "realisations/s", "n_gpus": 1,
+    # every rank ran its own share: realisations of all ranks over the slowest rank's step time
+    rate_batch = sharding.job_rate(len(bplans), t_batch / 1e3)
+    rate_seq = sharding.job_rate(len(bplans), t_seq / 1e3)
+    identical = sharding.sum_over_ranks(0.0 if identical else 1.0) == 0.0
+    t_batch, t_seq = sharding.max_over_ranks(t_batch), sharding.max_over_ranks(t_seq)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+    line = {"metric": MOCK_METRIC, "value": rate_batch, "unit": "realisations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
             "data": "synthetic: 8 seeded lognormal fields per grid size (seeds 1000+), one device buffer per mock",
@@ -424,7 +431,7 @@ def run_mocks(args):
                        "order": 3, "bins": {f"{n}^3": plans[n].nbins for n, _ in MOCKS},
                        "l2": "256 MiB buffer written between timed steps (L2 flushed)",
                        "tuned_config": {f"{n}^3": {"code": c, "contract_ms": round(m, 4)} for n, (c, m) in tuned.items()}},
-            "sequential": {"value": total / (t_seq / 1e3), "ms_per_step": t_seq},
+            "sequential": {"value": rate_seq, "ms_per_step": t_seq},
             "speedup_vs_sequential": t_seq / t_batch, "bit_identical_to_sequential": identical,
             "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
