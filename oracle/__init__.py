@@ -175,7 +175,8 @@ def direct_sample(delta, edges, order: int, bins, N: int | None = None):
 
 
 def counts_exact(N: int, edges, order: int, bins) -> np.ndarray:
-    """Exact polygon counts (n = 2, 3, 4) by integer pair convolutions of the shell indicators."""
+    """Exact polygon counts (n = 2..6) by integer convolutions of the shell indicators (pairs; for n = 5, 6
+    a group of n - 3 shells against a group of three)."""
     e = np.ascontiguousarray(edges, dtype=np.float64)
     b = np.ascontiguousarray(bins, dtype=np.int32)
     cnt = np.empty(b.shape[0], dtype=np.int64)

@@ -461,9 +461,127 @@ static int pair_conv(int N, const double* Fa, const double* Fb, double* work, in
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* exact counts for n = 5, 6 by group convolutions: the bin's shells split    */
+/* into a first group of n - 3 (two for n = 5, three for n = 6) and a second  */
+/* group of three.  With the closure map of a group g of shells,              */
+/*   G_g(p) = #{one grid mode in each shell of g, the modes summing to p}     */
+/*          = round(IDFT(prod_{s in g} DFT(1_Ss))(p) / N^3),                  */
+/* integers of at most prod |S_s| (each checked to lie within 1e-3 of one),   */
+/*   count = sum_p G_first(p) G_second(-p),  summed in 64-bit integers.       */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int N;
+    const int64_t* a;
+    const int64_t* b;
+    int64_t part[256];
+} cnt64_ctx;
+
+static void count64_range(void* vctx, int64_t begin, int64_t end, int tid) {
+    cnt64_ctx* c = (cnt64_ctx*)vctx;
+    const int N = c->N;
+    int64_t acc = 0;
+    for (int64_t i = begin; i < end; i++) {
+        if (!c->a[i]) continue;
+        const int x = (int)(i / ((int64_t)N * N)), y = (int)((i / N) % N), z = (int)(i % N);
+        const int64_t j = ((int64_t)((N - x) % N) * N + (N - y) % N) * N + (N - z) % N; /* -p */
+        acc += c->a[i] * c->b[j];
+    }
+    c->part[tid] = acc;
+}
+
+static int group_map(int N, const double* const* F, int nf, double* work, int64_t* out) {
+    const size_t n3 = (size_t)N * N * N;
+    for (size_t i = 0; i < n3; i++) {
+        double re = F[0][2 * i], im = F[0][2 * i + 1];
+        for (int f = 1; f < nf; f++) {
+            const double br = F[f][2 * i], bi = F[f][2 * i + 1];
+            const double t = re * br - im * bi;
+            im = re * bi + im * br;
+            re = t;
+        }
+        work[2 * i] = re;
+        work[2 * i + 1] = im;
+    }
+    int rc = orc_fft3d(work, N, N, N, +1);
+    if (rc) return rc;
+    for (size_t i = 0; i < n3; i++) {
+        const double v = work[2 * i] / (double)n3, r = nearbyint(v);
+        if (fabs(v - r) > 1e-3 || fabs(work[2 * i + 1] / (double)n3) > 1e-3)
+            return fail(-3, "orc_counts_exact: group convolution is not an integer");
+        out[i] = (int64_t)r;
+    }
+    return 0;
+}
+
+static int counts_exact_groups(int N, int nshell, const double* edges, int order, int64_t nbins, const int32_t* bins,
+                               int64_t* counts) {
+    const size_t n3 = (size_t)N * N * N;
+    const int g1 = order - 3; /* size of the first group; the second has three shells */
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    int* fslot = (int*)malloc(sizeof(int) * (size_t)(nshell + 1));
+    /* distinct groups: key = shells (1-based) padded with 0, stored 3 per group */
+    int32_t* gkey = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(2 * nbins + 1));
+    int64_t* bg = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)(nbins + 1)); /* per bin: its two group ids */
+    if (!smap || !fslot || !gkey || !bg) return fail(-2, "orc_counts_exact: out of memory");
+    int rc = orc_shell_map(N, nshell, edges, smap);
+    int nf = 0;
+    int64_t ng = 0;
+    for (int s = 0; s <= nshell; s++) fslot[s] = -1;
+    for (int64_t b = 0; b < nbins && !rc; b++) {
+        const int32_t* k = bins + b * order;
+        for (int t = 0; t < order; t++) {
+            if (k[t] < 1 || k[t] > nshell) rc = fail(-1, "orc_counts_exact: bin shell out of range");
+            else if (fslot[k[t]] < 0) fslot[k[t]] = nf++;
+        }
+        for (int h = 0; h < 2 && !rc; h++) {
+            int32_t key[3] = {0, 0, 0};
+            const int first = h == 0 ? 0 : g1, size = h == 0 ? g1 : 3;
+            for (int t = 0; t < size; t++) key[t] = k[first + t];
+            int64_t g = 0;
+            while (g < ng && memcmp(gkey + 3 * g, key, sizeof key)) g++;
+            if (g == ng) memcpy(gkey + 3 * ng++, key, sizeof key);
+            bg[2 * b + h] = g;
+        }
+    }
+    double* F = rc ? NULL : (double*)malloc(sizeof(double) * 2 * n3 * (size_t)(nf > 0 ? nf : 1));
+    double* work = rc ? NULL : (double*)malloc(sizeof(double) * 2 * n3);
+    int64_t* G = rc ? NULL : (int64_t*)malloc(sizeof(int64_t) * n3 * (size_t)(ng > 0 ? ng : 1));
+    if (!rc && (!F || !work || !G)) rc = fail(-2, "orc_counts_exact: out of memory");
+    for (int s = 1; s <= nshell && !rc; s++)
+        if (fslot[s] >= 0) rc = shell_dft(N, smap, s - 1, F + 2 * n3 * (size_t)fslot[s]);
+    for (int64_t g = 0; g < ng && !rc; g++) {
+        const double* Fs[3];
+        int nfg = 0;
+        for (int t = 0; t < 3; t++)
+            if (gkey[3 * g + t] > 0) Fs[nfg++] = F + 2 * n3 * (size_t)fslot[gkey[3 * g + t]];
+        rc = group_map(N, Fs, nfg, work, G + n3 * (size_t)g);
+    }
+    for (int64_t b = 0; b < nbins && !rc; b++) {
+        cnt64_ctx c;
+        memset(&c, 0, sizeof c);
+        c.N = N;
+        c.a = G + n3 * (size_t)bg[2 * b];
+        c.b = G + n3 * (size_t)bg[2 * b + 1];
+        par_for((int64_t)n3, count64_range, &c);
+        int64_t sum = 0;
+        for (int t = 0; t < 256; t++) sum += c.part[t];
+        counts[b] = sum;
+    }
+    free(smap);
+    free(fslot);
+    free(gkey);
+    free(bg);
+    free(F);
+    free(work);
+    free(G);
+    return rc;
+}
+
 int orc_counts_exact(int N, int nshell, const double* edges, int order, int64_t nbins, const int32_t* bins,
                      int64_t* counts) {
-    if (N < 2 || order < 2 || order > 4 || nbins < 0) return fail(-1, "orc_counts_exact: bad args (order 2..4)");
+    if (N < 2 || order < 2 || order > 6 || nbins < 0) return fail(-1, "orc_counts_exact: bad args (order 2..6)");
+    if (order >= 5) return counts_exact_groups(N, nshell, edges, order, nbins, bins, counts);
     const size_t n3 = (size_t)N * N * N;
     int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
     if (!smap) return fail(-2, "orc_counts_exact: out of memory");
@@ -567,13 +685,13 @@ int orc_estimate(int N, double L, const double* delta, int nshell, const double*
     if (!rc) rc = orc_shell_fields(N, NULL, smap, nsel, sel, fields, &im2);
     if (!rc) rc = orc_product_sums(N, fields, slot, order, nbins, bins, C, NULL);
     /* counts: the counting-field sum where FP64 keeps it within 1e-6 of an integer;     */
-    /* otherwise (large counts at n = 4) the exact pair-convolution count of the same bin */
+    /* otherwise (large counts at n >= 4) the exact convolution count of the same bin      */
     int64_t* exact = NULL;
     if (!rc) {
         int64_t nbad = 0;
         for (int64_t b = 0; b < nbins; b++)
             if (fabs(C[b] / (double)n3 - nearbyint(C[b] / (double)n3)) > 1e-6) nbad++;
-        if (nbad > 0 && order > 4) rc = fail(-3, "orc_estimate: polygon count is not an integer");
+        if (nbad > 0 && order > 6) rc = fail(-3, "orc_estimate: polygon count is not an integer");
         if (nbad > 0 && !rc) {
             int32_t* bad = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nbad * order));
             exact = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbins);

@@ -115,6 +115,40 @@ def test_exact_pair_convolution_counts_match_direct_enumeration(N, order, width,
     assert np.array_equal(exact, r["counts"])
 
 
+def dp_counts(N, edges, bins):
+    """Closed n-gon counts by dynamic programming over partial sums of grid modes (no FFT): the
+    histogram of q_1 + ... + q_t (mod N) grows one shell at a time; the count is its value at 0."""
+    smap = np_shell_map(N, edges)
+    modes = [np.argwhere(smap == s) for s in range(len(edges) - 1)]
+    out = []
+    for b in bins:
+        h = np.zeros((N, N, N), dtype=np.int64)
+        h[0, 0, 0] = 1
+        for k in b:
+            nh = np.zeros_like(h)
+            for q in modes[k - 1]:
+                nh += np.roll(h, shift=tuple(int(v) for v in q), axis=(0, 1, 2))
+            h = nh
+        out.append(int(h[0, 0, 0]))
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("N,order,width,nshell", [(13, 5, 1.0, 2), (16, 6, 1.0, 2), (12, 5, 1.5, 1)])
+def test_exact_group_convolution_counts_n5_n6(N, order, width, nshell):
+    """n = 5, 6: the group-convolution counts against dynamic programming over the tuples, the brute-force
+    sampler, and the counting-field sums of the estimator (which fall back to the exact counts)."""
+    e = fieldgen.unit_edges(nshell, width)
+    bins = oracle.enumerate_bins(e, order, oracle.RULE_ALL_SORTED)
+    exact = oracle.counts_exact(N, e, order, bins)
+    assert np.array_equal(exact, dp_counts(N, e, bins))
+    assert exact.max() > 0
+    if order == 5:
+        _, cnt = oracle.direct_sample(None, e, order, bins, N=N)
+        assert np.array_equal(exact, cnt)
+    r = oracle.estimate(np.zeros((N, N, N)), 1.0, e, order, bins=bins)
+    assert np.array_equal(exact, r["counts"])
+
+
 def test_counts_n2_are_mode_counts():
     N, e = 16, fieldgen.unit_edges(6)
     bins = oracle.enumerate_bins(e, 2, oracle.RULE_ALL_SORTED)
