@@ -69,7 +69,9 @@ typedef enum {
 
 /*
  * Create a plan for grid size N (one of 16, 24, 32, 48, 64, 96, 128, 160, 256),
- * box side L > 0, order n in [2, 4], `nshell` shells with `nshell + 1`
+ * box side L > 0, order n in [2, 6] (POLY_SPLIT_BF16: [2, 4]; n = 5, 6 run
+ * on the CUDA-core contraction, rows of two or three fields against columns
+ * of three), `nshell` shells with `nshell + 1`
  * strictly increasing edges (host array, units of k_F, edges[0] >= 0).
  * K = the largest integer with K^2 < edges[nshell]^2 must satisfy 2K+1 <= N,
  * and n*K < N unless POLY_ALLOW_ALIAS.  Plan creation enumerates the bins,
@@ -114,6 +116,7 @@ poly_status poly_estimate_host(poly_plan plan, const void* delta_x_host, double*
  * never stores pair products), contracts dL/dB with products of the other
  * fields, transforms each result forward, keeps its own shell and applies one
  * inverse transform (the adjoint of the estimator).  Asynchronous on `stream`.
+ * Orders 2 to 4 (POLY_ERR_UNSUPPORTED above).
  */
 poly_status poly_backward(poly_plan plan, const void* delta_x, const double* dL_dB, void* dL_ddelta, void* stream);
 

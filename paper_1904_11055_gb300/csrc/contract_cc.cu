@@ -1,8 +1,8 @@
 // CUDA-core contraction over grid cells (Eq. estimator, discrete form of App. A):
 //   S_b = sum_x prod_t D_{b_t}(x)
 // recast per tile as a GEMM  C[r][c] = sum_x A_r(x) B_c(x), where a row A_r is a
-// product of one or two shell fields (e.g. D_{k1} D_{k2}) and a column B_c the
-// product of the remaining ones (D_{k3}, or D_{k3} D_{k4}).  Cells are split
+// product of one to three shell fields (e.g. D_{k1} D_{k2}) and a column B_c the
+// product of the remaining ones (D_{k3}, D_{k3} D_{k4}, or three for n = 5, 6).  Cells are split
 // across blocks (split-K); every block writes its FP64 partial tile and a
 // fixed-order reduction gathers the bins.
 //
@@ -29,13 +29,13 @@ PS_DEV void load4(const double* p, double* v) {
 template <typename T, bool WEIGHTED, bool ABS>
 __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
     const T* __restrict__ fields, size_t fstride, int tile_ns, int64_t ncell, const T* __restrict__ weight,
-    const PsTile* __restrict__ tiles, int ntiles, const int* __restrict__ field_ids, const short2* __restrict__ rowf,
-    const short2* __restrict__ colf, int64_t chunks_per_split, double* __restrict__ partial) {
+    const PsTile* __restrict__ tiles, int ntiles, const int* __restrict__ field_ids, const short4* __restrict__ rowf,
+    const short4* __restrict__ colf, int64_t chunks_per_split, double* __restrict__ partial) {
     constexpr int CH = sizeof(T) == 8 ? 16 : 32, TM = kCcTM, TN = kCcTN;
     __shared__ T s_d[kCcMaxFields][CH + 1];
     __shared__ __align__(16) T s_a[CH][TM];
     __shared__ __align__(16) T s_b[CH][TN];
-    __shared__ short2 s_rf[TM], s_cf[TN];
+    __shared__ short4 s_rf[TM], s_cf[TN];
     __shared__ int s_fid[kCcMaxFields];
 
     const PsTile tile = tiles[blockIdx.x];
@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
     const int c0 = 16 * (warp & 3) + 4 * (lane & 3);
     const bool active = (tile.region_mask >> warp) & 1u;
 
-    for (int i = tid; i < TM; i += kCcThreads) s_rf[i] = i < tile.nrow ? rowf[tile.row_off + i] : make_short2(-1, -1);
-    for (int i = tid; i < TN; i += kCcThreads) s_cf[i] = i < tile.ncol ? colf[tile.col_off + i] : make_short2(-1, -1);
+    for (int i = tid; i < TM; i += kCcThreads) s_rf[i] = i < tile.nrow ? rowf[tile.row_off + i] : make_short4(-1, -1, -1, -1);
+    for (int i = tid; i < TN; i += kCcThreads) s_cf[i] = i < tile.ncol ? colf[tile.col_off + i] : make_short4(-1, -1, -1, -1);
     for (int i = tid; i < tile.nfield; i += kCcThreads) s_fid[i] = field_ids[tile.field_off + i];
 
     T acc[4][4];
@@ -96,11 +96,12 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
         // 2. row and column products
         for (int e = tid; e < CH * TM; e += kCcThreads) {
             const int x = e / TM, r = e - (e / TM) * TM;
-            const short2 f = s_rf[r];
+            const short4 f = s_rf[r];
             T v = 0;
             if (f.x >= 0) {
                 v = s_d[f.x][x];
                 if (f.y >= 0) v *= s_d[f.y][x];
+                if (f.z >= 0) v *= s_d[f.z][x];
                 if (WEIGHTED) {
                     const int64_t cell = base + x;
                     v *= cell < ncell ? weight[cell] : (T)0;
@@ -111,11 +112,12 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
         }
         for (int e = tid; e < CH * TN; e += kCcThreads) {
             const int x = e / TN, c = e - (e / TN) * TN;
-            const short2 f = s_cf[c];
+            const short4 f = s_cf[c];
             T v = 0;
             if (f.x >= 0) {
                 v = s_d[f.x][x];
                 if (f.y >= 0) v *= s_d[f.y][x];
+                if (f.z >= 0) v *= s_d[f.z][x];
                 if (ABS) v = v < 0 ? -v : v;
             }
             s_b[x][c] = v;
@@ -176,7 +178,7 @@ using namespace ps;
 
 cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
                            int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
-                           const short2* rowf, const short2* colf, int nsplit, int64_t chunks_per_split,
+                           const short4* rowf, const short4* colf, int nsplit, int64_t chunks_per_split,
                            double* partial, cudaStream_t st) {
     dim3 grid(ntiles, nsplit);
     if (is_double) {

@@ -41,7 +41,7 @@ inline int ps_cc_chunk(int is_double) { return is_double ? 16 : 32; }
 // fields: natural [s][cell] with stride field_stride (tile_ns == 0) or cell-tiled over tile_ns shells
 cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
                            int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
-                           const short2* rowf, const short2* colf, int nsplit, int64_t chunks_per_split,
+                           const short4* rowf, const short4* colf, int nsplit, int64_t chunks_per_split,
                            double* partial, cudaStream_t st);
 // S[b] = sum_split partial[split * slot_stride + slot[b]]
 cudaError_t ps_reduce_slots(const double* partial, int nsplit, int64_t slot_stride, const int64_t* slot,

@@ -121,7 +121,7 @@ extern "C" poly_status poly_estimate_noalloc(int N, double L, int nshell, const 
     const size_t o_fields = c.take((size_t)nshell * n3 * 4);
     const size_t o_tiles = c.take(hp.cc.tiles.size() * sizeof(PsTile));
     const size_t o_fid = c.take(hp.cc.field_ids.size() * sizeof(int));
-    const size_t o_rowf = c.take(hp.cc.rowf.size() * sizeof(short2)), o_colf = c.take(hp.cc.colf.size() * sizeof(short2));
+    const size_t o_rowf = c.take(hp.cc.rowf.size() * sizeof(short4)), o_colf = c.take(hp.cc.colf.size() * sizeof(short4));
     const size_t o_slot = c.take(hp.cc.slot.size() * sizeof(int64_t));
     const size_t o_part = c.take((size_t)nsplit * slot_stride * 8);
     const size_t o_S = c.take((size_t)hp.nbins * 8), o_cnt = c.take((size_t)hp.nbins * 8);
@@ -153,8 +153,8 @@ extern "C" poly_status poly_estimate_noalloc(int N, double L, int nshell, const 
                   {o_loff, line_off.data(), line_off.size() * sizeof(int)},
                   {o_tiles, hp.cc.tiles.data(), hp.cc.tiles.size() * sizeof(PsTile)},
                   {o_fid, hp.cc.field_ids.data(), hp.cc.field_ids.size() * sizeof(int)},
-                  {o_rowf, hp.cc.rowf.data(), hp.cc.rowf.size() * sizeof(short2)},
-                  {o_colf, hp.cc.colf.data(), hp.cc.colf.size() * sizeof(short2)},
+                  {o_rowf, hp.cc.rowf.data(), hp.cc.rowf.size() * sizeof(short4)},
+                  {o_colf, hp.cc.colf.data(), hp.cc.colf.size() * sizeof(short4)},
                   {o_slot, hp.cc.slot.data(), hp.cc.slot.size() * sizeof(int64_t)},
                   {o_cnt, counts, (size_t)hp.nbins * 8}};
     for (const Copy& cp : copies)
@@ -167,7 +167,7 @@ extern "C" poly_status poly_estimate_noalloc(int N, double L, int nshell, const 
         (e = ps_inverse(N, 0, 0, B + o_fhat, B + o_lines, (const int*)(B + o_loff), 0, nshell, K, 0, N, B + o_twi,
                         B + o_fields, (size_t)n3, nullptr, nullptr, 0, nshell, st)) ||
         (e = ps_contract_cc(0, 0, 0, B + o_fields, (size_t)n3, nshell, n3, nullptr, (const PsTile*)(B + o_tiles), ntiles,
-                            (const int*)(B + o_fid), (const short2*)(B + o_rowf), (const short2*)(B + o_colf), nsplit,
+                            (const int*)(B + o_fid), (const short4*)(B + o_rowf), (const short4*)(B + o_colf), nsplit,
                             cps, (double*)(B + o_part), st)) ||
         (e = ps_reduce_slots((const double*)(B + o_part), nsplit, slot_stride, (const int64_t*)(B + o_slot), hp.nbins,
                              (double*)(B + o_S), st)))

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -153,19 +154,26 @@ void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& li
 
 // ---------------------------------------------------------------------------
 // CUDA-core contraction tiles: rows = products of the first ra shells of a
-// bin, cols = products of the rest; rows grouped 64 at a time after sorting by
-// their column span, each group's column union cut into chunks of 64.
+// bin, cols = products of the rest (ra = 1, 2, 2, 2, 3 for n = 2..6); rows
+// grouped 64 at a time after sorting by their column span, each group's column
+// union cut into chunks of 64.
 // ---------------------------------------------------------------------------
 void build_cc_tiles(PsPlan* p, CcTiles& t) {
+    using Key = std::array<int, 3>;  // 1-based shells, -1 padded
     const int n = p->order;
-    const int ra = n >= 3 ? 2 : 1, ca = n - ra;
-    auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra == 2 ? b[1] : -1); };
-    auto ckey = [&](const int32_t* b) { return std::make_pair(b[ra], ca == 2 ? b[ra + 1] : -1); };
-    std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> rows;  // row -> sorted col keys
+    const int ra = n <= 2 ? 1 : (n <= 5 ? 2 : 3), ca = n - ra;
+    auto key = [](const int32_t* b, int cnt) {
+        Key k{-1, -1, -1};
+        for (int i = 0; i < cnt; i++) k[i] = b[i];
+        return k;
+    };
+    auto rkey = [&](const int32_t* b) { return key(b, ra); };
+    auto ckey = [&](const int32_t* b) { return key(b + ra, ca); };
+    std::map<Key, std::vector<Key>> rows;  // row -> col keys
     for (int64_t i = 0; i < p->nbins; i++) rows[rkey(&p->bins[i * n])].push_back(ckey(&p->bins[i * n]));
     struct RowInfo {
-        std::pair<int, int> key;
-        std::vector<std::pair<int, int>> cols;
+        Key key;
+        std::vector<Key> cols;
     };
     std::vector<RowInfo> ri;
     for (auto& kv : rows) {
@@ -177,10 +185,10 @@ void build_cc_tiles(PsPlan* p, CcTiles& t) {
     std::stable_sort(ri.begin(), ri.end(), [](const RowInfo& a, const RowInfo& b) {
         return std::make_pair(a.cols.front(), a.cols.back()) < std::make_pair(b.cols.front(), b.cols.back());
     });
-    std::map<std::tuple<int, int, int, int>, int64_t> slot_of;  // (row key, col key) -> slot
+    std::map<std::pair<Key, Key>, int64_t> slot_of;  // (row key, col key) -> slot
     for (size_t g = 0; g < ri.size(); g += kCcTM) {
         const size_t g1 = std::min(ri.size(), g + kCcTM);
-        std::vector<std::pair<int, int>> cu;
+        std::vector<Key> cu;
         for (size_t r = g; r < g1; r++) cu.insert(cu.end(), ri[r].cols.begin(), ri[r].cols.end());
         std::sort(cu.begin(), cu.end());
         cu.erase(std::unique(cu.begin(), cu.end()), cu.end());
@@ -202,18 +210,11 @@ void build_cc_tiles(PsPlan* p, CcTiles& t) {
                 t.field_ids.push_back(shell1 - 1);
                 return (short)id;
             };
-            for (size_t r = g; r < g1; r++) {
-                short2 f;
-                f.x = loc(ri[r].key.first);
-                f.y = loc(ri[r].key.second);
-                t.rowf.push_back(f);
-            }
-            std::map<std::pair<int, int>, int> cidx;
+            auto factors = [&](const Key& k) { return make_short4(loc(k[0]), loc(k[1]), loc(k[2]), -1); };
+            for (size_t r = g; r < g1; r++) t.rowf.push_back(factors(ri[r].key));
+            std::map<Key, int> cidx;
             for (size_t c = c0; c < c1; c++) {
-                short2 f;
-                f.x = loc(cu[c].first);
-                f.y = loc(cu[c].second);
-                t.colf.push_back(f);
+                t.colf.push_back(factors(cu[c]));
                 cidx[cu[c]] = (int)(c - c0);
             }
             tile.nfield = (int)local.size();
@@ -224,18 +225,13 @@ void build_cc_tiles(PsPlan* p, CcTiles& t) {
                     if (it == cidx.end()) continue;
                     const int rr = (int)(r - g), cc = it->second;
                     tile.region_mask |= 1u << ((rr / 32) * 4 + cc / 16);
-                    slot_of[{ri[r].key.first, ri[r].key.second, ck.first, ck.second}] =
-                        (int64_t)tid * (kCcTM * kCcTN) + rr * kCcTN + cc;
+                    slot_of[{ri[r].key, ck}] = (int64_t)tid * (kCcTM * kCcTN) + rr * kCcTN + cc;
                 }
             t.tiles.push_back(tile);
         }
     }
     t.slot.resize(p->nbins);
-    for (int64_t i = 0; i < p->nbins; i++) {
-        auto rk = rkey(&p->bins[i * n]);
-        auto ck = ckey(&p->bins[i * n]);
-        t.slot[i] = slot_of.at({rk.first, rk.second, ck.first, ck.second});
-    }
+    for (int64_t i = 0; i < p->nbins; i++) t.slot[i] = slot_of.at({rkey(&p->bins[i * n]), ckey(&p->bins[i * n])});
 }
 
 static int choose_splits(int ntiles, int64_t nchunks, int sms) {
@@ -326,8 +322,8 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
         }
         if (rc) break;
         if ((e = ps_contract_cc(1, 1, 0, d_iota, (size_t)nw, 0, nw, d_wgt, (const PsTile*)p->d_cc_tiles,
-                                (int)t.tiles.size(), (const int*)p->d_cc_field_ids, (const short2*)p->d_cc_rowf,
-                                (const short2*)p->d_cc_colf, nsplit, cps, (double*)d_part, st)) ||
+                                (int)t.tiles.size(), (const int*)p->d_cc_field_ids, (const short4*)p->d_cc_rowf,
+                                (const short4*)p->d_cc_colf, nsplit, cps, (double*)d_part, st)) ||
             (e = ps_reduce_slots((double*)d_part, nsplit, slot_stride, (const int64_t*)p->d_cc_slot, p->nbins,
                                  (double*)d_S, st))) {
             rc = cuda_error(e, "count contraction");
@@ -385,7 +381,9 @@ static void free_plan(PsPlan* p) {
 static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
                                poly_precision prec, unsigned flags) {
     if (!edges || nshell < 1 || nshell > 128) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
-    if (order < 2 || order > 4) return set_error(POLY_ERR_UNSUPPORTED, "order must be 2, 3 or 4");
+    if (order < 2 || order > 6) return set_error(POLY_ERR_UNSUPPORTED, "order must be in [2, 6]");
+    if (order > 4 && prec == POLY_SPLIT_BF16)
+        return set_error(POLY_ERR_UNSUPPORTED, "split-BF16 plans support orders 2 to 4 (FP32 and FP64: up to 6)");
     if (!(L > 0) || !std::isfinite(L)) return set_error(POLY_ERR_ARG, "L must be positive");
     if (flags & ~(POLY_BINS_ALL_SORTED | POLY_ALLOW_ALIAS)) return set_error(POLY_ERR_ARG, "unknown flag");
     if (!ps_supported_n(N)) return set_error(POLY_ERR_UNSUPPORTED, "grid size N not in the supported set");
@@ -536,7 +534,7 @@ poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st) {
     const size_t n3 = (size_t)p->N * p->N * p->N;
     if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->d_fields, n3, p->nshell, (int64_t)n3, nullptr,
                             (const PsTile*)p->d_cc_tiles, (int)p->cc.tiles.size(), (const int*)p->d_cc_field_ids,
-                            (const short2*)p->d_cc_rowf, (const short2*)p->d_cc_colf, p->cc_nsplit, p->cc_cps,
+                            (const short4*)p->d_cc_rowf, (const short4*)p->d_cc_colf, p->cc_nsplit, p->cc_cps,
                             p->d_partial, st)))
         return cuda_error(e, "contraction");
     if (!absval) mark(p, 3, st);

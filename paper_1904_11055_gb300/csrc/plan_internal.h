@@ -12,7 +12,7 @@
 struct CcTiles {
     std::vector<PsTile> tiles;
     std::vector<int> field_ids;
-    std::vector<short2> rowf, colf;
+    std::vector<short4> rowf, colf;  // up to three factors each (-1: none)
     std::vector<int64_t> slot;  // per bin: tile * 64 * 64 + r * 64 + c
 };
 

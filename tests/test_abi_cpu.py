@@ -41,7 +41,9 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("kwargs,status", [
-    (dict(N=64, order=5), 6),                                          # order outside [2, 4]
+    (dict(N=64, order=7), 6),                                          # order outside [2, 6]
+    (dict(N=64, order=5, edges=np.arange(6) + 0.5, prec=1), 6),         # split-BF16 only up to n = 4
+    (dict(N=64, order=6, edges=np.arange(12) + 0.5), 2),                # 6 * 11 >= 64: aliasing
     (dict(N=50), 6),                                                   # N not supported
     (dict(N=64, edges=[0.5, 1.5, 1.5]), 1),                            # edges not increasing
     (dict(N=64, edges=[-1.0, 1.5]), 1),                                # negative edge

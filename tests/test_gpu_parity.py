@@ -97,6 +97,29 @@ def test_matches_oracle(prec, N, order, nshell, kind, seed):
     assert err.max() <= TOL[prec], err.max()
 
 
+# ------------------------------------------------------------------ orders 5 and 6 (CUDA-core path: pairs or
+# triples of fields against triples)
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("N,order,nshell,seed", [(32, 5, 5, 21), (48, 6, 6, 22), (48, 5, 8, 23)])
+def test_higher_orders_match_oracle(prec, N, order, nshell, seed):
+    d = fieldgen.field("lognormal", N, seed, np.float32).astype(np.float64)
+    plan, _, _, err = check_against_oracle(d, 1000.0, fieldgen.unit_edges(nshell), order, prec)
+    assert plan.nbins > 50
+    assert err.max() <= TOL[prec], err.max()
+
+
+def test_higher_orders_refuse_split_bf16_and_the_adjoint():
+    e = fieldgen.unit_edges(4)
+    with pytest.raises(ps.PolyError) as ei:
+        ps.Plan(32, 1000.0, 5, e, "split_bf16")
+    assert ei.value.status == 6
+    plan = ps.Plan(32, 1000.0, 5, e, "fp32")
+    d = torch.from_numpy(fieldgen.field("lognormal", 32, 3, np.float32)).cuda()
+    with pytest.raises(ps.PolyError) as ei:
+        plan.backward(d, torch.ones(plan.nbins, dtype=torch.float64, device="cuda"))
+    assert ei.value.status == 6
+
+
 @pytest.fixture(scope="module")
 def field256():
     return fieldgen.field("lognormal", 256, 2, np.float32)
