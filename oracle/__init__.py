@@ -67,6 +67,7 @@ def _load():
         L.orc_direct_sample.argtypes = [i32, P, i32, P, i32, i64, P, P, P]
         L.orc_counts_exact.argtypes = [i32, i32, P, i32, i64, P, P]
         L.orc_gradient.argtypes = [i32, f64, P, i32, P, i32, i64, P, P, P, P]
+        L.orc_disconnected.argtypes = [i32, f64, P, i32, P, i64, P, P, P, P]
         _lib = L
     return _lib
 
@@ -182,6 +183,20 @@ def counts_exact(N: int, edges, order: int, bins) -> np.ndarray:
     cnt = np.empty(b.shape[0], dtype=np.int64)
     _check(_load().orc_counts_exact(int(N), e.size - 1, _p(e), int(order), b.shape[0], _p(b), _p(cnt)))
     return cnt
+
+
+def disconnected(delta, L: float, edges, bins, counts):
+    """Disconnected (Wick-paired) part of the trispectrum estimator per bin, and the shell powers
+    P(k) = sum_{q in S_k} |dhat(q)|^2.  Returns (B_disc, P)."""
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    b = np.ascontiguousarray(bins, dtype=np.int32)
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    out = np.empty(b.shape[0])
+    P = np.empty(e.size - 1)
+    _check(_load().orc_disconnected(d.shape[0], float(L), _p(d), e.size - 1, _p(e), b.shape[0], _p(b), _p(c),
+                                    _p(out), _p(P)))
+    return out, P
 
 
 def gradient(delta, L: float, edges, order: int, bins, counts, dLdB) -> np.ndarray:

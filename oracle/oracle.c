@@ -642,6 +642,51 @@ int orc_counts_exact(int N, int nshell, const double* edges, int order, int64_t 
 }
 
 /* ------------------------------------------------------------------------- */
+/* disconnected part of the trispectrum estimator (n = 4; not in the paper,   */
+/* whose Eq. estimator keeps it): the closed quadrilaterals that split into   */
+/* two zero-sum pairs, summed over the three pairings of Wick's theorem with  */
+/* the measured per-mode power |dhat(q)|^2 (real delta: dhat(-q) = dhat(q)*). */
+/* A pairing (a b)(c d) needs q_b = -q_a and q_d = -q_c, i.e. equal shells    */
+/* k_a = k_b and k_c = k_d (disjoint shells, S = -S); with                    */
+/*   P(k) = sum_{q in S_k} |dhat(q)|^2                                        */
+/*   S_disc_b = N^3 [d(k1,k2) d(k3,k4) P(k1) P(k3) + d(k1,k3) d(k2,k4) P(k1) P(k2) */
+/*                   + d(k1,k4) d(k2,k3) P(k1) P(k2)]                         */
+/* and the estimator's normalisation B_disc_b = c_4 S_disc_b / (N^3 count_b). */
+/* ------------------------------------------------------------------------- */
+int orc_disconnected(int N, double L, const double* delta, int nshell, const double* edges, int64_t nbins,
+                     const int32_t* bins, const int64_t* counts, double* B_disc, double* P_out) {
+    if (N < 2 || L <= 0.0 || nbins < 0 || nshell < 1) return fail(-1, "orc_disconnected: bad args");
+    const size_t n3 = (size_t)N * N * N;
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    double* dhat = (double*)malloc(sizeof(double) * 2 * n3);
+    double* P = (double*)calloc((size_t)nshell, sizeof(double));
+    if (!smap || !dhat || !P) return fail(-2, "orc_disconnected: out of memory");
+    int rc = orc_shell_map(N, nshell, edges, smap);
+    if (!rc) rc = orc_forward(N, delta, dhat);
+    for (size_t i = 0; i < n3 && !rc; i++)
+        if (smap[i] >= 0) P[smap[i]] += dhat[2 * i] * dhat[2 * i] + dhat[2 * i + 1] * dhat[2 * i + 1];
+    const double n3d = (double)n3, norm = pow(L * L * L, 3) / pow(n3d, 4);
+    for (int64_t b = 0; b < nbins && !rc; b++) {
+        const int32_t* k = bins + 4 * b;
+        for (int t = 0; t < 4; t++)
+            if (k[t] < 1 || k[t] > nshell) rc = fail(-1, "orc_disconnected: bin shell out of range");
+        if (rc) break;
+        const double p1 = P[k[0] - 1], p2 = P[k[1] - 1], p3 = P[k[2] - 1];
+        double sd = 0.0;
+        if (k[0] == k[1] && k[2] == k[3]) sd += p1 * p3;
+        if (k[0] == k[2] && k[1] == k[3]) sd += p1 * p2;
+        if (k[0] == k[3] && k[1] == k[2]) sd += p1 * p2;
+        sd *= n3d;
+        B_disc[b] = counts[b] > 0 ? norm * sd / (n3d * (double)counts[b]) : 0.0;
+    }
+    if (!rc && P_out) memcpy(P_out, P, sizeof(double) * (size_t)nshell);
+    free(smap);
+    free(dhat);
+    free(P);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* whole estimator (Eqs. estimator, volume, Vn; App. A):                      */
 /*   count_b = (1/N^3) sum_x prod iota  (an integer: the number of closed     */
 /*             n-gons of grid modes, Eq. Ncalc with V_f = k_F^3)              */

@@ -149,6 +149,54 @@ def test_exact_group_convolution_counts_n5_n6(N, order, width, nshell):
     assert np.array_equal(exact, r["counts"])
 
 
+def wick_brute_force(delta, edges, bins):
+    """N^3 x the Wick-paired sum over every closed quadrilateral of grid modes, tuple by tuple:
+    sum over (q1, q2, q3) with q4 = -(q1 + q2 + q3) in its shell of
+    [q1+q2=0][q3+q4=0]|d(q1)|^2|d(q3)|^2 + [q1+q3=0][q2+q4=0]|d(q1)|^2|d(q2)|^2 + [q1+q4=0][q2+q3=0]|d(q1)|^2|d(q2)|^2."""
+    N = delta.shape[0]
+    dh = np.fft.fftn(delta)
+    pw = np.abs(dh) ** 2
+    smap = np_shell_map(N, edges)
+    modes = [np.argwhere(smap == s) for s in range(len(edges) - 1)]
+    out = []
+    for b in bins:
+        q1, q2, q3 = (modes[k - 1] for k in b[:3])
+        A = q1[:, None, None, :]
+        B = q2[None, :, None, :]
+        C = q3[None, None, :, :]
+        D = (-(A + B + C)) % N
+        inb = smap[D[..., 0], D[..., 1], D[..., 2]] == b[3] - 1
+        zero = lambda u, v: np.all((u + v) % N == 0, axis=-1)
+        p1 = pw[A[..., 0], A[..., 1], A[..., 2]]
+        p2 = pw[B[..., 0], B[..., 1], B[..., 2]]
+        p3 = pw[C[..., 0], C[..., 1], C[..., 2]]
+        w = zero(A, B) & zero(C, D), zero(A, C) & zero(B, D), zero(A, D) & zero(B, C)
+        tot = (w[0] * p1 * p3 + w[1] * p1 * p2 + w[2] * p1 * p2) * inb
+        out.append(N ** 3 * tot.sum())
+    return np.array(out)
+
+
+def test_disconnected_trispectrum_matches_wick_enumeration():
+    N, L, e = 10, 50.0, fieldgen.unit_edges(3)
+    d = fieldgen.field("lognormal", N, 5, np.float64)
+    bins = oracle.enumerate_bins(e, 4, oracle.RULE_ALL_SORTED)
+    r = oracle.estimate(d, L, e, 4, bins=bins)
+    Bd, P = oracle.disconnected(d, L, e, bins, r["counts"])
+    Sd = wick_brute_force(d, e, bins)
+    c4 = (L ** 3) ** 3 / float(N ** 3) ** 4
+    ok = r["counts"] > 0
+    ref = np.where(ok, c4 * Sd / (N ** 3 * np.maximum(r["counts"], 1)), 0.0)
+    assert np.count_nonzero(ref) >= 3
+    assert np.allclose(Bd, ref, rtol=1e-12, atol=0.0)
+    # the shell powers are the per-mode power summed over each shell
+    smap = np_shell_map(N, e)
+    pw = np.abs(np.fft.fftn(d)) ** 2
+    assert np.allclose(P, [pw[smap == s].sum() for s in range(3)], rtol=1e-12)
+    # bins (k, k, k, k) pair under all three pairings: a positive disconnected part
+    kk = np.all(bins == bins[:, :1], axis=1)
+    assert np.all(Bd[kk & ok] > 0)
+
+
 def test_counts_n2_are_mode_counts():
     N, e = 16, fieldgen.unit_edges(6)
     bins = oracle.enumerate_bins(e, 2, oracle.RULE_ALL_SORTED)
