@@ -307,7 +307,16 @@ def run_ours(args):
             b.record()
             torch.cuda.synchronize()
             bms.append(a.elapsed_time(b))
+        dms = []
+        for _ in range(3 if ORDER == 4 else 0):  # the trispectrum's disconnected part (optional output)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.disconnected(d)
+            b.record()
+            torch.cuda.synchronize()
+            dms.append(a.elapsed_time(b))
         results[prec] = {"value": value, "ms_per_step": total_ms / args.steps, "roofline": roof,
+                         "disconnected_ms": statistics.median(dms) if dms else None,
                          "plan_ms": plan_ms, "backward_ms": statistics.median(bms) if bms else None,
                          "fields_roofline": fields_roof, "stage_ms": stage, "gpu_launches": launches,
                          "clocks": clk.summary(),
@@ -337,6 +346,9 @@ def run_ours(args):
                     "process; later plans with the same shells reuse the cached counts); outside the timed step"},
         "backward_ms": {"value": h["backward_ms"], "note": "poly_backward, dL/d delta of sum_b w_b B_b on the same "
                         "field, device-timed median of 3"},
+        **({"disconnected_ms": {"value": h["disconnected_ms"], "note": "poly_trispectrum_disconnected on the same "
+                                "field (forward transform, shell powers, per-bin pairings), device-timed median of 3"}}
+           if ORDER == 4 else {}),
         "precisions": {p: ({k: r[k] for k in ("value", "ms_per_step", "roofline", "stage_ms", "e2e", "plan_ms",
                                               "backward_ms")}
                            if "value" in r else r) for p, r in results.items()},

@@ -103,6 +103,24 @@ poly_status poly_plan_counts(poly_plan plan, int64_t* counts);
 poly_status poly_estimate(poly_plan plan, const void* delta_x, double* out, double* scale_or_null, void* stream);
 
 /*
+ * Disconnected (Gaussian, Wick-paired) part of the trispectrum estimate of
+ * delta_x, for order-4 plans (POLY_ERR_UNSUPPORTED otherwise).  The paper's
+ * estimator keeps it; subtract it from poly_estimate's B_b for the connected
+ * part.  Per bin b = (k1 >= k2 >= k3 >= k4), the closed quadrilaterals that
+ * split into two zero-sum pairs, summed over the three pairings with the
+ * measured mode power: with P(k) = sum_{q in S_k} |dhat(q)|^2,
+ *   B_disc_b = c_4 N^3 [d(k1,k2)d(k3,k4) P(k1)P(k3) + d(k1,k3)d(k2,k4) P(k1)P(k2)
+ *                       + d(k1,k4)d(k2,k3) P(k1)P(k2)] / (N^3 count_b),
+ * c_4 = V^3/N^12 as for B_b; zero for bins without two equal pairs.
+ * delta_x: device, N^3 real of the plan's input type.  out: device, nbins
+ * double.  shell_power_or_null: device, nshell double (P(k)), or NULL.
+ * Uses the plan's spectrum workspace (stream-ordered with poly_estimate);
+ * the first call allocates two small device tables.  Asynchronous on `stream`.
+ */
+poly_status poly_trispectrum_disconnected(poly_plan plan, const void* delta_x, double* out, double* shell_power_or_null,
+                                          void* stream);
+
+/*
  * The same as poly_estimate with HOST buffers: copies delta_x (host, N^3 real)
  * to the device, estimates, copies B_b to out (host, nbins double) and
  * synchronises `stream` before returning.

@@ -31,7 +31,8 @@ POLY_ALLOW_ALIAS = 0x2
 ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_plan_counts", "poly_estimate",
                "poly_estimate_host", "poly_backward", "poly_estimate_batched", "poly_plan_sync", "poly_plan_destroy",
                "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
-               "poly_plan_stats", "poly_estimate_noalloc", "poly_plan_tune", "poly_plan_set_config")
+               "poly_plan_stats", "poly_estimate_noalloc", "poly_plan_tune", "poly_plan_set_config",
+               "poly_trispectrum_disconnected")
 
 
 class poly_stats(ctypes.Structure):
@@ -75,6 +76,8 @@ def load_library():
     L.poly_estimate_noalloc.argtypes = [i32, f64, i32, P, P, P, P, P]
     L.poly_plan_tune.argtypes = [P, P, ctypes.POINTER(i32), ctypes.POINTER(f64), P]
     L.poly_plan_set_config.argtypes = [P, i32]
+    L.poly_trispectrum_disconnected.argtypes = [P, P, P, P, P]
+    L.poly_last_error.argtypes = []
     L.poly_debug_fail_alloc_after.argtypes = [i32]
     L.poly_debug_fail_alloc_after.restype = None
     for name in ABI_SYMBOLS:
@@ -129,6 +132,12 @@ def poly_estimate_host(plan: int, delta_host: np.ndarray, out_host: np.ndarray, 
 
 def poly_backward(plan: int, delta_ptr: int, dLdB_ptr: int, grad_ptr: int, stream: int | None) -> None:
     _check(load_library().poly_backward(plan, delta_ptr, dLdB_ptr, grad_ptr, stream), "poly_backward")
+
+
+def poly_trispectrum_disconnected(plan: int, delta_ptr: int, out_ptr: int, power_ptr: int | None,
+                                  stream: int | None) -> None:
+    _check(load_library().poly_trispectrum_disconnected(plan, delta_ptr, out_ptr, power_ptr, stream),
+           "poly_trispectrum_disconnected")
 
 
 def poly_estimate_batched(plans, field_ptrs, out_ptrs, stream: int | None) -> None:
@@ -238,6 +247,19 @@ class Plan:
         grad = torch.empty_like(delta) if grad is None else grad
         poly_backward(self.handle, delta.data_ptr(), g.data_ptr(), grad.data_ptr(), _stream_handle(stream))
         return grad
+
+    def disconnected(self, delta, out=None, power: bool = False, stream=None):
+        """Order-4 plans: the disconnected (Wick-paired) part B_disc of the trispectrum estimate of delta
+        (subtract it from estimate() for the connected part).  Returns B_disc [and the shell powers]."""
+        import torch
+
+        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
+        assert delta.numel() == self.N ** 3
+        out = torch.empty(self.nbins, dtype=torch.float64, device=delta.device) if out is None else out
+        pw = torch.empty(len(self.edges) - 1, dtype=torch.float64, device=delta.device) if power else None
+        poly_trispectrum_disconnected(self.handle, delta.data_ptr(), out.data_ptr(), pw.data_ptr() if power else None,
+                                      _stream_handle(stream))
+        return (out, pw) if power else out
 
     def sync(self, stream=None):
         poly_plan_sync(self.handle, _stream_handle(stream))

@@ -47,6 +47,10 @@ cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* 
 cudaError_t ps_reduce_slots(const double* partial, int nsplit, int64_t slot_stride, const int64_t* slot,
                             int64_t nbins, double* S, cudaStream_t st);
 // out[b] = norm * S[b] / (N^3 count[b])  (0 where count == 0)
+// disconnected part of the trispectrum: shell powers P (device, nshell) from the pruned spectrum, then B_disc per bin
+cudaError_t ps_disconnected(int is_double, const void* fhat, const void* lines, const int* line_off, int nshell, int K,
+                            const int32_t* bins, const int64_t* counts, int64_t nbins, double norm, double n3,
+                            double* P, double* out, cudaStream_t st);
 cudaError_t ps_normalise(const double* S, const int64_t* counts, int64_t nbins, double norm, double n3, double* out,
                          cudaStream_t st);
 

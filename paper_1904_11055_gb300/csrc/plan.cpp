@@ -568,6 +568,26 @@ poly_status ps_estimate_impl(PsPlan* p, const void* delta, double* out, double* 
     return POLY_OK;
 }
 
+// B_disc of every bin (order-4 plans): forward transform, shell powers, per-bin Wick pairings
+static poly_status ps_disconnected_impl(PsPlan* p, const void* delta, double* out, double* power, cudaStream_t st) {
+    if (!p->d_bins) {
+        PS_TRY(upload(p, (void**)&p->d_bins, p->bins));
+        PS_TRY(ps_alloc(p, (void**)&p->d_shell_power, (size_t)p->nshell * sizeof(double)));
+    }
+    cudaError_t e;
+    if ((e = ps_forward(p->N, p->is_double, delta, p->K, p->d_tw_fwd, p->d_W, p->d_fhat, p->d_spill, st)))
+        return cuda_error(e, "forward transform");
+    const double n3 = (double)p->N * p->N * p->N;
+    if ((e = ps_disconnected(p->is_double, p->d_fhat, p->d_lines, p->d_line_off, p->nshell, p->K, p->d_bins,
+                             p->d_counts, p->nbins, ps_norm(p), n3, p->d_shell_power, out, st)))
+        return cuda_error(e, "disconnected part");
+    p->launches += 4;
+    if (power && (e = cudaMemcpyAsync(power, p->d_shell_power, (size_t)p->nshell * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, st)))
+        return cuda_error(e, "shell power copy");
+    return POLY_OK;
+}
+
 static poly_status enter(poly_plan p, int* prev) {
     if (!p) return set_error(POLY_ERR_ARG, "NULL plan");
     *prev = -1;
@@ -636,6 +656,20 @@ poly_status poly_estimate(poly_plan p, const void* delta_x, double* out, double*
     int prev;
     PS_TRY(enter(p, &prev));
     poly_status s = ps_estimate_impl(p, delta_x, out, scale_or_null, (cudaStream_t)stream);
+    leave(p, prev);
+    return s;
+}
+
+poly_status poly_trispectrum_disconnected(poly_plan p, const void* delta_x, double* out, double* shell_power_or_null,
+                                          void* stream) {
+    if (!p || !delta_x || !out) return set_error(POLY_ERR_ARG, "NULL argument");
+    if (p->order != 4) return set_error(POLY_ERR_UNSUPPORTED, "the disconnected part is defined for order-4 plans");
+    if ((const void*)out == delta_x || (const void*)shell_power_or_null == delta_x ||
+        (const void*)shell_power_or_null == (const void*)out)
+        return set_error(POLY_ERR_ARG, "output aliases an input");
+    int prev;
+    PS_TRY(enter(p, &prev));
+    poly_status s = ps_disconnected_impl(p, delta_x, out, shell_power_or_null, (cudaStream_t)stream);
     leave(p, prev);
     return s;
 }

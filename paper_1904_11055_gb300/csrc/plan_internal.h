@@ -66,6 +66,9 @@ struct poly_plan_s {
     void* d_G = nullptr;      // nshell x N^3 real
     void* d_ghat = nullptr;   // union spectrum
     AdjTables* adj = nullptr;
+    // disconnected part of the trispectrum (allocated on first use)
+    int32_t* d_bins = nullptr;     // nbins x order, 1-based shells
+    double* d_shell_power = nullptr;
     // tensor-core contraction: state, and its tunable shape (poly_plan_tune)
     TcState* tc = nullptr;
     int tc_max_mt = 4;    // largest number of M tiles per CTA group

@@ -93,6 +93,12 @@ def test_tuning_and_batched_entries_reject_null_arguments(lib):
     assert lib.poly_estimate_batched(None, None, None, -1, None) == 1
 
 
+def test_every_abi_symbol_declares_its_argument_types(lib):
+    """Without argtypes ctypes passes Python ints as 32-bit C ints, which truncates pointers."""
+    for name in ps.ABI_SYMBOLS:
+        assert getattr(lib, name).argtypes is not None, name
+
+
 def test_binding_wrappers_marshal_without_a_device(lib):
     """Every ABI-named wrapper reaches the library and maps a NULL plan to POLY_ERR_ARG."""
     calls = [
@@ -103,6 +109,7 @@ def test_binding_wrappers_marshal_without_a_device(lib):
         lambda: ps.poly_plan_sync(None),
         lambda: ps.poly_estimate(None, None, None, None, None),
         lambda: ps.poly_backward(None, None, None, None, None),
+        lambda: ps.poly_trispectrum_disconnected(None, None, None, None, None),
     ]
     for call in calls:
         with pytest.raises(ps.PolyError) as ei:

@@ -108,6 +108,34 @@ def test_higher_orders_match_oracle(prec, N, order, nshell, seed):
     assert err.max() <= TOL[prec], err.max()
 
 
+# ------------------------------------------------------------------ disconnected part of the trispectrum
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5), ("split_bf16", 1e-5)])
+@pytest.mark.parametrize("N,nshell,width,seed", [(32, 7, 1.0, 31), (48, 7, 1.5, 32)])
+def test_disconnected_trispectrum_matches_oracle(prec, tol, N, nshell, width, seed):
+    e = fieldgen.unit_edges(nshell, width)
+    d64 = fieldgen.field("lognormal", N, seed, np.float32).astype(np.float64)
+    plan = ps.Plan(N, 1000.0, 4, e, prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    d = torch.from_numpy(d64).to("cuda", dt)
+    Bd, P = plan.disconnected(d, power=True)
+    torch.cuda.synchronize()
+    ref, Pref = oracle.disconnected(d64, 1000.0, e, plan.bins, plan.counts)
+    assert np.allclose(P.cpu().numpy(), Pref, rtol=tol, atol=0.0)
+    got = Bd.cpu().numpy()
+    assert np.array_equal(got == 0.0, ref == 0.0)
+    nz = ref != 0.0
+    assert nz.sum() >= nshell
+    assert np.max(np.abs(got[nz] - ref[nz]) / np.abs(ref[nz])) <= 2 * tol
+
+
+def test_disconnected_part_is_refused_below_order_4():
+    plan = ps.Plan(32, 1000.0, 3, fieldgen.unit_edges(6), "fp32")
+    d = torch.from_numpy(fieldgen.field("lognormal", 32, 3, np.float32)).cuda()
+    with pytest.raises(ps.PolyError) as ei:
+        plan.disconnected(d)
+    assert ei.value.status == 6
+
+
 def test_higher_orders_refuse_split_bf16_and_the_adjoint():
     e = fieldgen.unit_edges(4)
     with pytest.raises(ps.PolyError) as ei:
