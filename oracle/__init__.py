@@ -68,6 +68,7 @@ def _load():
         L.orc_counts_exact.argtypes = [i32, i32, P, i32, i64, P, P]
         L.orc_gradient.argtypes = [i32, f64, P, i32, P, i32, i64, P, P, P, P]
         L.orc_disconnected.argtypes = [i32, f64, P, i32, P, i64, P, P, P, P]
+        L.orc_estimate_ell.argtypes = [i32, f64, P, i32, P, i32, i32, i64, P, P, P, P]
         _lib = L
     return _lib
 
@@ -183,6 +184,19 @@ def counts_exact(N: int, edges, order: int, bins) -> np.ndarray:
     cnt = np.empty(b.shape[0], dtype=np.int64)
     _check(_load().orc_counts_exact(int(N), e.size - 1, _p(e), int(order), b.shape[0], _p(b), _p(cnt)))
     return cnt
+
+
+def estimate_ell(delta, L: float, edges, order: int, ell: int, bins) -> dict:
+    """Multipole estimator: the first leg of each bin weighted by L_ell(q_z/|q|); B (with the 2 ell + 1
+    factor), scale = sum_x |prod| / (N^3 count) with the weighted first leg, counts."""
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    b = np.ascontiguousarray(bins, dtype=np.int32)
+    nb = b.shape[0]
+    B, sc, cnt = np.empty(nb), np.empty(nb), np.empty(nb, dtype=np.int64)
+    _check(_load().orc_estimate_ell(d.shape[0], float(L), _p(d), e.size - 1, _p(e), int(order), int(ell), nb, _p(b),
+                                    _p(B), _p(sc), _p(cnt)))
+    return {"B": B, "scale": sc, "counts": cnt}
 
 
 def disconnected(delta, L: float, edges, bins, counts):

@@ -642,6 +642,120 @@ int orc_counts_exact(int N, int nshell, const double* edges, int order, int64_t 
 }
 
 /* ------------------------------------------------------------------------- */
+/* redshift-space multipoles (the extension the paper points to in Sec. 5,    */
+/* following Scoccimarro 2015): the first leg of each bin carries the         */
+/* Legendre weight L_ell(mu), mu = q_z/|q| (plane-parallel line of sight      */
+/* along the grid's z axis):                                                  */
+/*   D^ell_k(x) = sum_{q in S_k} L_ell(mu_q) dhat(q) e^{+2 pi i q.x/N}         */
+/*   S^ell_b    = sum_x D^ell_{k1}(x) prod_{t > 1} D_{kt}(x)                   */
+/*   B^ell_b    = (2 ell + 1) (V^{n-1}/N^{3n}) S^ell_b / (N^3 count_b)         */
+/* Even ell only: L_ell(-mu) = L_ell(mu) keeps the weighted fields real.      */
+/* ell = 0 is the monopole B_b.                                               */
+/* ------------------------------------------------------------------------- */
+static double legendre(int ell, double mu) {
+    double p0 = 1.0, p1 = mu;
+    if (ell == 0) return p0;
+    for (int n = 1; n < ell; n++) { /* Bonnet: (n+1) P_{n+1} = (2n+1) mu P_n - n P_{n-1} */
+        const double p2 = ((2.0 * n + 1.0) * mu * p1 - n * p0) / (n + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+static int shell_fields_weighted(int N, const double* dhat, const int32_t* smap, int nsel, const int32_t* shells,
+                                 int ell, double* fields) {
+    const size_t n3 = (size_t)N * N * N;
+    cplx* work = (cplx*)malloc(sizeof(cplx) * n3);
+    if (!work) return fail(-2, "orc_estimate_ell: out of memory");
+    const cplx* F = (const cplx*)dhat;
+    for (int t = 0; t < nsel; t++) {
+        for (size_t i = 0; i < n3; i++) {
+            work[i].re = work[i].im = 0.0;
+            if (smap[i] != shells[t]) continue;
+            const int x = (int)(i / ((size_t)N * N)), y = (int)((i / N) % N), z = (int)(i % N);
+            const double qx = x < (N + 1) / 2 ? x : x - N, qy = y < (N + 1) / 2 ? y : y - N,
+                         qz = z < (N + 1) / 2 ? z : z - N;
+            const double w = legendre(ell, qz / sqrt(qx * qx + qy * qy + qz * qz));
+            work[i].re = w * F[i].re;
+            work[i].im = w * F[i].im;
+        }
+        int rc = orc_fft3d((double*)work, N, N, N, +1);
+        if (rc) {
+            free(work);
+            return rc;
+        }
+        for (size_t i = 0; i < n3; i++) fields[(size_t)t * n3 + i] = work[i].re;
+    }
+    free(work);
+    return 0;
+}
+
+int orc_estimate(int N, double L, const double* delta, int nshell, const double* edges, int order, int64_t nbins,
+                 const int32_t* bins, double* B, double* R, double* scale, int64_t* counts, double* S_out,
+                 double* imag_max);
+
+int orc_estimate_ell(int N, double L, const double* delta, int nshell, const double* edges, int order, int ell,
+                     int64_t nbins, const int32_t* bins, double* B, double* scale, int64_t* counts) {
+    if (N < 2 || L <= 0.0 || order < 2 || order > 8 || nbins < 0 || ell < 0 || ell > 8 || (ell & 1))
+        return fail(-1, "orc_estimate_ell: bad args (even ell in [0, 8])");
+    const size_t n3 = (size_t)N * N * N;
+    /* counts: those of the monopole estimator (they do not depend on the weight) */
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nbins > 0 ? nbins : 1));
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    int32_t* slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * nshell + 1));
+    int32_t* sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)nshell);
+    int32_t* bins2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nbins * order > 0 ? nbins * order : 1));
+    double* dhat = (double*)malloc(sizeof(double) * 2 * n3);
+    double* S = (double*)malloc(sizeof(double) * (size_t)(nbins > 0 ? nbins : 1));
+    double* A = (double*)malloc(sizeof(double) * (size_t)(nbins > 0 ? nbins : 1));
+    if (!cnt || !smap || !slot || !sel || !bins2 || !dhat || !S || !A) return fail(-2, "orc_estimate_ell: out of memory");
+    int rc = orc_estimate(N, L, delta, nshell, edges, order, nbins, bins, NULL, NULL, NULL, cnt, NULL, NULL);
+    if (!rc) rc = orc_shell_map(N, nshell, edges, smap);
+    /* fields: [unweighted | weighted] per used shell; the first leg reads "shell" k1 + nshell */
+    int nsel = 0;
+    for (int s = 0; s <= 2 * nshell; s++) slot[s] = -1;
+    for (int64_t i = 0; i < nbins * order && !rc; i++) {
+        const int k = bins[i];
+        if (k < 1 || k > nshell) rc = fail(-1, "orc_estimate_ell: bin shell out of range");
+        else if (slot[k] < 0) {
+            slot[k] = nsel;
+            sel[nsel++] = k - 1;
+        }
+    }
+    for (int s = 1; s <= nshell; s++)
+        if (slot[s] >= 0) slot[s + nshell] = nsel + slot[s];
+    for (int64_t b = 0; b < nbins; b++)
+        for (int t = 0; t < order; t++) bins2[b * order + t] = bins[b * order + t] + (t == 0 ? nshell : 0);
+    double* fields = rc ? NULL : (double*)malloc(sizeof(double) * n3 * (size_t)(2 * (nsel > 0 ? nsel : 1)));
+    if (!rc && !fields) rc = fail(-2, "orc_estimate_ell: out of memory");
+    double im = 0.0;
+    if (!rc) rc = orc_forward(N, delta, dhat);
+    if (!rc) rc = orc_shell_fields(N, dhat, smap, nsel, sel, fields, &im);
+    if (!rc) rc = shell_fields_weighted(N, dhat, smap, nsel, sel, ell, fields + n3 * (size_t)nsel);
+    if (!rc) rc = orc_product_sums(N, fields, slot, order, nbins, bins2, S, A);
+    if (!rc) {
+        const double n3d = (double)n3, norm = (2.0 * ell + 1.0) * pow(L * L * L, order - 1) / pow(n3d, order);
+        for (int64_t b = 0; b < nbins; b++) {
+            const double den = n3d * (double)cnt[b];
+            if (B) B[b] = cnt[b] > 0 ? norm * S[b] / den : 0.0;
+            if (scale) scale[b] = cnt[b] > 0 ? A[b] / den : 0.0;
+            if (counts) counts[b] = cnt[b];
+        }
+    }
+    free(cnt);
+    free(smap);
+    free(slot);
+    free(sel);
+    free(bins2);
+    free(dhat);
+    free(S);
+    free(A);
+    free(fields);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* disconnected part of the trispectrum estimator (n = 4; not in the paper,   */
 /* whose Eq. estimator keeps it): the closed quadrilaterals that split into   */
 /* two zero-sum pairs, summed over the three pairings of Wick's theorem with  */
