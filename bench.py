@@ -28,18 +28,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "bispectrum configs/s at 256³ N_max=64, split-BF16 vs FP32 on GB300 at rel err ≤1e-5"
-N, L, NSHELL, ORDER, SEED, WIDTH = 256, 1000.0, 64, 3, 2, 1.0
+N, L, NSHELL, ORDER, SEED, WIDTH, ELL = 256, 1000.0, 64, 3, 2, 1.0, 0
 WORKLOAD = "bispectrum, 256^3 lognormal field (seed 2), 64 unit shells k_F..64k_F, n=3, 24432 bins"
 
 
-def set_workload(n: int, nshell: int, order: int, width: float = 1.0):
-    """Other sizes (profiling cases, trispectrum); the default is the metric's workload."""
-    global N, NSHELL, ORDER, WORKLOAD, WIDTH
-    if (n, nshell, order, width) == (N, NSHELL, ORDER, WIDTH):
+def set_workload(n: int, nshell: int, order: int, width: float = 1.0, ell: int = 0):
+    """Other sizes (profiling cases, trispectrum, multipoles); the default is the metric's workload."""
+    global N, NSHELL, ORDER, WORKLOAD, WIDTH, ELL
+    if (n, nshell, order, width, ell) == (N, NSHELL, ORDER, WIDTH, ELL):
         return
-    N, NSHELL, ORDER, WIDTH = n, nshell, order, width
-    WORKLOAD = (f"order-{order} polyspectrum, {n}^3 lognormal field (seed 2), {nshell} shells of width {width:g} k_F "
-                f"(not the metric workload)")
+    N, NSHELL, ORDER, WIDTH, ELL = n, nshell, order, width, ell
+    WORKLOAD = (f"order-{order} polyspectrum{f', multipole ell={ell} (first leg)' if ell else ''}, {n}^3 lognormal "
+                f"field (seed 2), {nshell} shells of width {width:g} k_F (not the metric workload)")
 SAMPLE_SHELLS = (59, 60, 61, 62, 63, 64)  # CPU baseline sample: the bins among these shells
 
 
@@ -245,7 +245,7 @@ def run_ours(args):
         try:
             torch.cuda.synchronize()
             t_plan = time.perf_counter()
-            plan = ps.Plan(N, L, ORDER, edges, prec)
+            plan = ps.Plan(N, L, ORDER, edges, prec, ell=ELL)
             torch.cuda.synchronize()
             plan_ms = (time.perf_counter() - t_plan) * 1e3
         except ps.PolyError as e:
@@ -297,10 +297,10 @@ def run_ours(args):
         w = torch.from_numpy(np.random.default_rng(5).standard_normal(plan.nbins)).cuda()
         grad = torch.empty_like(d)
         bms = []
-        if ORDER <= 4:  # the adjoint covers orders 2 to 4
+        if ORDER <= 4 and ELL == 0:  # the adjoint covers monopole plans of orders 2 to 4
             plan.backward(d, w, grad)
             torch.cuda.synchronize()
-        for _ in range(3 if ORDER <= 4 else 0):
+        for _ in range(3 if ORDER <= 4 and ELL == 0 else 0):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             plan.backward(d, w, grad)
@@ -308,7 +308,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             bms.append(a.elapsed_time(b))
         dms = []
-        for _ in range(3 if ORDER == 4 else 0):  # the trispectrum's disconnected part (optional output)
+        for _ in range(3 if ORDER == 4 and ELL == 0 else 0):  # the trispectrum's disconnected part (optional output)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             plan.disconnected(d)
@@ -348,7 +348,7 @@ def run_ours(args):
                         "field, device-timed median of 3"},
         **({"disconnected_ms": {"value": h["disconnected_ms"], "note": "poly_trispectrum_disconnected on the same "
                                 "field (forward transform, shell powers, per-bin pairings), device-timed median of 3"}}
-           if ORDER == 4 else {}),
+           if ORDER == 4 and ELL == 0 else {}),
         "precisions": {p: ({k: r[k] for k in ("value", "ms_per_step", "roofline", "stage_ms", "e2e", "plan_ms",
                                               "backward_ms")}
                            if "value" in r else r) for p, r in results.items()},
@@ -462,10 +462,11 @@ def main():
     ap.add_argument("--nshell", type=int, default=NSHELL)
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--width", type=float, default=1.0, help="shell width in k_F (the trispectrum workload: 1.5)")
+    ap.add_argument("--ell", type=int, default=0, help="redshift-space multipole of the first leg (even; FP32/FP64)")
     ap.add_argument("--workload", default="metric", choices=["metric", "mocks"],
                     help="mocks: 512 mixed-size realisations through poly_estimate_batched")
     args = ap.parse_args()
-    set_workload(args.N, args.nshell, args.order, args.width)
+    set_workload(args.N, args.nshell, args.order, args.width, args.ell)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

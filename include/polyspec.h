@@ -87,6 +87,22 @@ poly_status poly_plan_create(poly_plan* out, int N, double L, int order, int nsh
 /* Number of bins the plan outputs. */
 poly_status poly_plan_nbins(poly_plan plan, int64_t* nbins);
 
+/*
+ * Redshift-space multipoles (the extension Sec. 5 points to): the same as
+ * poly_plan_create, but the first leg k1 of every bin carries the Legendre
+ * weight L_ell(q_z/|q|) (plane-parallel line of sight along the grid's z
+ * axis), and poly_estimate returns
+ *   B^ell_b = (2 ell + 1) c_n sum_x D^ell_{k1}(x) prod_{t>1} D_{kt}(x) / (N^3 count_b),
+ *   D^ell_k(x) = sum_{q in S_k} L_ell(q_z/|q|) dhat(q) e^{+2 pi i q.x/N}.
+ * ell even in [0, 8] (POLY_ERR_ARG otherwise; odd multipoles of a real field
+ * are not real); ell = 0 is poly_plan_create.  POLY_FP32 and POLY_FP64 only
+ * (POLY_ERR_UNSUPPORTED for split-BF16).  The plan holds 2 * nshell fields;
+ * counts are the plain polygon counts.  poly_backward and
+ * poly_trispectrum_disconnected return POLY_ERR_UNSUPPORTED for ell > 0.
+ */
+poly_status poly_plan_create_multipole(poly_plan* out, int N, double L, int order, int nshell, const double* edges,
+                                       poly_precision prec, unsigned flags, int ell);
+
 /* Bins as 1-based shell numbers, host array of nbins * order int32, paper order. */
 poly_status poly_plan_bins(poly_plan plan, int32_t* idx);
 

@@ -32,7 +32,7 @@ ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_pl
                "poly_estimate_host", "poly_backward", "poly_estimate_batched", "poly_plan_sync", "poly_plan_destroy",
                "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
                "poly_plan_stats", "poly_estimate_noalloc", "poly_plan_tune", "poly_plan_set_config",
-               "poly_trispectrum_disconnected")
+               "poly_trispectrum_disconnected", "poly_plan_create_multipole")
 
 
 class poly_stats(ctypes.Structure):
@@ -58,6 +58,7 @@ def load_library():
     L = ctypes.CDLL(LIB_PATH)
     P, i32, i64, f64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint
     L.poly_plan_create.argtypes = [ctypes.POINTER(P), i32, f64, i32, i32, P, i32, u32]
+    L.poly_plan_create_multipole.argtypes = [ctypes.POINTER(P), i32, f64, i32, i32, P, i32, u32, i32]
     L.poly_plan_nbins.argtypes = [P, ctypes.POINTER(i64)]
     L.poly_plan_bins.argtypes = [P, P]
     L.poly_plan_counts.argtypes = [P, P]
@@ -99,6 +100,17 @@ def poly_plan_create(N: int, L: float, order: int, edges, prec: int = POLY_FP32,
     _check(load_library().poly_plan_create(ctypes.byref(h), int(N), float(L), int(order), e.size - 1,
                                            e.ctypes.data_as(ctypes.c_void_p), int(prec), int(flags)),
            "poly_plan_create")
+    return h.value
+
+
+def poly_plan_create_multipole(N: int, L: float, order: int, edges, prec: int = POLY_FP32, flags: int = 0,
+                               ell: int = 0) -> int:
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load_library().poly_plan_create_multipole(ctypes.byref(h), int(N), float(L), int(order), e.size - 1,
+                                                     e.ctypes.data_as(ctypes.c_void_p), int(prec), int(flags),
+                                                     int(ell)),
+           "poly_plan_create_multipole")
     return h.value
 
 
@@ -205,11 +217,15 @@ def _stream_handle(stream):
 class Plan:
     """A plan for one (N, L, n, edges, precision); owns the library handle."""
 
-    def __init__(self, N: int, L: float, order: int, edges, precision: str | int = "fp32", flags: int = 0):
+    def __init__(self, N: int, L: float, order: int, edges, precision: str | int = "fp32", flags: int = 0,
+                 ell: int = 0):
+        """ell > 0: redshift-space multipole plan (the first leg weighted by L_ell(q_z/|q|))."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.N, self.L, self.order, self.prec, self.flags = int(N), float(L), int(order), prec, int(flags)
+        self.ell = int(ell)
         self.edges = np.ascontiguousarray(edges, dtype=np.float64)
-        self.handle = poly_plan_create(N, L, order, self.edges, prec, flags)
+        self.handle = (poly_plan_create(N, L, order, self.edges, prec, flags) if self.ell == 0 else
+                       poly_plan_create_multipole(N, L, order, self.edges, prec, flags, self.ell))
         self.nbins = poly_plan_nbins(self.handle)
         self.bins = poly_plan_bins(self.handle, order)
         self.counts = poly_plan_counts(self.handle)

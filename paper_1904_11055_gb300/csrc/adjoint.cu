@@ -172,8 +172,8 @@ static poly_status adj_prepare(PsPlan* p, AdjTables& A) {
 }
 
 poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, void* dL_ddelta, cudaStream_t st) {
-    if (p->order > 4) {
-        ps_set_last_error("poly_backward supports orders 2 to 4");
+    if (p->order > 4 || p->ell != 0) {
+        ps_set_last_error("poly_backward supports monopole plans of orders 2 to 4");
         return POLY_ERR_UNSUPPORTED;
     }
     if (!p->adj) {

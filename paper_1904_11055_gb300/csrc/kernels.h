@@ -51,6 +51,8 @@ cudaError_t ps_reduce_slots(const double* partial, int nsplit, int64_t slot_stri
 cudaError_t ps_disconnected(int is_double, const void* fhat, const void* lines, const int* line_off, int nshell, int K,
                             const int32_t* bins, const int64_t* counts, int64_t nbins, double norm, double n3,
                             double* P, double* out, cudaStream_t st);
+// out = L_ell(kz/|q|) * fhat over the pruned half spectrum (even ell; the mode q = 0 gets weight 0)
+cudaError_t ps_legendre_weight(int is_double, const void* fhat, int K, int ell, void* out, cudaStream_t st);
 cudaError_t ps_normalise(const double* S, const int64_t* counts, int64_t nbins, double norm, double n3, double* out,
                          cudaStream_t st);
 

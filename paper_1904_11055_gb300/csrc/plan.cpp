@@ -158,8 +158,8 @@ void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& li
 // grouped 64 at a time after sorting by their column span, each group's column
 // union cut into chunks of 64.
 // ---------------------------------------------------------------------------
-void build_cc_tiles(PsPlan* p, CcTiles& t) {
-    using Key = std::array<int, 3>;  // 1-based shells, -1 padded
+void build_cc_tiles(PsPlan* p, CcTiles& t, int first_shift) {
+    using Key = std::array<int, 3>;  // 1-based field slots, -1 padded
     const int n = p->order;
     const int ra = n <= 2 ? 1 : (n <= 5 ? 2 : 3), ca = n - ra;
     auto key = [](const int32_t* b, int cnt) {
@@ -167,7 +167,12 @@ void build_cc_tiles(PsPlan* p, CcTiles& t) {
         for (int i = 0; i < cnt; i++) k[i] = b[i];
         return k;
     };
-    auto rkey = [&](const int32_t* b) { return key(b, ra); };
+    // first_shift > 0: the bin's first leg reads the weighted field slot k1 + first_shift (multipoles)
+    auto rkey = [&](const int32_t* b) {
+        Key k = key(b, ra);
+        k[0] += first_shift;
+        return k;
+    };
     auto ckey = [&](const int32_t* b) { return key(b + ra, ca); };
     std::map<Key, std::vector<Key>> rows;  // row -> col keys
     for (int64_t i = 0; i < p->nbins; i++) rows[rkey(&p->bins[i * n])].push_back(ckey(&p->bins[i * n]));
@@ -379,8 +384,11 @@ static void free_plan(PsPlan* p) {
 }
 
 static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
-                               poly_precision prec, unsigned flags) {
+                               poly_precision prec, unsigned flags, int ell) {
     if (!edges || nshell < 1 || nshell > 128) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
+    if (ell < 0 || ell > 8 || (ell & 1)) return set_error(POLY_ERR_ARG, "ell must be even, in [0, 8]");
+    if (ell > 0 && prec == POLY_SPLIT_BF16)
+        return set_error(POLY_ERR_UNSUPPORTED, "multipole plans run in FP32 or FP64 (CUDA-core contraction)");
     if (order < 2 || order > 6) return set_error(POLY_ERR_UNSUPPORTED, "order must be in [2, 6]");
     if (order > 4 && prec == POLY_SPLIT_BF16)
         return set_error(POLY_ERR_UNSUPPORTED, "split-BF16 plans support orders 2 to 4 (FP32 and FP64: up to 6)");
@@ -398,6 +406,8 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     p->N = N;
     p->L = L;
     p->order = order;
+    p->ell = ell;
+    p->nfield = ell > 0 ? 2 * nshell : nshell;
     p->nshell = nshell;
     p->edges.assign(edges, edges + nshell + 1);
     p->prec = prec;
@@ -455,7 +465,7 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     PS_TRY(upload(p, (void**)&p->d_line_off, off));
 
     // contraction tiles (CUDA-core path; the counts use them too)
-    build_cc_tiles(p, p->cc);
+    build_cc_tiles(p, p->cc, 0);
     PS_TRY(upload(p, &p->d_cc_tiles, p->cc.tiles));
     PS_TRY(upload(p, &p->d_cc_field_ids, p->cc.field_ids));
     PS_TRY(upload(p, &p->d_cc_rowf, p->cc.rowf));
@@ -468,7 +478,8 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     const size_t nl = (size_t)(2 * K + 1) * (K + 1);
     PS_TRY(ps_alloc(p, &p->d_W, (size_t)N * nl * 2 * es));
     PS_TRY(ps_alloc(p, &p->d_fhat, nl * (2 * K + 1) * 2 * es));
-    PS_TRY(ps_alloc(p, &p->d_fields, (size_t)nshell * n3 * es));
+    PS_TRY(ps_alloc(p, &p->d_fields, (size_t)p->nfield * n3 * es));
+    if (ell > 0) PS_TRY(ps_alloc(p, &p->d_fhat_w, nl * (2 * K + 1) * 2 * es));
     {   // x-pass output, indexed by the global line offset: every line of every shell and of
         // the union of the shells (used by the adjoint), at every x
         const size_t lines_all = (size_t)off[nshell + 1];
@@ -492,6 +503,19 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     // exact counts (plan time, cached)
     PS_TRY(compute_counts(p, st));
     PS_CUDA(cudaMemcpy(p->d_counts, p->counts.data(), p->nbins * 8, cudaMemcpyHostToDevice));
+    if (ell > 0) {
+        // the counts used the plain tiles; the estimate's first leg reads the weighted fields
+        for (void* d : {p->d_cc_tiles, p->d_cc_field_ids, p->d_cc_rowf, p->d_cc_colf, p->d_cc_slot}) ps_free(p, d);
+        p->cc = CcTiles();
+        build_cc_tiles(p, p->cc, nshell);
+        PS_TRY(upload(p, &p->d_cc_tiles, p->cc.tiles));
+        PS_TRY(upload(p, &p->d_cc_field_ids, p->cc.field_ids));
+        PS_TRY(upload(p, &p->d_cc_rowf, p->cc.rowf));
+        PS_TRY(upload(p, &p->d_cc_colf, p->cc.colf));
+        PS_TRY(upload(p, &p->d_cc_slot, p->cc.slot));
+        if ((int64_t)p->cc.tiles.size() * kCcTM * kCcTN != p->cc_slot_stride)
+            return set_error(POLY_ERR_ARG, "multipole tiles differ in shape from the plain ones");
+    }
     PS_CUDA(cudaDeviceSynchronize());
     return POLY_OK;
 }
@@ -517,13 +541,31 @@ poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st) {
     if (!ps_xpre_fits(p, 0, p->nshell)) return set_error(POLY_ERR_ARG, "x-pass buffer too small");
     if (p->is_double)
         e = ps_inverse(p->N, 1, 0, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, 0, p->N, p->d_tw_inv,
-                       p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, p->d_xpre, p->max_lines, p->nshell, st);
+                       p->d_fields, (size_t)p->N * p->N * p->N, p->d_spill, p->d_xpre, p->max_lines, p->nfield, st);
     else
         e = ps_inverse_ranged_f32(p->N, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, p->d_tw_inv,
-                                  p->d_fields, (size_t)p->N * p->N * p->N, p->d_xpre, p->max_lines, p->nshell,
+                                  p->d_fields, (size_t)p->N * p->N * p->N, p->d_xpre, p->max_lines, p->nfield,
                                   p->shell_kz.data(), st);
     if (e) return cuda_error(e, "shell fields");
     p->launches += 2;  // x pass + plane kernel
+    if (p->ell > 0) {
+        // multipoles: the Legendre-weighted spectrum through the same inverse, into slots nshell .. 2 nshell - 1
+        // (the cell-tiled layout puts slot s of a 32-cell block at s * 32, so the base moves by nshell * 32)
+        const size_t es = p->is_double ? 8 : 4;
+        void* out_w = (char*)p->d_fields + (size_t)p->nshell * 32 * es;
+        if ((e = ps_legendre_weight(p->is_double, p->d_fhat, p->K, p->ell, p->d_fhat_w, st)))
+            return cuda_error(e, "multipole weights");
+        if (p->is_double)
+            e = ps_inverse(p->N, 1, 0, p->d_fhat_w, p->d_lines, p->d_line_off, 0, p->nshell, p->K, 0, p->N,
+                           p->d_tw_inv, out_w, (size_t)p->N * p->N * p->N, p->d_spill, p->d_xpre, p->max_lines,
+                           p->nfield, st);
+        else
+            e = ps_inverse_ranged_f32(p->N, p->d_fhat_w, p->d_lines, p->d_line_off, 0, p->nshell, p->K, p->d_tw_inv,
+                                      out_w, (size_t)p->N * p->N * p->N, p->d_xpre, p->max_lines, p->nfield,
+                                      p->shell_kz.data(), st);
+        if (e) return cuda_error(e, "weighted shell fields");
+        p->launches += 3;
+    }
     mark(p, 2, st);
     return POLY_OK;
 }
@@ -532,7 +574,7 @@ poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st) {
     cudaError_t e;
     if (p->prec == POLY_SPLIT_BF16 && !absval) return ps_tc_sums(p, st);
     const size_t n3 = (size_t)p->N * p->N * p->N;
-    if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->d_fields, n3, p->nshell, (int64_t)n3, nullptr,
+    if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->d_fields, n3, p->nfield, (int64_t)n3, nullptr,
                             (const PsTile*)p->d_cc_tiles, (int)p->cc.tiles.size(), (const int*)p->d_cc_field_ids,
                             (const short4*)p->d_cc_rowf, (const short4*)p->d_cc_colf, p->cc_nsplit, p->cc_cps,
                             p->d_partial, st)))
@@ -545,9 +587,9 @@ poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st) {
     return POLY_OK;
 }
 
-double ps_norm(const PsPlan* p) {
+double ps_norm(const PsPlan* p) {  // c_n, times 2 ell + 1 for a multipole plan
     const double n3 = (double)p->N * p->N * p->N;
-    return std::pow(p->L * p->L * p->L, p->order - 1) / std::pow(n3, p->order);
+    return (2.0 * p->ell + 1.0) * std::pow(p->L * p->L * p->L, p->order - 1) / std::pow(n3, p->order);
 }
 
 poly_status ps_estimate_impl(PsPlan* p, const void* delta, double* out, double* scale, cudaStream_t st) {
@@ -610,6 +652,11 @@ extern "C" {
 
 poly_status poly_plan_create(poly_plan* out, int N, double L, int order, int nshell, const double* edges,
                              poly_precision prec, unsigned flags) {
+    return poly_plan_create_multipole(out, N, L, order, nshell, edges, prec, flags, 0);
+}
+
+poly_status poly_plan_create_multipole(poly_plan* out, int N, double L, int order, int nshell, const double* edges,
+                                       poly_precision prec, unsigned flags, int ell) {
     if (!out) return set_error(POLY_ERR_ARG, "NULL output pointer");
     *out = nullptr;
     g_last_error.clear();
@@ -617,7 +664,7 @@ poly_status poly_plan_create(poly_plan* out, int N, double L, int order, int nsh
     if (!p) return set_error(POLY_ERR_ALLOC, "host allocation failed");
     poly_status s;
     try {
-        s = create_plan(p, N, L, order, nshell, edges, prec, flags);
+        s = create_plan(p, N, L, order, nshell, edges, prec, flags, ell);
     } catch (const std::bad_alloc&) {
         s = set_error(POLY_ERR_ALLOC, "host allocation failed");
     } catch (const std::exception& ex) {
@@ -663,7 +710,8 @@ poly_status poly_estimate(poly_plan p, const void* delta_x, double* out, double*
 poly_status poly_trispectrum_disconnected(poly_plan p, const void* delta_x, double* out, double* shell_power_or_null,
                                           void* stream) {
     if (!p || !delta_x || !out) return set_error(POLY_ERR_ARG, "NULL argument");
-    if (p->order != 4) return set_error(POLY_ERR_UNSUPPORTED, "the disconnected part is defined for order-4 plans");
+    if (p->order != 4 || p->ell != 0)
+        return set_error(POLY_ERR_UNSUPPORTED, "the disconnected part is defined for order-4 monopole plans");
     if ((const void*)out == delta_x || (const void*)shell_power_or_null == delta_x ||
         (const void*)shell_power_or_null == (const void*)out)
         return set_error(POLY_ERR_ARG, "output aliases an input");

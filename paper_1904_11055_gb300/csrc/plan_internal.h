@@ -30,6 +30,8 @@ struct poly_plan_s {
     unsigned flags = 0;
     int is_double = 0;
     int K = 0;  // largest integer wavevector component inside the outer shell
+    int ell = 0;     // multipole of the first leg (0: the monopole estimator)
+    int nfield = 0;  // field slots in the cell-tiled array: nshell, or 2 nshell with the weighted set for ell > 0
     int device = -1;
     int sms = 0;
     // bins and counts (host)
@@ -55,6 +57,7 @@ struct poly_plan_s {
     // workspace
     void* d_W = nullptr;       // forward intermediate, N x (2K+1)(K+1) complex
     void* d_fhat = nullptr;    // pruned half spectrum, (2K+1)(K+1)(2K+1) complex
+    void* d_fhat_w = nullptr;  // the same weighted by L_ell(kz/|q|) (ell > 0)
     void* d_fields = nullptr;  // nshell x N^3 real
     void* d_spill = nullptr;   // plane-kernel overflow (FP64 at large K)
     double* d_partial = nullptr;
@@ -89,7 +92,7 @@ void ps_set_last_error(const std::string& msg);
 // host-side tables (plan.cpp)
 void enumerate_bins(int nshell, const std::vector<double>& edges, int order, bool all_sorted, std::vector<int32_t>& out);
 void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines);
-void build_cc_tiles(PsPlan* p, CcTiles& t);
+void build_cc_tiles(PsPlan* p, CcTiles& t, int first_shift = 0);
 poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st);
 // true when the x-pass buffer holds shells [s0, s0 + ns) (global line offsets)
 bool ps_xpre_fits(const PsPlan* p, int s0, int ns);

@@ -136,6 +136,33 @@ def test_disconnected_part_is_refused_below_order_4():
     assert ei.value.status == 6
 
 
+# ------------------------------------------------------------------ redshift-space multipoles (first leg L_ell)
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("N,order,nshell,ell,seed", [(32, 3, 8, 2, 41), (48, 3, 12, 4, 42), (32, 4, 6, 2, 43)])
+def test_multipoles_match_oracle(prec, N, order, nshell, ell, seed):
+    e = fieldgen.unit_edges(nshell)
+    d64 = fieldgen.field("lognormal", N, seed, np.float32).astype(np.float64)
+    plan = ps.Plan(N, 1000.0, order, e, prec, ell=ell)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    B = plan.estimate(torch.from_numpy(d64).to("cuda", dt)).cpu().numpy()
+    ref = oracle.estimate_ell(d64, 1000.0, e, order, ell, plan.bins)
+    assert np.array_equal(plan.counts, ref["counts"])
+    err = np.abs(B - ref["B"]) / ((2 * ell + 1) * norm(1000.0, N, order) * ref["scale"])
+    assert err.max() <= TOL[prec], err.max()
+    assert np.abs(ref["B"]).max() > 0
+
+
+def test_multipole_zero_is_the_plain_plan_and_refuses_the_adjoint():
+    e = fieldgen.unit_edges(6)
+    d = torch.from_numpy(fieldgen.field("lognormal", 32, 5, np.float32)).cuda()
+    plain, m0 = ps.Plan(32, 1000.0, 3, e, "fp32"), ps.Plan(32, 1000.0, 3, e, "fp32", ell=0)
+    assert torch.equal(plain.estimate(d), m0.estimate(d))
+    m2 = ps.Plan(32, 1000.0, 3, e, "fp32", ell=2)
+    with pytest.raises(ps.PolyError) as ei:
+        m2.backward(d, torch.ones(m2.nbins, dtype=torch.float64, device="cuda"))
+    assert ei.value.status == 6
+
+
 def test_higher_orders_refuse_split_bf16_and_the_adjoint():
     e = fieldgen.unit_edges(4)
     with pytest.raises(ps.PolyError) as ei:
