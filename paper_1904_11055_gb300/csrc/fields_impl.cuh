@@ -237,7 +237,7 @@ struct HalfPairReader {  // Z(kz) built from rows y1, y2 of Hb (kz lines)
 // Output layout of the shell fields: natural [s][x][y][z] (tile_ns == 0), or
 // cell-tiled [cell / 32][s][cell % 32] over tile_ns shells, so that one 32-cell
 // chunk of every shell is one contiguous block (what the contractions stream).
-template <typename T>
+template <typename T, int N>
 struct RowPairWriter {  // final stage: real part -> row y1, imaginary part -> row y2
     T* plane;       // natural layout: this plane's first cell
     T* base;        // tiled layout: the whole field array
@@ -249,8 +249,17 @@ struct RowPairWriter {  // final stage: real part -> row y1, imaginary part -> r
     PS_DEV void write(int l, int pos, Cx<T> v) const {
         const int y1 = y0 + 2 * l, y2 = y1 + 1;
         if (tile_ns > 0) {
-            base[at(y1, pos)] = v.re;
-            if (y2 < n) base[at(y2, pos)] = v.im;
+            if constexpr (N % 32 == 0) {
+                // a row starts a 32-cell block: cell (y, pos) lies in block row(y) + pos / 32 at pos % 32,
+                // and row y + 1 starts N / 32 blocks later
+                const size_t blk = (((size_t)x * N + y1) * N) >> 5;
+                T* r = base + blk * (size_t)tile_ns * 32 + (size_t)s * 32 + (size_t)(pos >> 5) * tile_ns * 32 + (pos & 31);
+                r[0] = v.re;
+                if (y2 < N) r[(size_t)(N / 32) * tile_ns * 32] = v.im;
+            } else {
+                base[at(y1, pos)] = v.re;
+                if (y2 < n) base[at(y2, pos)] = v.im;
+            }
         } else {
             plane[(size_t)y1 * n + pos] = v.re;
             if (y2 < n) plane[(size_t)y2 * n + pos] = v.im;
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) inv_plane_kernel(
     for (int p0 = warp * LPW; p0 < npairs; p0 += WARPS * LPW) {
         const int nl = min(LPW, npairs - p0);
         HalfPairReader<T> rd{Hb, ls, Ks, N, 2 * p0};
-        RowPairWriter<T> wr{plane, out, 2 * p0, N, x, s, tile_ns};
+        RowPairWriter<T, N> wr{plane, out, 2 * p0, N, x, s, tile_ns};
         warp_fft<T, N, +1>(zb, nl, s_tw, lane, rd, wr);
     }
 }
