@@ -177,7 +177,7 @@ poly_status poly_estimate_batched(const poly_plan* plans, const void* const* fie
  * Autotuner for the plan's contraction shape (no counterpart in the paper).
  * For a POLY_SPLIT_BF16 plan it times the tensor-core contraction on the
  * shell fields of delta_x (device, N^3 float) for each candidate shape:
- * at most 2, 3 or 4 M tiles per CTA group, and a CTA budget of 1/2, 1 or 2
+ * at most 2, 3 or 4 M tiles per CTA group, and a CTA budget of 1/2, 1, 2, 3 or 4
  * times the SM count.  The plan keeps the fastest.  config_out receives an
  * opaque code for it (give it to poly_plan_set_config to restore the choice
  * without timing, e.g. from a cache on disk) and ms_out the contraction time

@@ -805,7 +805,9 @@ static poly_status apply_tc_config(PsPlan* p, int max_mt, int cta_mult) {
 static bool decode_config(int config, int* max_mt, int* cta_mult) {
     *max_mt = config & 15;
     *cta_mult = (config >> 4) & 15;
-    return *max_mt >= 1 && *max_mt <= 4 && (*cta_mult == 1 || *cta_mult == 2 || *cta_mult == 4) && (config >> 8) == 0;
+    return *max_mt >= 1 && *max_mt <= 4 && (*cta_mult == 1 || *cta_mult == 2 || *cta_mult == 4 || *cta_mult == 6 ||
+                                            *cta_mult == 8) &&
+           (config >> 8) == 0;
 }
 
 poly_status poly_plan_tune(poly_plan p, const void* delta_x, int* config_out, double* ms_out, void* stream) {
@@ -825,7 +827,7 @@ poly_status poly_plan_tune(poly_plan p, const void* delta_x, int* config_out, do
     float best = -1.f;
     int best_mt = old_mt, best_mult = old_mult;
     for (int mt = 2; mt <= 4 && !s; mt++)
-        for (int mult : {1, 2, 4}) {
+        for (int mult : {1, 2, 4, 6, 8}) {  // CTA budget of 1/2 to 4 waves
             if (s) break;
             poly_status a = apply_tc_config(p, mt, mult);
             if (a == POLY_ERR_UNSUPPORTED) continue;  // this grouping does not fit
