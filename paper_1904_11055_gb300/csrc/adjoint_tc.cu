@@ -16,14 +16,15 @@
 // chunk j is a fixed offset and the epilogue reads the 16 D_j of its cell at
 // fixed shared-memory offsets.  A chunk is kept only where m has an entry.
 //
-// A block owns one group of m's (all their chunks, at most 512 - K columns)
+// A block owns one group of m's (all their chunks, at most (512 - K) / 2 columns)
 // and a range of 128-cell tiles.  A tile's fields are four contiguous blocks of
 // the cell-tiled layout; one thread of the MMA warp brings them into shared
-// memory with bulk copies, two tiles ahead (double buffer), into rows padded
-// with zeros up to K.  Eight cell warps (two per TMEM lane quadrant) write A,
-// and after the MMAs run the epilogue, each over one half of the group's m's;
-// the MMA warp issues the MMAs.  The accumulators and A are single-buffered: a
-// tile's MMAs wait for the previous tile's epilogue.
+// memory with bulk copies into three buffers, rows padded with zeros up to K.
+// Eight cell warps (two per TMEM lane quadrant) write A and run the epilogue,
+// each over one half of the group's m's; the MMA warp issues the MMAs.  The
+// accumulators are double-buffered (two halves of TMEM next to A): once the
+// MMAs of tile t are done, the cell warps write A of tile t + 1, whose MMAs
+// then run while the cell warps reduce tile t.
 #include <cuda.h>
 
 #include <algorithm>
@@ -44,6 +45,7 @@ constexpr int kAtThreads = 32 * kAtCellWarps + 32;  // + the MMA warp
 constexpr int kAtMaxRuns = 2;                       // N runs of <= 256 columns per group
 constexpr int kAtMaxK = 128;                        // padded shell count (K) at most
 constexpr int kAtChunk = 16;                        // columns per chunk (one j block)
+constexpr int kAtDBufs = 3;                         // field tiles in flight (t - 1 in its epilogue, t, t + 1)
 
 struct AtGroup {
     int chunk_off, nchunk;    // chunks [chunk_off, chunk_off + nchunk) of the chunk table
@@ -68,8 +70,9 @@ __global__ void at_scatter_kernel(const float* __restrict__ w, const int* __rest
 
 // chunk[c]: bits 0-7 jb, bits 8-15 m, bit 16: last chunk of its m.
 // D: cell-tiled fields, [cell / 32][nshell][cell % 32]; ncell a multiple of 32.
+// acap: TMEM columns of one accumulator buffer (two buffers at columns 0 and acap; A at 512 - kp).
 __global__ void __launch_bounds__(kAtThreads, 1)
-    at_contract_kernel(const float* __restrict__ D, int nshell, int kp, int64_t ntile, int64_t ncell,
+    at_contract_kernel(const float* __restrict__ D, int nshell, int kp, int acap, int64_t ntile, int64_t ncell,
                        const AtGroup* __restrict__ groups, int ngroups, int ranges, const int* __restrict__ chunks,
                        const uint8_t* __restrict__ bhi_g, const uint8_t* __restrict__ blo_g, float* __restrict__ G,
                        int* __restrict__ err) {
@@ -83,34 +86,37 @@ __global__ void __launch_bounds__(kAtThreads, 1)
     const int dfloats = kAtCells * kp;        // one tile of fields, [4][kp][32]
     uint8_t* s_bh = smem_raw;                 // [ncol/8][kp/8] core matrices
     uint8_t* s_bl = smem_raw + bbytes;
-    float* s_d = reinterpret_cast<float*>(smem_raw + 2 * bbytes);  // two tiles
-    int* s_chunk = reinterpret_cast<int*>(s_d + 2 * dfloats);
+    float* s_d = reinterpret_cast<float*>(smem_raw + 2 * bbytes);  // kAtDBufs tiles
+    int* s_chunk = reinterpret_cast<int*>(s_d + kAtDBufs * dfloats);
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_chunk + ((grp.nchunk + 1) & ~1));
-    uint64_t* a_ready = bars;
-    uint64_t* acc_ready = bars + 1;
-    uint64_t* drain = bars + 2;
-    uint64_t* d_full = bars + 3;  // two
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 5);
+    uint64_t* a_ready = bars;        // A of the next tile written (8 cell warps)
+    uint64_t* acc_full = bars + 1;   // [2] the MMAs into accumulator buffer b completed
+    uint64_t* acc_free = bars + 3;   // [2] the epilogue read accumulator buffer b (8 cell warps)
+    uint64_t* drain = bars + 5;
+    uint64_t* d_full = bars + 6;     // [kAtDBufs] a tile's fields landed
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 6 + kAtDBufs);
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // B of this group, the chunk table, and the zero rows [nshell, kp) of both field buffers
+    // B of this group, the chunk table, and the zero rows [nshell, kp) of every field buffer
     for (int i = tid; i < bbytes / 16; i += kAtThreads) {
         reinterpret_cast<uint4*>(s_bh)[i] = reinterpret_cast<const uint4*>(bhi_g + grp.b_off)[i];
         reinterpret_cast<uint4*>(s_bl)[i] = reinterpret_cast<const uint4*>(blo_g + grp.b_off)[i];
     }
     for (int c = tid; c < grp.nchunk; c += kAtThreads) s_chunk[c] = chunks[grp.chunk_off + c];
     const int npad = (kp - nshell) * 32;
-    for (int i = tid; i < 8 * npad; i += kAtThreads) {
+    for (int i = tid; i < 4 * kAtDBufs * npad; i += kAtThreads) {
         const int blk = i / npad, r = i - blk * npad;  // blk: buffer * 4 + quadrant
         s_d[(blk >> 2) * dfloats + (blk & 3) * kp * 32 + nshell * 32 + r] = 0.f;
     }
     if (tid == 0) {
         tc::mbar_init(a_ready, kAtCellWarps);
-        tc::mbar_init(acc_ready, 1);
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(acc_full + b, 1);
+            tc::mbar_init(acc_free + b, kAtCellWarps);
+        }
         tc::mbar_init(drain, 1);
-        tc::mbar_init(d_full, 1);
-        tc::mbar_init(d_full + 1, 1);
+        for (int b = 0; b < kAtDBufs; b++) tc::mbar_init(d_full + b, 1);
         tc::mbar_fence_init();
         *s_abort = 0;
     }
@@ -129,9 +135,10 @@ __global__ void __launch_bounds__(kAtThreads, 1)
     if (warp == kAtCellWarps) {
         // ------------------------------------------------------ field copies, MMA issue
         const bool el = tc::elect_one();
-        int64_t last[2] = {-1, -1};  // last tile copied into each buffer
+        int64_t last[kAtDBufs];  // last tile copied into each buffer
+        for (int b = 0; b < kAtDBufs; b++) last[b] = -1;
         auto load_tile = [&](int64_t t) {
-            const int b = (int)((t - t0) & 1);
+            const int b = (int)((t - t0) % kAtDBufs);
             const int64_t c0 = t * kAtCells;
             const int nq = (int)((ncell - c0 < kAtCells ? ncell - c0 : kAtCells) / 32);
             const uint32_t qbytes = (uint32_t)nshell * 32u * 4u;
@@ -140,38 +147,34 @@ __global__ void __launch_bounds__(kAtThreads, 1)
                 tc::bulk_load(s_d + b * dfloats + q * kp * 32, D + (size_t)(c0 + 32 * q) * nshell, qbytes, d_full + b);
             last[b] = t;
         };
-        if (el)
-            for (int64_t t = t0; t < t1 && t < t0 + 2; t++) load_tile(t);
+        if (el && t0 < t1) load_tile(t0);
         const uint32_t bh = tc::smem_u32(s_bh), bl = tc::smem_u32(s_bl);
         const uint64_t desc_k = ((uint64_t)(((sbo >> 4) & 0x3FFFu) | (1u << 14)) << 32) | (uint64_t)((128u >> 4) << 16);
-        uint32_t ph = 0;
+        const uint32_t idesc = tc::idesc_bf16(128, ncol);  // ncol <= acap <= 240: one MMA run
         for (int64_t t = t0; t < t1; t++) {
-            if (!tc::mbar_wait_warp(a_ready, ph, s_abort)) break;
-            ph ^= 1u;
+            const int64_t k = t - t0;
+            const int b = (int)(k & 1);
+            if (!tc::mbar_wait_warp(a_ready, (uint32_t)(k & 1), s_abort)) break;
+            // the epilogue of tile t - 2 has read accumulator buffer b
+            if (k >= 2 && !tc::mbar_wait_warp(acc_free + b, (uint32_t)(((k >> 1) - 1) & 1), s_abort)) break;
             tc::fence_after_sync();
             if (el) {
-                // the epilogue of tile t - 1 is done: its buffer takes tile t + 1
-                if (t > t0 && t + 1 < t1) load_tile(t + 1);
-                for (int r = 0; r < kAtMaxRuns; r++) {
-                    const int n0 = r * 256;
-                    if (n0 >= ncol) break;
-                    const int nn = ncol - n0 < 256 ? ncol - n0 : 256;
-                    const uint32_t idesc = tc::idesc_bf16(128, nn);
-                    uint32_t acc = 0u;
-                    for (int ks = 0; ks < kp / 16; ks++) {
-                        if (!((grp.kmask[r] >> ks) & 1)) continue;
-                        const uint32_t bo = (uint32_t)(n0 / 8) * sbo + (uint32_t)ks * 256u;
-                        const uint64_t dh = desc_k | (uint64_t)(((bh + bo) >> 4) & 0x3FFFu);
-                        const uint64_t dl = desc_k | (uint64_t)(((bl + bo) >> 4) & 0x3FFFu);
-                        const uint32_t ah = tmem + a0 + (uint32_t)(ks * 8), al = ah + (uint32_t)(kp / 2);
-                        const uint32_t d = tmem + (uint32_t)n0;
-                        tc::mma_ts(d, ah, dh, idesc, acc);  // hi x hi
-                        tc::mma_ts(d, ah, dl, idesc, 1u);   // hi x lo
-                        tc::mma_ts(d, al, dh, idesc, 1u);   // lo x hi
-                        acc = 1u;
-                    }
+                // the epilogue of tile t - 2 is done: its field buffer takes tile t + 1
+                if (t + 1 < t1) load_tile(t + 1);
+                uint32_t acc = 0u;
+                for (int ks = 0; ks < kp / 16; ks++) {
+                    if (!((grp.kmask[0] >> ks) & 1)) continue;
+                    const uint32_t bo = (uint32_t)ks * 256u;
+                    const uint64_t dh = desc_k | (uint64_t)(((bh + bo) >> 4) & 0x3FFFu);
+                    const uint64_t dl = desc_k | (uint64_t)(((bl + bo) >> 4) & 0x3FFFu);
+                    const uint32_t ah = tmem + a0 + (uint32_t)(ks * 8), al = ah + (uint32_t)(kp / 2);
+                    const uint32_t d = tmem + (uint32_t)(b * acap);
+                    tc::mma_ts(d, ah, dh, idesc, acc);  // hi x hi
+                    tc::mma_ts(d, ah, dl, idesc, 1u);   // hi x lo
+                    tc::mma_ts(d, al, dh, idesc, 1u);   // lo x hi
+                    acc = 1u;
                 }
-                tc::mma_commit(acc_ready);
+                tc::mma_commit(acc_full + b);
             }
             __syncwarp();
         }
@@ -180,10 +183,10 @@ __global__ void __launch_bounds__(kAtThreads, 1)
             tc::mma_commit(drain);
             volatile int no_abort = 0;
             tc::mbar_wait(drain, 0, &no_abort);
-            for (int b = 0; b < 2; b++)
+            for (int b = 0; b < kAtDBufs; b++)
                 if (last[b] >= 0) {
                     no_abort = 0;
-                    tc::mbar_wait(d_full + b, (uint32_t)(((last[b] - t0) >> 1) & 1), &no_abort);
+                    tc::mbar_wait(d_full + b, (uint32_t)(((last[b] - t0) / kAtDBufs) & 1), &no_abort);
                 }
         }
         __syncwarp();
@@ -192,13 +195,12 @@ __global__ void __launch_bounds__(kAtThreads, 1)
         const int q = warp & 3, h = warp >> 2;  // lane quadrant, half of the m's
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int c_begin = h ? grp.hsplit : 0, c_end = h ? grp.nchunk : grp.hsplit;
-        uint32_t ph = 0;
-        for (int64_t t = t0; t < t1; t++) {
-            const int b = (int)((t - t0) & 1);
-            if (!tc::mbar_wait_warp(d_full + b, (uint32_t)(((t - t0) >> 1) & 1), s_abort)) break;
-            const float* sd = s_d + b * dfloats + q * kp * 32 + lane;  // shell s at sd[32 s], s < kp
-            const int64_t cell = t * kAtCells + 32 * q + lane;
-            // A: hi/lo pairs of shells, 32 shells per store pair; the two halves take alternate blocks
+        // A of tile t (hi/lo pairs of shells, 32 shells per store pair; the two halves take alternate blocks)
+        auto build_a = [&](int64_t t) -> bool {
+            const int64_t k = t - t0;
+            const int b = (int)(k % kAtDBufs);
+            if (!tc::mbar_wait_warp(d_full + b, (uint32_t)((k / kAtDBufs) & 1), s_abort)) return false;
+            const float* sd = s_d + b * dfloats + q * kp * 32 + lane;
             for (int k0 = 32 * h; k0 < kp; k0 += 64) {
                 uint32_t hi[16], lo[16];
 #pragma unroll
@@ -210,15 +212,24 @@ __global__ void __launch_bounds__(kAtThreads, 1)
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(a_ready);
-            if (!tc::mbar_wait_warp(acc_ready, ph, s_abort)) break;
-            ph ^= 1u;
+            return true;
+        };
+        bool ok = t0 >= t1 || build_a(t0);
+        for (int64_t t = t0; t < t1 && ok; t++) {
+            const int64_t k = t - t0;
+            const int b = (int)(k & 1);
+            if (!tc::mbar_wait_warp(acc_full + b, (uint32_t)((k >> 1) & 1), s_abort)) break;
             tc::fence_after_sync();
+            // the MMAs of tile t are done with A: write the next tile's, so its MMAs run during this epilogue
+            if (t + 1 < t1 && !build_a(t + 1)) break;
             // G_m(x) = sum over m's chunks (m, jb) of sum_i D_{16 jb + i}(x) T[x][(m, 16 jb + i)]
+            const float* sd = s_d + (int)(k % kAtDBufs) * dfloats + q * kp * 32 + lane;
+            const int64_t cell = t * kAtCells + 32 * q + lane;
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             for (int c = c_begin; c < c_end; c++) {
                 const int cd = s_chunk[c];
                 uint32_t v[16];
-                tc::tmem_ld16(tmem + lane_base + (uint32_t)(c * kAtChunk), v);
+                tc::tmem_ld16(tmem + lane_base + (uint32_t)(b * acap + c * kAtChunk), v);
                 const float* dj = sd + 32 * kAtChunk * (cd & 255);
                 float x[16];
 #pragma unroll
@@ -232,6 +243,8 @@ __global__ void __launch_bounds__(kAtThreads, 1)
                 }
             }
             tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(acc_free + b);
         }
     }
     tc::fence_before_sync();
@@ -250,7 +263,7 @@ using namespace ps;
 struct AtState {
     std::vector<AtGroup> groups;
     std::vector<int> empty_m;  // shells with no entry: G_m = 0
-    int kp = 0, ranges = 1, max_nchunk = 0;
+    int kp = 0, acap = 0, ranges = 1, max_nchunk = 0;
     size_t smem = 0;
     void *d_groups = nullptr, *d_chunks = nullptr, *d_pos = nullptr, *d_bhi = nullptr, *d_blo = nullptr;
     int* d_err = nullptr;
@@ -259,7 +272,8 @@ struct AtState {
 
 static size_t at_smem_bytes(int nchunk, int kp) {
     const size_t ncol = (size_t)nchunk * kAtChunk;
-    return 2 * ncol / 8 * kp * 16 + 2 * (size_t)kAtCells * kp * 4 + (size_t)(nchunk + 1) * 4 + 64;
+    return 2 * ncol / 8 * kp * 16 + kAtDBufs * (size_t)kAtCells * kp * 4 + (size_t)(nchunk + 1) * 4 + 8 * (8 + kAtDBufs) +
+           16;
 }
 
 // ent: the adjoint's entries in order (m ascending), each (m, f1, f2) with f1 <= f2.
@@ -283,7 +297,9 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
     }
     // groups of consecutive m's within TMEM (512 - kp columns) and the block's shared memory, split into
     // two halves of about equal chunk counts
-    const int chunk_cap = std::min(kAtMaxRuns * 256, (512 - kp) / 16 * 16) / kAtChunk;
+    // two accumulator buffers next to A: acap columns each, one MMA run of at most 256
+    S->acap = std::min(256, (512 - kp) / 2 / 32 * 32);  // each buffer starts on a 32-column boundary
+    const int chunk_cap = S->acap / kAtChunk;
     auto fits = [&](int nchunk) { return nchunk <= chunk_cap && at_smem_bytes(nchunk, kp) <= 227 * 1024; };
     std::vector<int> chunks;
     std::map<std::pair<int, int>, std::pair<int, int>> chpos;  // (m, jb) -> (group, chunk)
@@ -375,7 +391,7 @@ cudaError_t ps_at_contract(PsPlan* p, AtState* S, const float* w, cudaStream_t s
         if ((e = cudaMemsetAsync((float*)p->d_G + (size_t)m * ncell, 0, (size_t)ncell * 4, st))) return e;
     const int64_t ntile = (ncell + kAtCells - 1) / kAtCells;
     const unsigned nblk = (unsigned)(S->groups.size() * (size_t)S->ranges);
-    at_contract_kernel<<<nblk, kAtThreads, S->smem, st>>>((const float*)p->d_fields, p->nshell, S->kp, ntile, ncell,
+    at_contract_kernel<<<nblk, kAtThreads, S->smem, st>>>((const float*)p->d_fields, p->nshell, S->kp, S->acap, ntile, ncell,
                                                           (const AtGroup*)S->d_groups, (int)S->groups.size(), S->ranges,
                                                           (const int*)S->d_chunks, (const uint8_t*)S->d_bhi,
                                                           (const uint8_t*)S->d_blo, (float*)p->d_G, S->d_err);
