@@ -226,6 +226,37 @@ def test_full_size_trispectrum_256cube_sampled(prec, field256, oracle256_n4):
     assert err.max() <= TOL[prec], err.max()
 
 
+def test_order5_128cube_sampled():
+    """n = 5 at the size bench.py measures it (128^3, 16 unit shells, 15,056 bins), FP32, on the bins among
+    five shells; counts bit-exact."""
+    e = fieldgen.unit_edges(16)
+    d = fieldgen.field("lognormal", 128, 2, np.float32)
+    plan, B = gpu_estimate(d, 1000.0, e, 5, "fp32")
+    assert plan.nbins == 15056
+    shells = {16, 15, 9, 4, 1}
+    idx = np.array([i for i, b in enumerate(plan.bins) if set(b.tolist()) <= shells])
+    assert len(idx) >= 30
+    ref = oracle.estimate(d.astype(np.float64), 1000.0, e, 5, bins=plan.bins[idx])
+    assert np.array_equal(plan.counts[idx], ref["counts"])
+    err = np.abs(B[idx] - ref["B"]) / (norm(1000.0, 128, 5) * ref["scale"])
+    assert err.max() <= TOL["fp32"], err.max()
+
+
+def test_quadrupole_256cube_sampled(field256):
+    """ell = 2 multipole bispectrum at 256^3 with 64 unit shells (the size bench.py measures), FP32, on the
+    triangles among five shells."""
+    e = fieldgen.unit_edges(64)
+    plan = ps.Plan(256, 1000.0, 3, e, "fp32", ell=2)
+    B = plan.estimate(torch.from_numpy(field256).cuda()).cpu().numpy()
+    shells = {64, 40, 33, 17, 2}
+    idx = np.array([i for i, b in enumerate(plan.bins) if set(b.tolist()) <= shells])
+    assert len(idx) >= 10
+    ref = oracle.estimate_ell(field256.astype(np.float64), 1000.0, e, 3, 2, plan.bins[idx])
+    assert np.array_equal(plan.counts[idx], ref["counts"])
+    err = np.abs(B[idx] - ref["B"]) / (5 * norm(1000.0, 256, 3) * ref["scale"])
+    assert err.max() <= TOL["fp32"], err.max()
+
+
 # ------------------------------------------------------------------ entry points agree bit for bit
 def test_host_entry_matches_device_entry():
     d = fieldgen.field("lognormal", 32, 5, np.float32)
