@@ -52,7 +52,7 @@ typedef enum {
     POLY_ERR_ALLOC = 3,       /* device or host allocation failed */
     POLY_ERR_CUDA = 4,        /* a CUDA runtime call or kernel failed */
     POLY_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (see poly_plan_sync) */
-    POLY_ERR_UNSUPPORTED = 6, /* valid request outside what this build implements */
+    POLY_ERR_UNSUPPORTED = 6, /* valid request outside what the library implements */
     POLY_ERR_COUNT = 7        /* a polygon count came out non-integral (numerical failure) */
 } poly_status;
 

@@ -1,6 +1,6 @@
 """Parity of the CUDA path with the FP64 oracle, through the C ABI.
 
-Error measure (the bound of the benchmark spec, same physical prefactor on
+Error measure (the stated tolerance bound, same physical prefactor on
 both sides): err_b = |B_gpu - B_ref| / (c_n * scale_ref_b) with
 scale_ref_b = sum_x |prod D| / (N^3 count_b) from the oracle and
 c_n = V^{n-1} / N^{3n}.  Bars: 1e-4 for the plain FP32 path, 1e-5 for the
