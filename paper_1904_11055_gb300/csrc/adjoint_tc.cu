@@ -16,15 +16,16 @@
 // chunk j is a fixed offset and the epilogue reads the 16 D_j of its cell at
 // fixed shared-memory offsets.  A chunk is kept only where m has an entry.
 //
-// A block owns one group of m's (all their chunks, at most (512 - K) / 2 columns)
-// and a range of 128-cell tiles.  A tile's fields are four contiguous blocks of
-// the cell-tiled layout; one thread of the MMA warp brings them into shared
-// memory with bulk copies into three buffers, rows padded with zeros up to K.
-// Eight cell warps (two per TMEM lane quadrant) write A and run the epilogue,
-// each over one half of the group's m's; the MMA warp issues the MMAs.  The
-// accumulators are double-buffered (two halves of TMEM next to A): once the
-// MMAs of tile t are done, the cell warps write A of tile t + 1, whose MMAs
-// then run while the cell warps reduce tile t.
+// A group of m's holds their chunks in at most (512 - K) / 2 columns.  A block
+// owns a pair of groups (members 0 and 1, each with its own half of TMEM next
+// to A) and a range of 128-cell tiles; both members use the same A.  A tile's
+// fields are four contiguous blocks of the cell-tiled layout; one thread of the
+// MMA warp brings them into shared memory with bulk copies, two tiles ahead,
+// rows padded with zeros up to K.  Eight cell warps (two per TMEM lane
+// quadrant) write A and run the epilogues, each over one half of a member's
+// m's; the MMA warp issues the MMAs.  Per tile: member 1's MMAs run while the
+// cell warps reduce member 0; then the cell warps write the next tile's A, and
+// the next tile's member-0 MMAs run while they reduce member 1.
 #include <cuda.h>
 
 #include <algorithm>
@@ -45,7 +46,7 @@ constexpr int kAtThreads = 32 * kAtCellWarps + 32;  // + the MMA warp
 constexpr int kAtMaxRuns = 2;                       // N runs of <= 256 columns per group
 constexpr int kAtMaxK = 128;                        // padded shell count (K) at most
 constexpr int kAtChunk = 16;                        // columns per chunk (one j block)
-constexpr int kAtDBufs = 3;                         // field tiles in flight (t - 1 in its epilogue, t, t + 1)
+constexpr int kAtDBufs = 3;                         // field tiles in flight (t in its epilogue, t + 1, t + 2)
 
 struct AtGroup {
     int chunk_off, nchunk;    // chunks [chunk_off, chunk_off + nchunk) of the chunk table
@@ -70,7 +71,8 @@ __global__ void at_scatter_kernel(const float* __restrict__ w, const int* __rest
 
 // chunk[c]: bits 0-7 jb, bits 8-15 m, bit 16: last chunk of its m.
 // D: cell-tiled fields, [cell / 32][nshell][cell % 32]; ncell a multiple of 32.
-// acap: TMEM columns of one accumulator buffer (two buffers at columns 0 and acap; A at 512 - kp).
+// A block takes the pair of groups (2 pr, 2 pr + 1) (the second may be absent); acap: TMEM columns of one
+// accumulator buffer (member b at column b * acap; A at 512 - kp).
 __global__ void __launch_bounds__(kAtThreads, 1)
     at_contract_kernel(const float* __restrict__ D, int nshell, int kp, int acap, int64_t ntile, int64_t ncell,
                        const AtGroup* __restrict__ groups, int ngroups, int ranges, const int* __restrict__ chunks,
@@ -78,32 +80,41 @@ __global__ void __launch_bounds__(kAtThreads, 1)
                        int* __restrict__ err) {
     // every pointer below is smem_raw plus an offset, so that the compiler keeps shared-memory loads
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    const AtGroup grp = groups[blockIdx.x % ngroups];
-    const int range = blockIdx.x / ngroups;
-    const int ncol = grp.nchunk * kAtChunk;
+    const int npairs = (ngroups + 1) / 2;
+    const int pr = blockIdx.x % npairs, range = blockIdx.x / npairs;
+    AtGroup gm[2];
+    gm[0] = groups[2 * pr];
+    if (2 * pr + 1 < ngroups) gm[1] = groups[2 * pr + 1];
+    else gm[1] = AtGroup{0, 0, 0, 0, {0, 0}};
     const uint32_t sbo = (uint32_t)kp * 16u;  // bytes per 8 columns of B (kp/8 core matrices of 128 B)
-    const int bbytes = ncol / 8 * (int)sbo;
+    const int ncol0 = gm[0].nchunk * kAtChunk, ncol1 = gm[1].nchunk * kAtChunk;
+    const int bbytes0 = ncol0 / 8 * (int)sbo, bbytes1 = ncol1 / 8 * (int)sbo;
     const int dfloats = kAtCells * kp;        // one tile of fields, [4][kp][32]
-    uint8_t* s_bh = smem_raw;                 // [ncol/8][kp/8] core matrices
-    uint8_t* s_bl = smem_raw + bbytes;
-    float* s_d = reinterpret_cast<float*>(smem_raw + 2 * bbytes);  // kAtDBufs tiles
-    int* s_chunk = reinterpret_cast<int*>(s_d + kAtDBufs * dfloats);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(s_chunk + ((grp.nchunk + 1) & ~1));
+    uint8_t* s_b = smem_raw;                  // member 0: hi, lo; member 1: hi, lo ([ncol/8][kp/8] core matrices)
+    float* s_d = reinterpret_cast<float*>(smem_raw + 2 * (bbytes0 + bbytes1));  // kAtDBufs tiles
+    int* s_chunk = reinterpret_cast<int*>(s_d + kAtDBufs * dfloats);           // member 0's, then member 1's
+    const int nch_all = gm[0].nchunk + gm[1].nchunk;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_chunk + ((nch_all + 1) & ~1));
     uint64_t* a_ready = bars;        // A of the next tile written (8 cell warps)
-    uint64_t* acc_full = bars + 1;   // [2] the MMAs into accumulator buffer b completed
-    uint64_t* acc_free = bars + 3;   // [2] the epilogue read accumulator buffer b (8 cell warps)
+    uint64_t* acc_full = bars + 1;   // [2] the MMAs of member b completed
+    uint64_t* acc_free = bars + 3;   // [2] the epilogue read member b's accumulators (8 cell warps)
     uint64_t* drain = bars + 5;
     uint64_t* d_full = bars + 6;     // [kAtDBufs] a tile's fields landed
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 6 + kAtDBufs);
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // B of this group, the chunk table, and the zero rows [nshell, kp) of every field buffer
-    for (int i = tid; i < bbytes / 16; i += kAtThreads) {
-        reinterpret_cast<uint4*>(s_bh)[i] = reinterpret_cast<const uint4*>(bhi_g + grp.b_off)[i];
-        reinterpret_cast<uint4*>(s_bl)[i] = reinterpret_cast<const uint4*>(blo_g + grp.b_off)[i];
+    // B of both members, the chunk tables, and the zero rows [nshell, kp) of every field buffer
+    for (int i = tid; i < bbytes0 / 16; i += kAtThreads) {
+        reinterpret_cast<uint4*>(s_b)[i] = reinterpret_cast<const uint4*>(bhi_g + gm[0].b_off)[i];
+        reinterpret_cast<uint4*>(s_b + bbytes0)[i] = reinterpret_cast<const uint4*>(blo_g + gm[0].b_off)[i];
     }
-    for (int c = tid; c < grp.nchunk; c += kAtThreads) s_chunk[c] = chunks[grp.chunk_off + c];
+    for (int i = tid; i < bbytes1 / 16; i += kAtThreads) {
+        reinterpret_cast<uint4*>(s_b + 2 * bbytes0)[i] = reinterpret_cast<const uint4*>(bhi_g + gm[1].b_off)[i];
+        reinterpret_cast<uint4*>(s_b + 2 * bbytes0 + bbytes1)[i] = reinterpret_cast<const uint4*>(blo_g + gm[1].b_off)[i];
+    }
+    for (int c = tid; c < gm[0].nchunk; c += kAtThreads) s_chunk[c] = chunks[gm[0].chunk_off + c];
+    for (int c = tid; c < gm[1].nchunk; c += kAtThreads) s_chunk[gm[0].nchunk + c] = chunks[gm[1].chunk_off + c];
     const int npad = (kp - nshell) * 32;
     for (int i = tid; i < 4 * kAtDBufs * npad; i += kAtThreads) {
         const int blk = i / npad, r = i - blk * npad;  // blk: buffer * 4 + quadrant
@@ -147,36 +158,47 @@ __global__ void __launch_bounds__(kAtThreads, 1)
                 tc::bulk_load(s_d + b * dfloats + q * kp * 32, D + (size_t)(c0 + 32 * q) * nshell, qbytes, d_full + b);
             last[b] = t;
         };
-        if (el && t0 < t1) load_tile(t0);
-        const uint32_t bh = tc::smem_u32(s_bh), bl = tc::smem_u32(s_bl);
+        if (el)
+            for (int64_t t = t0; t < t1 && t < t0 + kAtDBufs; t++) load_tile(t);
         const uint64_t desc_k = ((uint64_t)(((sbo >> 4) & 0x3FFFu) | (1u << 14)) << 32) | (uint64_t)((128u >> 4) << 16);
-        const uint32_t idesc = tc::idesc_bf16(128, ncol);  // ncol <= acap <= 240: one MMA run
         for (int64_t t = t0; t < t1; t++) {
             const int64_t k = t - t0;
-            const int b = (int)(k & 1);
             if (!tc::mbar_wait_warp(a_ready, (uint32_t)(k & 1), s_abort)) break;
-            // the epilogue of tile t - 2 has read accumulator buffer b
-            if (k >= 2 && !tc::mbar_wait_warp(acc_free + b, (uint32_t)(((k >> 1) - 1) & 1), s_abort)) break;
-            tc::fence_after_sync();
-            if (el) {
-                // the epilogue of tile t - 2 is done: its field buffer takes tile t + 1
-                if (t + 1 < t1) load_tile(t + 1);
-                uint32_t acc = 0u;
-                for (int ks = 0; ks < kp / 16; ks++) {
-                    if (!((grp.kmask[0] >> ks) & 1)) continue;
-                    const uint32_t bo = (uint32_t)ks * 256u;
-                    const uint64_t dh = desc_k | (uint64_t)(((bh + bo) >> 4) & 0x3FFFu);
-                    const uint64_t dl = desc_k | (uint64_t)(((bl + bo) >> 4) & 0x3FFFu);
-                    const uint32_t ah = tmem + a0 + (uint32_t)(ks * 8), al = ah + (uint32_t)(kp / 2);
-                    const uint32_t d = tmem + (uint32_t)(b * acap);
-                    tc::mma_ts(d, ah, dh, idesc, acc);  // hi x hi
-                    tc::mma_ts(d, ah, dl, idesc, 1u);   // hi x lo
-                    tc::mma_ts(d, al, dh, idesc, 1u);   // lo x hi
-                    acc = 1u;
+            bool ok = true;
+            for (int b = 0; b < 2 && ok; b++) {
+                // the epilogue of member b for tile t - 1 has read its accumulators
+                if (k > 0 && !tc::mbar_wait_warp(acc_free + b, (uint32_t)((k - 1) & 1), s_abort)) {
+                    ok = false;
+                    break;
                 }
-                tc::mma_commit(acc_full + b);
+                tc::fence_after_sync();
+                if (el) {
+                    // tile t - 1 is fully reduced: its field buffer takes tile t - 1 + kAtDBufs
+                    if (b == 1 && k > 0 && t - 1 + kAtDBufs < t1) load_tile(t - 1 + kAtDBufs);
+                    const int ncol = b ? ncol1 : ncol0;
+                    if (ncol > 0) {
+                        const uint32_t bh = tc::smem_u32(s_b + (b ? 2 * bbytes0 : 0));
+                        const uint32_t bl = bh + (uint32_t)(b ? bbytes1 : bbytes0);
+                        const uint32_t idesc = tc::idesc_bf16(128, ncol);  // ncol <= acap <= 256: one MMA run
+                        uint32_t acc = 0u;
+                        for (int ks = 0; ks < kp / 16; ks++) {
+                            if (!((gm[b].kmask[0] >> ks) & 1)) continue;
+                            const uint32_t bo = (uint32_t)ks * 256u;
+                            const uint64_t dh = desc_k | (uint64_t)(((bh + bo) >> 4) & 0x3FFFu);
+                            const uint64_t dl = desc_k | (uint64_t)(((bl + bo) >> 4) & 0x3FFFu);
+                            const uint32_t ah = tmem + a0 + (uint32_t)(ks * 8), al = ah + (uint32_t)(kp / 2);
+                            const uint32_t d = tmem + (uint32_t)(b * acap);
+                            tc::mma_ts(d, ah, dh, idesc, acc);  // hi x hi
+                            tc::mma_ts(d, ah, dl, idesc, 1u);   // hi x lo
+                            tc::mma_ts(d, al, dh, idesc, 1u);   // lo x hi
+                            acc = 1u;
+                        }
+                    }
+                    tc::mma_commit(acc_full + b);  // also for an absent member: it arrives once the MMAs so far finish
+                }
+                __syncwarp();
             }
-            __syncwarp();
+            if (!ok) break;
         }
         // every MMA and copy issued completes before the block frees its columns and exits
         if (el) {
@@ -192,9 +214,8 @@ __global__ void __launch_bounds__(kAtThreads, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------ cells: A, epilogue
-        const int q = warp & 3, h = warp >> 2;  // lane quadrant, half of the m's
+        const int q = warp & 3, h = warp >> 2;  // lane quadrant, half of each member's m's
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        const int c_begin = h ? grp.hsplit : 0, c_end = h ? grp.nchunk : grp.hsplit;
         // A of tile t (hi/lo pairs of shells, 32 shells per store pair; the two halves take alternate blocks)
         auto build_a = [&](int64_t t) -> bool {
             const int64_t k = t - t0;
@@ -214,20 +235,13 @@ __global__ void __launch_bounds__(kAtThreads, 1)
             if (lane == 0) tc::mbar_arrive(a_ready);
             return true;
         };
-        bool ok = t0 >= t1 || build_a(t0);
-        for (int64_t t = t0; t < t1 && ok; t++) {
-            const int64_t k = t - t0;
-            const int b = (int)(k & 1);
-            if (!tc::mbar_wait_warp(acc_full + b, (uint32_t)((k >> 1) & 1), s_abort)) break;
-            tc::fence_after_sync();
-            // the MMAs of tile t are done with A: write the next tile's, so its MMAs run during this epilogue
-            if (t + 1 < t1 && !build_a(t + 1)) break;
-            // G_m(x) = sum over m's chunks (m, jb) of sum_i D_{16 jb + i}(x) T[x][(m, 16 jb + i)]
-            const float* sd = s_d + (int)(k % kAtDBufs) * dfloats + q * kp * 32 + lane;
-            const int64_t cell = t * kAtCells + 32 * q + lane;
+        // G_m(x) = sum over m's chunks (m, jb) of sum_i D_{16 jb + i}(x) T[x][(m, 16 jb + i)], member b
+        auto epilogue = [&](int b, const float* sd, int64_t cell) {
+            const int base_c = b ? gm[0].nchunk : 0;
+            const int c_begin = h ? gm[b].hsplit : 0, c_end = h ? gm[b].nchunk : gm[b].hsplit;
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             for (int c = c_begin; c < c_end; c++) {
-                const int cd = s_chunk[c];
+                const int cd = s_chunk[base_c + c];
                 uint32_t v[16];
                 tc::tmem_ld16(tmem + lane_base + (uint32_t)(b * acap + c * kAtChunk), v);
                 const float* dj = sd + 32 * kAtChunk * (cd & 255);
@@ -245,6 +259,22 @@ __global__ void __launch_bounds__(kAtThreads, 1)
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(acc_free + b);
+        };
+        bool ok = t0 >= t1 || build_a(t0);
+        for (int64_t t = t0; t < t1 && ok; t++) {
+            const int64_t k = t - t0;
+            const float* sd = s_d + (int)(k % kAtDBufs) * dfloats + q * kp * 32 + lane;
+            const int64_t cell = t * kAtCells + 32 * q + lane;
+            // member 0 (its MMAs are done; member 1's run meanwhile)
+            if (!tc::mbar_wait_warp(acc_full, (uint32_t)(k & 1), s_abort)) break;
+            tc::fence_after_sync();
+            epilogue(0, sd, cell);
+            // every MMA of tile t is done with A: write the next tile's, then reduce member 1 while
+            // the next tile's member-0 MMAs run
+            if (!tc::mbar_wait_warp(acc_full + 1, (uint32_t)(k & 1), s_abort)) break;
+            tc::fence_after_sync();
+            if (t + 1 < t1 && !build_a(t + 1)) break;
+            epilogue(1, sd, cell);
         }
     }
     tc::fence_before_sync();
@@ -270,10 +300,11 @@ struct AtState {
     int nent = 0;
 };
 
-static size_t at_smem_bytes(int nchunk, int kp) {
-    const size_t ncol = (size_t)nchunk * kAtChunk;
-    return 2 * ncol / 8 * kp * 16 + kAtDBufs * (size_t)kAtCells * kp * 4 + (size_t)(nchunk + 1) * 4 + 8 * (8 + kAtDBufs) +
-           16;
+// shared memory of a block whose pair of groups has nc0 and nc1 chunks
+static size_t at_smem_bytes(int nc0, int nc1, int kp) {
+    const size_t ncol = (size_t)(nc0 + nc1) * kAtChunk;
+    return 2 * ncol / 8 * kp * 16 + kAtDBufs * (size_t)kAtCells * kp * 4 + (size_t)(nc0 + nc1 + 1) * 4 +
+           8 * (8 + kAtDBufs) + 16;
 }
 
 // ent: the adjoint's entries in order (m ascending), each (m, f1, f2) with f1 <= f2.
@@ -300,7 +331,8 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
     // two accumulator buffers next to A: acap columns each, one MMA run of at most 256
     S->acap = std::min(256, (512 - kp) / 2 / 32 * 32);  // each buffer starts on a 32-column boundary
     const int chunk_cap = S->acap / kAtChunk;
-    auto fits = [&](int nchunk) { return nchunk <= chunk_cap && at_smem_bytes(nchunk, kp) <= 227 * 1024; };
+    // a group fits when two groups of its size fit one block (the blocks take pairs of groups)
+    auto fits = [&](int nchunk) { return nchunk <= chunk_cap && at_smem_bytes(nchunk, nchunk, kp) <= 227 * 1024; };
     std::vector<int> chunks;
     std::map<std::pair<int, int>, std::pair<int, int>> chpos;  // (m, jb) -> (group, chunk)
     size_t b_total = 0;
@@ -351,10 +383,10 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
     }
     S->nent = (int)ent.size();
     // at least half the SM's shared memory: one block per SM, so no block waits in tcgen05.alloc for another
-    S->smem = std::max<size_t>(at_smem_bytes(S->max_nchunk, kp), 116 * 1024);
+    S->smem = std::max<size_t>(at_smem_bytes(S->max_nchunk, S->max_nchunk, kp), 116 * 1024);
     const int64_t ntile = (ncell + kAtCells - 1) / kAtCells;
-    S->ranges = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (2 * p->sms + (int)S->groups.size() - 1) /
-                                                                       (int)S->groups.size()));
+    const int npairs = ((int)S->groups.size() + 1) / 2;
+    S->ranges = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (2 * p->sms + npairs - 1) / npairs));
     auto up = [&](void** d, const void* h, size_t bytes) -> poly_status {
         poly_status s = ps_alloc(p, d, bytes);
         if (s) return s;
@@ -390,7 +422,7 @@ cudaError_t ps_at_contract(PsPlan* p, AtState* S, const float* w, cudaStream_t s
     for (int m : S->empty_m)
         if ((e = cudaMemsetAsync((float*)p->d_G + (size_t)m * ncell, 0, (size_t)ncell * 4, st))) return e;
     const int64_t ntile = (ncell + kAtCells - 1) / kAtCells;
-    const unsigned nblk = (unsigned)(S->groups.size() * (size_t)S->ranges);
+    const unsigned nblk = (unsigned)(((S->groups.size() + 1) / 2) * (size_t)S->ranges);
     at_contract_kernel<<<nblk, kAtThreads, S->smem, st>>>((const float*)p->d_fields, p->nshell, S->kp, S->acap, ntile, ncell,
                                                           (const AtGroup*)S->d_groups, (int)S->groups.size(), S->ranges,
                                                           (const int*)S->d_chunks, (const uint8_t*)S->d_bhi,
