@@ -9,6 +9,8 @@
 // FP32 instantiation: products and per-chunk accumulation in FP32, flushed to
 // FP64 every kFlushChunks chunks.  FP64 instantiation: FP64 throughout (the
 // plain method, and the exact polygon counts over the symmetry wedge).
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -26,7 +28,8 @@ PS_DEV void load4(const double* p, double* v) {
     v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
 }
 
-template <typename T, bool WEIGHTED, bool ABS>
+// NF: factors per row or column at most (2 for n <= 4, 3 for n = 5, 6); the third is never read for NF = 2.
+template <typename T, bool WEIGHTED, bool ABS, int NF>
 __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
     const T* __restrict__ fields, size_t fstride, int tile_ns, int64_t ncell, const T* __restrict__ weight,
     const PsTile* __restrict__ tiles, int ntiles, const int* __restrict__ field_ids, const short4* __restrict__ rowf,
@@ -35,7 +38,8 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
     __shared__ T s_d[kCcMaxFields][CH + 1];
     __shared__ __align__(16) T s_a[CH][TM];
     __shared__ __align__(16) T s_b[CH][TN];
-    __shared__ short4 s_rf[TM], s_cf[TN];
+    using FT = typename std::conditional<NF == 3, short4, short2>::type;  // factor record in shared memory
+    __shared__ FT s_rf[TM], s_cf[TN];
     __shared__ int s_fid[kCcMaxFields];
 
     const PsTile tile = tiles[blockIdx.x];
@@ -46,8 +50,13 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
     const int c0 = 16 * (warp & 3) + 4 * (lane & 3);
     const bool active = (tile.region_mask >> warp) & 1u;
 
-    for (int i = tid; i < TM; i += kCcThreads) s_rf[i] = i < tile.nrow ? rowf[tile.row_off + i] : make_short4(-1, -1, -1, -1);
-    for (int i = tid; i < TN; i += kCcThreads) s_cf[i] = i < tile.ncol ? colf[tile.col_off + i] : make_short4(-1, -1, -1, -1);
+    auto narrow = [](short4 f) {
+        if constexpr (NF == 3) return f;
+        else return make_short2(f.x, f.y);
+    };
+    const short4 none = make_short4(-1, -1, -1, -1);
+    for (int i = tid; i < TM; i += kCcThreads) s_rf[i] = narrow(i < tile.nrow ? rowf[tile.row_off + i] : none);
+    for (int i = tid; i < TN; i += kCcThreads) s_cf[i] = narrow(i < tile.ncol ? colf[tile.col_off + i] : none);
     for (int i = tid; i < tile.nfield; i += kCcThreads) s_fid[i] = field_ids[tile.field_off + i];
 
     T acc[4][4];
@@ -81,6 +90,10 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
             }
         }
     };
+    // the row and column this thread forms products for are the same in every chunk
+    static_assert(kCcThreads % TM == 0 && kCcThreads % TN == 0, "rows and columns per thread must not vary");
+    const int r = tid % TM, c = tid % TN;
+    const FT frow = s_rf[r], fcol = s_cf[c];
     if (cbeg < cend) fetch(cbeg);
     int since_flush = 0;
     for (int64_t ch = cbeg; ch < cend; ch++) {
@@ -94,14 +107,14 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
         __syncthreads();
         fetch(ch + 1);
         // 2. row and column products
-        for (int e = tid; e < CH * TM; e += kCcThreads) {
-            const int x = e / TM, r = e - (e / TM) * TM;
-            const short4 f = s_rf[r];
+        for (int x = tid / TM; x < CH; x += kCcThreads / TM) {  // this thread's row r, every cell x it owns
+            const FT f = frow;
             T v = 0;
             if (f.x >= 0) {
                 v = s_d[f.x][x];
                 if (f.y >= 0) v *= s_d[f.y][x];
-                if (f.z >= 0) v *= s_d[f.z][x];
+                if constexpr (NF == 3)
+                    if (f.z >= 0) v *= s_d[f.z][x];
                 if (WEIGHTED) {
                     const int64_t cell = base + x;
                     v *= cell < ncell ? weight[cell] : (T)0;
@@ -110,14 +123,14 @@ __global__ void __launch_bounds__(kCcThreads) contract_cc_kernel(
             }
             s_a[x][r] = v;
         }
-        for (int e = tid; e < CH * TN; e += kCcThreads) {
-            const int x = e / TN, c = e - (e / TN) * TN;
-            const short4 f = s_cf[c];
+        for (int x = tid / TN; x < CH; x += kCcThreads / TN) {
+            const FT f = fcol;
             T v = 0;
             if (f.x >= 0) {
                 v = s_d[f.x][x];
                 if (f.y >= 0) v *= s_d[f.y][x];
-                if (f.z >= 0) v *= s_d[f.z][x];
+                if constexpr (NF == 3)
+                    if (f.z >= 0) v *= s_d[f.z][x];
                 if (ABS) v = v < 0 ? -v : v;
             }
             s_b[x][c] = v;
@@ -176,36 +189,48 @@ __global__ void normalise_kernel(const double* __restrict__ S, const int64_t* __
 
 using namespace ps;
 
-cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
-                           int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
-                           const short4* rowf, const short4* colf, int nsplit, int64_t chunks_per_split,
-                           double* partial, cudaStream_t st) {
+template <int NF>
+static cudaError_t contract_cc_launch(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
+                                      int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles,
+                                      const int* field_ids, const short4* rowf, const short4* colf, int nsplit,
+                                      int64_t chunks_per_split, double* partial, cudaStream_t st) {
     dim3 grid(ntiles, nsplit);
     if (is_double) {
         if (weighted)
-            contract_cc_kernel<double, true, false><<<grid, kCcThreads, 0, st>>>(
+            contract_cc_kernel<double, true, false, NF><<<grid, kCcThreads, 0, st>>>(
                 (const double*)fields, field_stride, tile_ns, ncell, (const double*)weight, tiles, ntiles, field_ids, rowf,
                 colf, chunks_per_split, partial);
         else if (absval)
-            contract_cc_kernel<double, false, true><<<grid, kCcThreads, 0, st>>>(
+            contract_cc_kernel<double, false, true, NF><<<grid, kCcThreads, 0, st>>>(
                 (const double*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
         else
-            contract_cc_kernel<double, false, false><<<grid, kCcThreads, 0, st>>>(
+            contract_cc_kernel<double, false, false, NF><<<grid, kCcThreads, 0, st>>>(
                 (const double*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
     } else {
         if (weighted) return cudaErrorInvalidValue;
         if (absval)
-            contract_cc_kernel<float, false, true><<<grid, kCcThreads, 0, st>>>(
+            contract_cc_kernel<float, false, true, NF><<<grid, kCcThreads, 0, st>>>(
                 (const float*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
         else
-            contract_cc_kernel<float, false, false><<<grid, kCcThreads, 0, st>>>(
+            contract_cc_kernel<float, false, false, NF><<<grid, kCcThreads, 0, st>>>(
                 (const float*)fields, field_stride, tile_ns, ncell, nullptr, tiles, ntiles, field_ids, rowf, colf,
                 chunks_per_split, partial);
     }
     return cudaGetLastError();
+}
+
+cudaError_t ps_contract_cc(int is_double, int weighted, int absval, int nf, const void* fields, size_t field_stride,
+                           int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
+                           const short4* rowf, const short4* colf, int nsplit, int64_t chunks_per_split,
+                           double* partial, cudaStream_t st) {
+    if (nf == 3)
+        return contract_cc_launch<3>(is_double, weighted, absval, fields, field_stride, tile_ns, ncell, weight, tiles,
+                                     ntiles, field_ids, rowf, colf, nsplit, chunks_per_split, partial, st);
+    return contract_cc_launch<2>(is_double, weighted, absval, fields, field_stride, tile_ns, ncell, weight, tiles, ntiles,
+                                 field_ids, rowf, colf, nsplit, chunks_per_split, partial, st);
 }
 
 cudaError_t ps_reduce_slots(const double* partial, int nsplit, int64_t slot_stride, const int64_t* slot,

@@ -39,7 +39,8 @@ inline int ps_cc_chunk(int is_double) { return is_double ? 16 : 32; }
 
 // partial[(split * ntiles + tile) * 64 * 64 + r * 64 + c] = sum over the split's cells
 // fields: natural [s][cell] with stride field_stride (tile_ns == 0) or cell-tiled over tile_ns shells
-cudaError_t ps_contract_cc(int is_double, int weighted, int absval, const void* fields, size_t field_stride,
+// nf: factors per row or column at most (2 for n <= 4, 3 for n = 5, 6)
+cudaError_t ps_contract_cc(int is_double, int weighted, int absval, int nf, const void* fields, size_t field_stride,
                            int tile_ns, int64_t ncell, const void* weight, const PsTile* tiles, int ntiles, const int* field_ids,
                            const short4* rowf, const short4* colf, int nsplit, int64_t chunks_per_split,
                            double* partial, cudaStream_t st);

@@ -166,7 +166,7 @@ extern "C" poly_status poly_estimate_noalloc(int N, double L, int nshell, const 
     if ((e = ps_forward(N, 0, delta_x, K, B + o_twf, B + o_W, B + o_fhat, nullptr, st)) ||
         (e = ps_inverse(N, 0, 0, B + o_fhat, B + o_lines, (const int*)(B + o_loff), 0, nshell, K, 0, N, B + o_twi,
                         B + o_fields, (size_t)n3, nullptr, nullptr, 0, nshell, st)) ||
-        (e = ps_contract_cc(0, 0, 0, B + o_fields, (size_t)n3, nshell, n3, nullptr, (const PsTile*)(B + o_tiles), ntiles,
+        (e = ps_contract_cc(0, 0, 0, 2, B + o_fields, (size_t)n3, nshell, n3, nullptr, (const PsTile*)(B + o_tiles), ntiles,
                             (const int*)(B + o_fid), (const short4*)(B + o_rowf), (const short4*)(B + o_colf), nsplit,
                             cps, (double*)(B + o_part), st)) ||
         (e = ps_reduce_slots((const double*)(B + o_part), nsplit, slot_stride, (const int64_t*)(B + o_slot), hp.nbins,

@@ -215,7 +215,12 @@ void build_cc_tiles(PsPlan* p, CcTiles& t, int first_shift) {
                 t.field_ids.push_back(shell1 - 1);
                 return (short)id;
             };
-            auto factors = [&](const Key& k) { return make_short4(loc(k[0]), loc(k[1]), loc(k[2]), -1); };
+            auto factors = [&](const Key& k) {  // in order: local ids follow first appearance, row by row
+                const short a = loc(k[0]);
+                const short b = loc(k[1]);
+                const short c = loc(k[2]);
+                return make_short4(a, b, c, -1);
+            };
             for (size_t r = g; r < g1; r++) t.rowf.push_back(factors(ri[r].key));
             std::map<Key, int> cidx;
             for (size_t c = c0; c < c1; c++) {
@@ -326,7 +331,7 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
             }
         }
         if (rc) break;
-        if ((e = ps_contract_cc(1, 1, 0, d_iota, (size_t)nw, 0, nw, d_wgt, (const PsTile*)p->d_cc_tiles,
+        if ((e = ps_contract_cc(1, 1, 0, p->order >= 5 ? 3 : 2, d_iota, (size_t)nw, 0, nw, d_wgt, (const PsTile*)p->d_cc_tiles,
                                 (int)t.tiles.size(), (const int*)p->d_cc_field_ids, (const short4*)p->d_cc_rowf,
                                 (const short4*)p->d_cc_colf, nsplit, cps, (double*)d_part, st)) ||
             (e = ps_reduce_slots((double*)d_part, nsplit, slot_stride, (const int64_t*)p->d_cc_slot, p->nbins,
@@ -574,7 +579,7 @@ poly_status ps_sums(PsPlan* p, bool absval, cudaStream_t st) {
     cudaError_t e;
     if (p->prec == POLY_SPLIT_BF16 && !absval) return ps_tc_sums(p, st);
     const size_t n3 = (size_t)p->N * p->N * p->N;
-    if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->d_fields, n3, p->nfield, (int64_t)n3, nullptr,
+    if ((e = ps_contract_cc(p->is_double, 0, absval ? 1 : 0, p->order >= 5 ? 3 : 2, p->d_fields, n3, p->nfield, (int64_t)n3, nullptr,
                             (const PsTile*)p->d_cc_tiles, (int)p->cc.tiles.size(), (const int*)p->d_cc_field_ids,
                             (const short4*)p->d_cc_rowf, (const short4*)p->d_cc_colf, p->cc_nsplit, p->cc_cps,
                             p->d_partial, st)))
