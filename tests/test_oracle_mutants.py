@@ -37,6 +37,20 @@ MUTANTS = {
                             "test_oracle_estimator.py -k gradient"),
     "adjoint_no_mask": ("if (smap[q] == m) H[q] = work[q];", "if (smap[q] >= 0) H[q] = work[q];",
                         "test_oracle_estimator.py -k gradient"),
+    "group_dropped_factor": ("for (int f = 1; f < nf; f++) {", "for (int f = 1; f < nf - 1; f++) {",
+                             "test_oracle_estimator.py -k n5_n6"),
+    "group_wrong_partner": ("c.b = G + n3 * (size_t)bg[2 * b + 1];", "c.b = G + n3 * (size_t)bg[2 * b];",
+                            "test_oracle_estimator.py -k n5_n6"),
+    "disconnected_pairing": ("if (k[0] == k[1] && k[2] == k[3]) sd += p1 * p3;", "if (k[0] == k[1]) sd += p1 * p3;",
+                             "test_oracle_estimator.py -k disconnected"),
+    "disconnected_power": ("P[smap[i]] += dhat[2 * i] * dhat[2 * i] + dhat[2 * i + 1] * dhat[2 * i + 1];",
+                           "P[smap[i]] += dhat[2 * i] * dhat[2 * i];", "test_oracle_estimator.py -k disconnected"),
+    "legendre_sign": ("((2.0 * n + 1.0) * mu * p1 - n * p0) / (n + 1.0);", "((2.0 * n + 1.0) * mu * p1 + n * p0) / (n + 1.0);",
+                      "test_oracle_estimator.py -k multipole"),
+    "multipole_axis": ("legendre(ell, qz / sqrt(qx * qx + qy * qy + qz * qz));",
+                       "legendre(ell, qx / sqrt(qx * qx + qy * qy + qz * qz));", "test_oracle_estimator.py -k multipole"),
+    "multipole_factor": ("norm = (2.0 * ell + 1.0) * pow(L * L * L, order - 1)", "norm = pow(L * L * L, order - 1)",
+                         "test_oracle_estimator.py -k multipole"),
 }
 
 
