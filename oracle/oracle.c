@@ -523,11 +523,11 @@ static int counts_exact_groups(int N, int nshell, const double* edges, int order
     /* distinct groups: key = shells (1-based) padded with 0, stored 3 per group */
     int32_t* gkey = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(2 * nbins + 1));
     int64_t* bg = (int64_t*)malloc(sizeof(int64_t) * 2 * (size_t)(nbins + 1)); /* per bin: its two group ids */
-    if (!smap || !fslot || !gkey || !bg) return fail(-2, "orc_counts_exact: out of memory");
-    int rc = orc_shell_map(N, nshell, edges, smap);
+    int rc = (!smap || !fslot || !gkey || !bg) ? fail(-2, "orc_counts_exact: out of memory")
+                                                : orc_shell_map(N, nshell, edges, smap);
     int nf = 0;
     int64_t ng = 0;
-    for (int s = 0; s <= nshell; s++) fslot[s] = -1;
+    for (int s = 0; s <= nshell && fslot; s++) fslot[s] = -1;
     for (int64_t b = 0; b < nbins && !rc; b++) {
         const int32_t* k = bins + b * order;
         for (int t = 0; t < order; t++) {
