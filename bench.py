@@ -147,6 +147,31 @@ def cpu_baseline(delta_f32):
                       f"(full forward FFT, 6 shell + 6 counting fields, FP64), {dt:.1f} s"}
 
 
+def cufft_fields_ms(torch, d, edges, reps=3):
+    """The shell fields through cuFFT (torch.fft), as a timed cross-check of the library's pruned transforms:
+    one full R2C, then per shell a mask multiply and a full C2R into one reused buffer (N_max x N^3 outputs
+    written, as the library writes).  Device-timed median of `reps`."""
+    N = d.shape[0]
+    f = torch.fft.fftfreq(N, d=1.0 / N, device=d.device)
+    fz = torch.fft.rfftfreq(N, d=1.0 / N, device=d.device)
+    q2 = f[:, None, None] ** 2 + f[None, :, None] ** 2 + fz[None, None, :] ** 2
+    e2 = torch.tensor([float(x) ** 2 for x in edges], device=d.device, dtype=q2.dtype)
+    smap = torch.bucketize(q2, e2, right=True) - 1  # shell s: e_s^2 <= |q|^2 < e_{s+1}^2
+    smap[q2 == 0] = -1
+    out = torch.empty_like(d)
+    ms = []
+    for _ in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        F = torch.fft.rfftn(d)
+        for s in range(len(edges) - 1):
+            out.copy_(torch.fft.irfftn(torch.where(smap == s, F, 0), s=(N, N, N), norm="forward"))
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms[1:])
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -310,6 +335,7 @@ def run_ours(args):
             b.record()
             torch.cuda.synchronize()
             bms.append(a.elapsed_time(b))
+        cufft_ms = cufft_fields_ms(torch, d, edges) if prec == precisions[0] and ELL == 0 else None
         dms = []
         for _ in range(3 if ORDER == 4 and ELL == 0 else 0):  # the trispectrum's disconnected part (optional output)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -319,7 +345,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             dms.append(a.elapsed_time(b))
         results[prec] = {"value": value, "ms_per_step": total_ms / args.steps, "roofline": roof,
-                         "disconnected_ms": statistics.median(dms) if dms else None,
+                         "disconnected_ms": statistics.median(dms) if dms else None, "cufft_fields_ms": cufft_ms,
                          "plan_ms": plan_ms, "backward_ms": statistics.median(bms) if bms else None,
                          "tuned_config": {"code": tuned[0], "contract_ms": round(tuned[1], 4)},
                          "fields_roofline": fields_roof, "stage_ms": stage, "gpu_launches": launches,
@@ -351,6 +377,11 @@ def run_ours(args):
                     "process; later plans with the same shells reuse the cached counts); outside the timed step"},
         "backward_ms": {"value": h["backward_ms"], "note": "poly_backward, dL/d delta of sum_b w_b B_b on the same "
                         "field, device-timed median of 3"},
+        "cufft_cross_check": {"fields_ms": h["cufft_fields_ms"], "library_fields_ms": h["stage_ms"]["ms_forward"] +
+                              h["stage_ms"]["ms_fields"],
+                              "note": "the same shell fields through cuFFT (torch.fft: full R2C, per-shell mask, full "
+                                      "C2R), device-timed median of 3, against the library's forward + shell-field "
+                                      "stages"},
         **({"disconnected_ms": {"value": h["disconnected_ms"], "note": "poly_trispectrum_disconnected on the same "
                                 "field (forward transform, shell powers, per-bin pairings), device-timed median of 3"}}
            if ORDER == 4 and ELL == 0 else {}),

@@ -257,6 +257,33 @@ def test_quadrupole_256cube_sampled(field256):
     assert err.max() <= TOL["fp32"], err.max()
 
 
+def test_matches_an_independent_cufft_route():
+    """The estimate against the same estimator built from cuFFT shell fields (torch.fft) and plain torch
+    reductions: an independent GPU route, FP64 throughout, 48^3 and 10 shells."""
+    N, L, e = 48, 1000.0, fieldgen.unit_edges(10)
+    d = fieldgen.field("lognormal", N, 17, np.float32)
+    plan = ps.Plan(N, L, 3, e, "fp32")
+    B = plan.estimate(torch.from_numpy(d).cuda()).cpu().numpy()
+    dt = torch.from_numpy(d.astype(np.float64)).cuda()
+    f = torch.fft.fftfreq(N, d=1.0 / N, device="cuda", dtype=torch.float64)
+    fz = torch.fft.rfftfreq(N, d=1.0 / N, device="cuda", dtype=torch.float64)
+    q2 = f[:, None, None] ** 2 + f[None, :, None] ** 2 + fz[None, None, :] ** 2
+    F = torch.fft.rfftn(dt)
+    D = []
+    for s in range(10):
+        m = (q2 >= e[s] ** 2) & (q2 < e[s + 1] ** 2) & (q2 > 0)
+        D.append(torch.fft.irfftn(torch.where(m, F, 0), s=(N, N, N), norm="forward").reshape(-1))
+    D = torch.stack(D)
+    b = torch.from_numpy(plan.bins.astype(np.int64) - 1).cuda()
+    S = (D[b[:, 0]] * D[b[:, 1]] * D[b[:, 2]]).sum(dim=1)
+    A = (D[b[:, 0]] * D[b[:, 1]] * D[b[:, 2]]).abs().sum(dim=1)
+    cnt = torch.from_numpy(plan.counts).cuda().double()
+    ref = (norm(L, N, 3) * S / (N ** 3 * cnt)).cpu().numpy()
+    scale = (A / (N ** 3 * cnt)).cpu().numpy()
+    err = np.abs(B - ref) / (norm(L, N, 3) * scale)
+    assert err.max() <= TOL["fp32"], err.max()
+
+
 # ------------------------------------------------------------------ entry points agree bit for bit
 def test_host_entry_matches_device_entry():
     d = fieldgen.field("lognormal", 32, 5, np.float32)
