@@ -140,11 +140,11 @@ def cpu_baseline(delta_f32):
     allb = oracle.enumerate_bins(edges, ORDER)
     sel = np.array([i for i, b in enumerate(allb) if set(b.tolist()) <= set(SAMPLE_SHELLS)])
     t0 = time.perf_counter()
-    oracle.estimate(delta_f32.astype(np.float64), L, edges, ORDER, bins=allb[sel])
+    ref = oracle.estimate(delta_f32.astype(np.float64), L, edges, ORDER, bins=allb[sel])
     dt = time.perf_counter() - t0
     return {"value": len(sel) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(sel)} bins among shells {SAMPLE_SHELLS[0]}-{SAMPLE_SHELLS[-1]} of the 256^3 field "
-                      f"(full forward FFT, 6 shell + 6 counting fields, FP64), {dt:.1f} s"}
+                      f"(full forward FFT, 6 shell + 6 counting fields, FP64), {dt:.1f} s"}, sel, ref
 
 
 def cufft_fields_ms(torch, d, edges, reps=3):
@@ -232,6 +232,7 @@ def time_precision(ps, torch, plan, d, args, flush_buf, dist_ok):
     torch.cuda.synchronize()
     if dist_ok:
         torch.distributed.barrier()
+    time_precision.last_out = out.cpu().numpy()
     launches = ps.poly_plan_stats(plan.handle)["launches"] - launches0
     ps.poly_plan_set_timing(plan.handle, False)
     mean = {k: statistics.fmean(s[k] for s in stages) for k in ("ms_forward", "ms_fields", "ms_contract", "ms_reduce")}
@@ -346,6 +347,7 @@ def run_ours(args):
             dms.append(a.elapsed_time(b))
         results[prec] = {"value": value, "ms_per_step": total_ms / args.steps, "roofline": roof,
                          "disconnected_ms": statistics.median(dms) if dms else None, "cufft_fields_ms": cufft_ms,
+                         "B": time_precision.last_out,
                          "plan_ms": plan_ms, "backward_ms": statistics.median(bms) if bms else None,
                          "tuned_config": {"code": tuned[0], "contract_ms": round(tuned[1], 4)},
                          "fields_roofline": fields_roof, "stage_ms": stage, "gpu_launches": launches,
@@ -389,8 +391,15 @@ def run_ours(args):
                                               "backward_ms")}
                            if "value" in r else r) for p, r in results.items()},
     }
-    if world == 1 and not args.no_cpu_baseline and (N, NSHELL, ORDER) == (256, 64, 3):
-        line["cpu_baseline"] = cpu_baseline(delta_np)
+    if world == 1 and not args.no_cpu_baseline and (N, NSHELL, ORDER) == (256, 64, 3) and ELL == 0:
+        line["cpu_baseline"], sel, ref = cpu_baseline(delta_np)
+        # the error of every precision against the FP64 oracle on the same bins, in units of the tolerance scale
+        # c_n sum_x |prod D| / (N^3 count) (bars: 1e-5 split-BF16, 1e-4 FP32)
+        c_n = (L ** 3) ** (ORDER - 1) / float(N ** 3) ** ORDER
+        line["error_vs_oracle"] = {
+            p: float(np.max(np.abs(r["B"][sel] - ref["B"]) / (c_n * ref["scale"]))) for p, r in results.items()
+            if "B" in r}
+        line["error_vs_oracle"]["bins"] = int(len(sel))
     print(json.dumps(line), flush=True)
     if dist_ok:
         torch.distributed.destroy_process_group()
