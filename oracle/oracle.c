@@ -1002,6 +1002,137 @@ int orc_direct_sample(int N, const double* delta /* NULL: counts only */, int ns
 }
 
 /* ------------------------------------------------------------------------- */
+/* full-shape trispectrum (Eq. Tkfull, which the paper leaves as future       */
+/* work): the closed quadrilaterals of one bin (k1, k2, k3, k4), split by the */
+/* diagonals p1 = q1 - q2 and p2 = q1 - q3 (Eq. Tkfull's                      */
+/* delta_D(p1 - q1 + q2) delta_D(p2 - q1 + q3)) into diagonal bins            */
+/* j: de_j^2 <= |p|^2 < de_{j+1}^2 (p = 0 falls in bin 0 when de_0 = 0):      */
+/*   S[j1][j2]     = N^3 Re sum prod_t dhat(q_t)                             */
+/*   count[j1][j2] = the number of those quadrilaterals,                      */
+/* over q_t in S_{k_t} with q1 + q2 + q3 + q4 = 0 (mod N); the components of  */
+/* p are differences of the signed (-N/2 .. N/2 - 1) representatives.        */
+/* Summed over diagonal bins that cover every |p| they give S_b and count_b   */
+/* of the angle-averaged trispectrum.  Direct enumeration over q1, q2, q3.    */
+/* `delta` may be NULL (counts only).                                         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int N, ndiag;
+    const double* de2;
+    const cplx* dhat;
+    const int32_t* smap;
+    int32_t* modes[4];
+    int32_t nm[4];
+    int k4;
+    double* S;   /* [256][ndiag * ndiag] */
+    int64_t* C;  /* [256][ndiag * ndiag] */
+} tfull_ctx;
+
+static int signed_freq(int i, int N) { return i < (N + 1) / 2 ? i : i - N; }
+
+static int diag_bin(const double* de2, int nd, double p2) {
+    for (int j = 0; j < nd; j++)
+        if (de2[j] <= p2 && p2 < de2[j + 1]) return j;
+    return -1;
+}
+
+static void tfull_range(void* vctx, int64_t begin, int64_t end, int tid) {
+    tfull_ctx* c = (tfull_ctx*)vctx;
+    const int N = c->N, nd = c->ndiag;
+    double* S = c->S + (size_t)tid * nd * nd;
+    int64_t* C = c->C + (size_t)tid * nd * nd;
+    for (int64_t a = begin; a < end; a++) {
+        const int32_t i1 = c->modes[0][a];
+        const int x1 = (int)(i1 / (N * N)), y1 = (int)((i1 / N) % N), z1 = (int)(i1 % N);
+        for (int32_t b = 0; b < c->nm[1]; b++) {
+            const int32_t i2 = c->modes[1][b];
+            const int x2 = (int)(i2 / (N * N)), y2 = (int)((i2 / N) % N), z2 = (int)(i2 % N);
+            const double u0 = signed_freq(x1, N) - signed_freq(x2, N), u1 = signed_freq(y1, N) - signed_freq(y2, N),
+                         u2 = signed_freq(z1, N) - signed_freq(z2, N);
+            const int j1 = diag_bin(c->de2, nd, u0 * u0 + u1 * u1 + u2 * u2);
+            if (j1 < 0) continue;
+            for (int32_t g = 0; g < c->nm[2]; g++) {
+                const int32_t i3 = c->modes[2][g];
+                const int x3 = (int)(i3 / (N * N)), y3 = (int)((i3 / N) % N), z3 = (int)(i3 % N);
+                const int x4 = ((-(x1 + x2 + x3)) % N + N) % N, y4 = ((-(y1 + y2 + y3)) % N + N) % N,
+                          z4 = ((-(z1 + z2 + z3)) % N + N) % N;
+                const int64_t i4 = ((int64_t)x4 * N + y4) * N + z4;
+                if (c->smap[i4] != c->k4) continue;
+                const double w0 = signed_freq(x1, N) - signed_freq(x3, N), w1 = signed_freq(y1, N) - signed_freq(y3, N),
+                             w2 = signed_freq(z1, N) - signed_freq(z3, N);
+                const int j2 = diag_bin(c->de2, nd, w0 * w0 + w1 * w1 + w2 * w2);
+                if (j2 < 0) continue;
+                C[j1 * nd + j2]++;
+                if (c->dhat) {
+                    const cplx f1 = c->dhat[i1], f2 = c->dhat[i2], f3 = c->dhat[i3], f4 = c->dhat[i4];
+                    const double ar = f1.re * f2.re - f1.im * f2.im, ai = f1.re * f2.im + f1.im * f2.re;
+                    const double br = f3.re * f4.re - f3.im * f4.im, bi = f3.re * f4.im + f3.im * f4.re;
+                    S[j1 * nd + j2] += ar * br - ai * bi;
+                }
+            }
+        }
+    }
+}
+
+int orc_trispectrum_full(int N, const double* delta, int nshell, const double* edges, const int32_t* k, int ndiag,
+                         const double* dedges, double* S, int64_t* counts) {
+    if (N < 2 || ndiag < 1 || !k) return fail(-1, "orc_trispectrum_full: bad args");
+    for (int t = 0; t < 4; t++)
+        if (k[t] < 1 || k[t] > nshell) return fail(-1, "orc_trispectrum_full: bin shell out of range");
+    for (int j = 0; j < ndiag; j++)
+        if (!(dedges[j] >= 0.0 && dedges[j + 1] > dedges[j])) return fail(-1, "orc_trispectrum_full: diagonal edges");
+    const size_t n3 = (size_t)N * N * N;
+    tfull_ctx c;
+    memset(&c, 0, sizeof c);
+    c.N = N;
+    c.ndiag = ndiag;
+    double* de2 = (double*)malloc(sizeof(double) * (size_t)(ndiag + 1));
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    double* dhat = delta ? (double*)malloc(sizeof(double) * 2 * n3) : NULL;
+    c.S = (double*)calloc((size_t)256 * ndiag * ndiag, sizeof(double));
+    c.C = (int64_t*)calloc((size_t)256 * ndiag * ndiag, sizeof(int64_t));
+    int rc = (!de2 || !smap || (delta && !dhat) || !c.S || !c.C) ? fail(-2, "orc_trispectrum_full: out of memory")
+                                                                 : orc_shell_map(N, nshell, edges, smap);
+    for (int j = 0; j <= ndiag && !rc; j++) de2[j] = dedges[j] * dedges[j];
+    if (!rc && delta) rc = orc_forward(N, delta, dhat);
+    for (int t = 0; t < 3 && !rc; t++) {
+        int32_t cnt = 0;
+        for (size_t i = 0; i < n3; i++) cnt += smap[i] == k[t] - 1;
+        c.modes[t] = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt + 1));
+        if (!c.modes[t]) {
+            rc = fail(-2, "orc_trispectrum_full: out of memory");
+            break;
+        }
+        c.nm[t] = 0;
+        for (size_t i = 0; i < n3; i++)
+            if (smap[i] == k[t] - 1) c.modes[t][c.nm[t]++] = (int32_t)i;
+    }
+    if (!rc) {
+        c.de2 = de2;
+        c.dhat = (const cplx*)dhat;
+        c.smap = smap;
+        c.k4 = k[3] - 1;
+        par_for(c.nm[0], tfull_range, &c);
+        for (int j = 0; j < ndiag * ndiag; j++) {
+            double sv = 0.0;
+            int64_t cv = 0;
+            for (int t = 0; t < 256; t++) {
+                sv += c.S[(size_t)t * ndiag * ndiag + j];
+                cv += c.C[(size_t)t * ndiag * ndiag + j];
+            }
+            if (S) S[j] = (double)n3 * sv;
+            if (counts) counts[j] = cv;
+        }
+    }
+    for (int t = 0; t < 3; t++) free(c.modes[t]);
+    free(de2);
+    free(smap);
+    free(dhat);
+    free(c.S);
+    free(c.C);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* adjoint of the estimator for L = sum_b g_b B_b (g = dL/dB).                */
 /* B_b = c_b S_b with c_b = V^{n-1}/N^{3n} / (N^3 count_b) and               */
 /* S_b = sum_x prod_t D_{b_t}(x); D_m = inverse(mask_m * forward(delta)).    */

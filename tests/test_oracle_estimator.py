@@ -243,6 +243,53 @@ def test_multipole_estimator_rejects_odd_ell():
         oracle.estimate_ell(np.zeros((12, 12, 12)), 1.0, fieldgen.unit_edges(3), 3, 1, [[1, 1, 1]])
 
 
+def test_full_shape_trispectrum_reduces_to_the_angle_average():
+    """Eq. Tkfull: summed over diagonal bins that cover every |q1 - q2| and |q1 - q3|, the full-shape sums
+    and counts of each bin are the angle-averaged trispectrum's S_b and count_b."""
+    N, L, e = 14, 100.0, fieldgen.unit_edges(3)
+    d = fieldgen.field("lognormal", N, 8, np.float64)
+    bins = oracle.enumerate_bins(e, 4, oracle.RULE_ALL_SORTED)
+    ref = oracle.estimate(d, L, e, 4, bins=bins)
+    de = np.concatenate([[0.0], np.arange(8) + 0.5])  # diagonals 0, then unit bins up to 7.5 > 2 * 3.5
+    for b, S_b, c_b in zip(bins, ref["S"], ref["counts"]):
+        r = oracle.trispectrum_full(d, L, e, b, de)
+        assert r["counts"].sum() == c_b
+        assert abs(r["S"].sum() - S_b) <= 1e-9 * max(1.0, np.abs(r["S"]).sum())
+    assert ref["counts"].max() > 0
+
+
+def test_full_shape_trispectrum_matches_enumeration():
+    """The diagonal binning against an independent enumeration of the quadrilaterals with numpy."""
+    N, L, e = 10, 100.0, fieldgen.unit_edges(2)
+    d = fieldgen.field("lognormal", N, 9, np.float64)
+    de = np.array([0.0, 0.5, 1.5, 2.5, 3.5, 5.0])
+    k = (2, 2, 1, 1)
+    dh = np.fft.fftn(d)
+    smap = np_shell_map(N, e)
+    f = np.fft.fftfreq(N) * N
+    modes = [np.argwhere(smap == s) for s in range(2)]
+    S = np.zeros((5, 5))
+    C = np.zeros((5, 5), dtype=np.int64)
+    for q1 in modes[k[0] - 1]:
+        for q2 in modes[k[1] - 1]:
+            p1 = f[q1] - f[q2]
+            j1 = np.searchsorted(de ** 2, p1 @ p1, side="right") - 1
+            for q3 in modes[k[2] - 1]:
+                q4 = (-(q1 + q2 + q3)) % N
+                if smap[tuple(q4)] != k[3] - 1:
+                    continue
+                p2 = f[q1] - f[q3]
+                j2 = np.searchsorted(de ** 2, p2 @ p2, side="right") - 1
+                if not (0 <= j1 < 5 and 0 <= j2 < 5):
+                    continue
+                C[j1, j2] += 1
+                S[j1, j2] += np.real(dh[tuple(q1)] * dh[tuple(q2)] * dh[tuple(q3)] * dh[tuple(q4)])
+    r = oracle.trispectrum_full(d, L, e, k, de)
+    assert np.array_equal(r["counts"], C)
+    assert np.allclose(r["S"], N ** 3 * S, rtol=1e-10, atol=1e-10 * np.abs(N ** 3 * S).max())
+    assert C.sum() > 0 and np.count_nonzero(C) > 3
+
+
 def test_counts_n2_are_mode_counts():
     N, e = 16, fieldgen.unit_edges(6)
     bins = oracle.enumerate_bins(e, 2, oracle.RULE_ALL_SORTED)

@@ -49,6 +49,9 @@ MUTANTS = {
                       "test_oracle_estimator.py -k multipole"),
     "multipole_axis": ("legendre(ell, qz / sqrt(qx * qx + qy * qy + qz * qz));",
                        "legendre(ell, qx / sqrt(qx * qx + qy * qy + qz * qz));", "test_oracle_estimator.py -k multipole"),
+    "full_shape_diagonal": ("const double w0 = signed_freq(x1, N) - signed_freq(x3, N),",
+                            "const double w0 = signed_freq(x1, N) - signed_freq(x2, N),",
+                            "test_oracle_estimator.py -k full_shape"),
     "multipole_factor": ("norm = (2.0 * ell + 1.0) * pow(L * L * L, order - 1)", "norm = pow(L * L * L, order - 1)",
                          "test_oracle_estimator.py -k multipole"),
 }
