@@ -26,6 +26,17 @@ extern "C" {
  */
 int poly_diag_tc_gemm(const uint16_t* A_host, const uint16_t* B_host, int N, float* D_host);
 
+/*
+ * A stalled producer, simulated: one warp waits on a shared-memory barrier
+ * that nothing arrives on, through the same bounded wait the pipelines use
+ * (a clock64 budget of about 2 s).  The wait gives up, the kernel sets the
+ * error word and returns, and the host reports what the pipelines report for
+ * it.  Returns 5 (POLY_ERR_TIMEOUT) when the wait gave up as designed, 0 if
+ * it completed (which would be a defect), 4 on a CUDA error.  ms_out
+ * (nullable) receives the kernel's duration.  Synchronises the device.
+ */
+int poly_diag_stalled_wait(double* ms_out);
+
 #ifdef __cplusplus
 }
 #endif

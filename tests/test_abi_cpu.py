@@ -32,6 +32,10 @@ def test_header_declares_the_binding_names():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_symbols():
         assert hasattr(lib, name), name
+    diag = open(os.path.join(ROOT, "include", "polyspec_diag.h")).read()
+    diag = re.sub(r"/\*.*?\*/", "", diag, flags=re.S)
+    for name in set(re.findall(r"\b(poly_diag_[a-z_0-9]+)\s*\(", diag)):
+        assert hasattr(lib, name), name
 
 
 def test_status_strings(lib):

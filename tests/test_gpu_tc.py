@@ -74,3 +74,24 @@ def test_tcgen05_gemm_distinguishes_every_element():
     B[np.arange(64), np.arange(64) % 32] = 2.0 ** (np.arange(64) % 8)
     D = run_gemm(A, B)
     assert np.array_equal(D, A @ B.T)
+
+
+def test_bounded_wait_gives_up_on_a_stalled_producer():
+    """A wait on a barrier that nothing arrives on (a stalled producer) ends with POLY_ERR_TIMEOUT after the
+    clock budget, through the pipelines' own bounded wait, and leaves the context usable."""
+    from paper_1904_11055_gb300 import build
+
+    build.build()
+    import fieldgen
+
+    lib = ps.load_library()
+    lib.poly_diag_stalled_wait.argtypes = [ctypes.c_void_p]
+    lib.poly_diag_stalled_wait.restype = ctypes.c_int
+    ms = ctypes.c_double()
+    assert lib.poly_diag_stalled_wait(ctypes.byref(ms)) == 5  # POLY_ERR_TIMEOUT
+    assert 300.0 < ms.value < 30000.0, ms.value
+    plan = ps.Plan(16, 100.0, 3, fieldgen.unit_edges(4), "split_bf16")
+    d = torch.from_numpy(fieldgen.field("lognormal", 16, 1, np.float32)).cuda()
+    B = plan.estimate(d)
+    torch.cuda.synchronize()
+    assert torch.isfinite(B).all()
