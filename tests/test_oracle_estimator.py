@@ -312,6 +312,21 @@ def test_triangle_counts_follow_eq_ntri():
     assert abs(np.median(ratio[big]) - 1.0) < 0.05
 
 
+def test_quadrilateral_counts_follow_eq_nquad():
+    """Eq. Nquad's clean form (8 pi^3 dk^4 k1 k2 k3 k4 (-k1 + k2 + k3 + 3 k4 - |k1 - k2 - k3 + k4|)) holds to
+    about 40 % (Sec. 4.2); a loose band on the bins with k4 >= 3."""
+    N, e = 32, fieldgen.unit_edges(7)
+    r = oracle.estimate(np.zeros((N, N, N)), 1.0, e, 4)
+    k = r["bins"].astype(float)
+    nq = 8 * np.pi ** 3 * k.prod(axis=1) * (-k[:, 0] + k[:, 1] + k[:, 2] + 3 * k[:, 3]
+                                            - np.abs(k[:, 0] - k[:, 1] - k[:, 2] + k[:, 3]))
+    sel = (k[:, 3] >= 3) & (nq > 0)
+    ratio = r["counts"][sel] / nq[sel]
+    assert sel.sum() > 50
+    assert np.all((ratio > 0.4) & (ratio < 1.6))
+    assert abs(np.median(ratio) - 1.0) < 0.15
+
+
 # --------------------------------------------------------------------------- product sums
 @pytest.mark.parametrize("N,order,nshell,kind,seed", [(16, 3, 6, "white", 1), (18, 3, 5, "lognormal", 2),
                                                       (12, 4, 4, "white", 3), (16, 2, 6, "white", 4)])
