@@ -1,4 +1,4 @@
-"""Pins for the oracle's own FFT: a library DFT (numpy.fft) and Parseval's identity."""
+"""Pins for the oracle's own FFT: the O(n^2) DFT written out, a library DFT (numpy.fft) and Parseval's identity."""
 import numpy as np
 import pytest
 
@@ -13,6 +13,26 @@ def test_fft1d_matches_numpy(n, sign):
     got = oracle.fft1d(x, sign)
     ref = np.fft.fft(x) if sign == -1 else np.fft.ifft(x) * n
     assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n", [8, 12, 15, 16])
+def test_fft1d_matches_the_dft_definition(n):
+    """X[k] = sum_j x[j] exp(sign 2 pi i j k / n), summed term by term."""
+    rng = np.random.default_rng(100 + n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    jk = np.outer(np.arange(n), np.arange(n))
+    for sign in (-1, 1):
+        ref = np.exp(sign * 2j * np.pi * jk / n) @ x
+        assert np.abs(oracle.fft1d(x, sign) - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_fft3d_matches_the_dft_definition():
+    """The 8^3 transform against the separable sum over all 8^3 points, term by term."""
+    rng = np.random.default_rng(8)
+    a = rng.standard_normal((8, 8, 8)) + 1j * rng.standard_normal((8, 8, 8))
+    W = np.exp(-2j * np.pi * np.outer(np.arange(8), np.arange(8)) / 8)
+    ref = np.einsum("ax,by,cz,xyz->abc", W, W, W, a)
+    assert np.abs(oracle.fft3d(a, -1) - ref).max() < 1e-11
 
 
 @pytest.mark.parametrize("shape", [(8, 8, 8), (6, 10, 12), (16, 5, 9), (3, 1, 4)])
