@@ -37,6 +37,17 @@ int poly_diag_tc_gemm(const uint16_t* A_host, const uint16_t* B_host, int N, flo
  */
 int poly_diag_stalled_wait(double* ms_out);
 
+/*
+ * The plan's shell fields of delta_x (device, N^3 real of the plan's type):
+ * runs the forward transform and the shell-field stage exactly as
+ * poly_estimate does, synchronises `stream`, and copies the fields to
+ * fields_host (host, nfield x N^3 of the plan's real type, natural layout
+ * [slot][x][y][z]; nfield = nshell, or 2 nshell for a multipole plan, the
+ * Legendre-weighted fields after the plain ones).  `plan` is a poly_plan.
+ * Returns a poly_status.
+ */
+int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

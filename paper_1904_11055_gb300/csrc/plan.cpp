@@ -17,6 +17,7 @@
 #include "../../include/polyspec.h"
 #include "kernels.h"
 #include "plan_internal.h"
+#include "../../include/polyspec_diag.h"
 
 namespace {
 
@@ -723,6 +724,32 @@ poly_status poly_trispectrum_disconnected(poly_plan p, const void* delta_x, doub
     int prev;
     PS_TRY(enter(p, &prev));
     poly_status s = ps_disconnected_impl(p, delta_x, out, shell_power_or_null, (cudaStream_t)stream);
+    leave(p, prev);
+    return s;
+}
+
+int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* stream) {
+    PsPlan* p = (PsPlan*)plan;
+    if (!p || !delta_x || !fields_host) return set_error(POLY_ERR_ARG, "NULL argument");
+    int prev;
+    PS_TRY(enter(p, &prev));
+    cudaStream_t st = (cudaStream_t)stream;
+    poly_status s = ps_fields(p, delta_x, st);
+    const size_t n3 = (size_t)p->N * p->N * p->N, es = p->is_double ? 8 : 4, nf = (size_t)p->nfield;
+    std::vector<unsigned char> tiled;
+    cudaError_t e;
+    if (!s && (e = cudaStreamSynchronize(st))) s = cuda_error(e, "stream synchronise");
+    if (!s) {
+        tiled.resize(nf * n3 * es);
+        if ((e = cudaMemcpy(tiled.data(), p->d_fields, tiled.size(), cudaMemcpyDeviceToHost)))
+            s = cuda_error(e, "device to host copy");
+    }
+    if (!s) {  // cell-tiled [cell / 32][slot][cell % 32] -> natural [slot][cell]
+        unsigned char* out = (unsigned char*)fields_host;
+        for (size_t f = 0; f < nf; f++)
+            for (size_t cell = 0; cell < n3; cell++)
+                std::memcpy(out + (f * n3 + cell) * es, tiled.data() + ((cell >> 5) * nf * 32 + f * 32 + (cell & 31)) * es, es);
+    }
     leave(p, prev);
     return s;
 }
