@@ -48,6 +48,33 @@ int poly_diag_stalled_wait(double* ms_out);
  */
 int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* stream);
 
+/*
+ * The host tables a plan builds, computed on the host alone (no device call):
+ * the bins (Sec. 4.2 ordering, App. B polygon rule unless POLY_BINS_ALL_SORTED),
+ * the shell line tables of the pruned inverse transforms and the CUDA-core
+ * contraction tiles.  Arguments N, order, edges (nshell + 1 values), flags and
+ * ell are those of poly_plan_create_multipole and are checked the same way
+ * (precision taken as FP64); the tiles are the final ones, so for ell > 0 the
+ * first leg reads the weighted slot k_1 - 1 + nshell.
+ *   sizes[7] (required) receives the element counts: bins (tuples), tiles,
+ *   field ids, row factor records, column factor records, lines, line offsets.
+ *   Each other pointer may be NULL (not written) or a caller-owned host buffer:
+ *   bins      int32 [nbins][order], 1-based shells;
+ *   tiles     int32 [ntiles][8]: row_off, nrow, col_off, ncol, field_off, nfield,
+ *             region_mask (bit (r / 32) * 4 + c / 16), padding;
+ *   field_ids int32, 0-based field slots, tile t's at field_off .. + nfield;
+ *   rowf/colf int16 [][4]: up to three tile-local field indices (-1: none),
+ *             row r of tile t at rowf[row_off + r], column c at colf[col_off + c];
+ *   slot      int64 [nbins]: t * 4096 + r * 64 + c, the product that is bin b;
+ *   lines     int16 [nlines][4]: ky, kz >= 0, a, b: shell s's modes on the line
+ *             (ky, kz) are those with a <= |kx| <= b; lines line_off[s] ..
+ *             line_off[s + 1] - 1, and slot nshell holds the union of all shells.
+ * Returns a poly_status.
+ */
+int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
+                          int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids, int16_t* rowf,
+                          int16_t* colf, int64_t* slot, int16_t* lines, int32_t* line_off);
+
 #ifdef __cplusplus
 }
 #endif

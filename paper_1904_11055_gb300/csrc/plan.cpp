@@ -389,8 +389,11 @@ static void free_plan(PsPlan* p) {
     delete p;
 }
 
-static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
-                               poly_precision prec, unsigned flags, int ell) {
+// The host part of plan creation: argument checks, the bins, the shell line tables
+// (slot nshell holds the union of all shells, used by the adjoint) and the
+// CUDA-core contraction tiles over the plain fields.  Touches no device.
+static poly_status plan_host_tables(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
+                                    poly_precision prec, unsigned flags, int ell, std::vector<short>& lines) {
     if (!edges || nshell < 1 || nshell > 128) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
     if (ell < 0 || ell > 8 || (ell & 1)) return set_error(POLY_ERR_ARG, "ell must be even, in [0, 8]");
     if (ell > 0 && prec == POLY_SPLIT_BF16)
@@ -430,6 +433,33 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     enumerate_bins(nshell, p->edges, order, (flags & POLY_BINS_ALL_SORTED) != 0, p->bins);
     p->nbins = (int64_t)p->bins.size() / order;
 
+    // shell line tables
+    std::vector<int> off{0};
+    for (int s = 0; s < nshell; s++) {
+        build_lines(p, p->edges.data(), s, lines);
+        int kzm = 0;
+        for (size_t l = off.back(); l < lines.size() / 4; l++) kzm = std::max(kzm, (int)lines[4 * l + 1]);
+        p->shell_kz.push_back(kzm);
+        off.push_back((int)(lines.size() / 4));
+    }
+    {
+        const double ue[2] = {p->edges[0], p->edges[nshell]};
+        build_lines(p, ue, 0, lines);
+        off.push_back((int)(lines.size() / 4));
+    }
+    p->line_off = off;
+    for (int s = 0; s <= nshell; s++) p->max_lines = std::max(p->max_lines, off[s + 1] - off[s]);
+    build_cc_tiles(p, p->cc, 0);
+    return POLY_OK;
+}
+
+static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
+                               poly_precision prec, unsigned flags, int ell) {
+    std::vector<short> lines;
+    PS_TRY(plan_host_tables(p, N, L, order, nshell, edges, prec, flags, ell, lines));
+    const int K = p->K;
+    const std::vector<int>& off = p->line_off;
+
     PS_CUDA(cudaGetDevice(&p->device));
     cudaDeviceProp prop;
     PS_CUDA(cudaGetDeviceProperties(&prop, p->device));
@@ -450,28 +480,10 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
     PS_TRY(upload(p, &p->d_tw_fwd, twf));
     PS_TRY(upload(p, &p->d_tw_inv, twi));
 
-    // shell line tables; slot nshell holds the union of all shells (adjoint)
-    std::vector<short> lines;
-    std::vector<int> off{0};
-    for (int s = 0; s < nshell; s++) {
-        build_lines(p, p->edges.data(), s, lines);
-        int kzm = 0;
-        for (size_t l = off.back(); l < lines.size() / 4; l++) kzm = std::max(kzm, (int)lines[4 * l + 1]);
-        p->shell_kz.push_back(kzm);
-        off.push_back((int)(lines.size() / 4));
-    }
-    {
-        const double ue[2] = {p->edges[0], p->edges[nshell]};
-        build_lines(p, ue, 0, lines);
-        off.push_back((int)(lines.size() / 4));
-    }
-    p->line_off = off;
-    for (int s = 0; s <= nshell; s++) p->max_lines = std::max(p->max_lines, off[s + 1] - off[s]);
     PS_TRY(upload(p, &p->d_lines, lines));
     PS_TRY(upload(p, (void**)&p->d_line_off, off));
 
     // contraction tiles (CUDA-core path; the counts use them too)
-    build_cc_tiles(p, p->cc, 0);
     PS_TRY(upload(p, &p->d_cc_tiles, p->cc.tiles));
     PS_TRY(upload(p, &p->d_cc_field_ids, p->cc.field_ids));
     PS_TRY(upload(p, &p->d_cc_rowf, p->cc.rowf));
@@ -752,6 +764,32 @@ int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* s
     }
     leave(p, prev);
     return s;
+}
+
+int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
+                          int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids, int16_t* rowf,
+                          int16_t* colf, int64_t* slot, int16_t* lines, int32_t* line_off) {
+    if (!sizes) return set_error(POLY_ERR_ARG, "NULL sizes");
+    PsPlan h;  // host tables only: no device call, no device memory
+    std::vector<short> ln;
+    PS_TRY(plan_host_tables(&h, N, 1.0, order, nshell, edges, POLY_FP64, flags, ell, ln));
+    if (ell > 0) {  // as poly_plan_create_multipole leaves them: the first leg on the weighted slots
+        h.cc = CcTiles();
+        build_cc_tiles(&h, h.cc, nshell);
+    }
+    const int64_t n[7] = {h.nbins, (int64_t)h.cc.tiles.size(), (int64_t)h.cc.field_ids.size(),
+                          (int64_t)h.cc.rowf.size(), (int64_t)h.cc.colf.size(), (int64_t)ln.size() / 4,
+                          (int64_t)h.line_off.size()};
+    for (int i = 0; i < 7; i++) sizes[i] = n[i];
+    if (bins) std::memcpy(bins, h.bins.data(), h.bins.size() * sizeof(int32_t));
+    if (tiles) std::memcpy(tiles, h.cc.tiles.data(), h.cc.tiles.size() * sizeof(PsTile));
+    if (field_ids) std::memcpy(field_ids, h.cc.field_ids.data(), h.cc.field_ids.size() * sizeof(int32_t));
+    if (rowf) std::memcpy(rowf, h.cc.rowf.data(), h.cc.rowf.size() * sizeof(short4));
+    if (colf) std::memcpy(colf, h.cc.colf.data(), h.cc.colf.size() * sizeof(short4));
+    if (slot) std::memcpy(slot, h.cc.slot.data(), h.cc.slot.size() * sizeof(int64_t));
+    if (lines) std::memcpy(lines, ln.data(), ln.size() * sizeof(short));
+    if (line_off) std::memcpy(line_off, h.line_off.data(), h.line_off.size() * sizeof(int32_t));
+    return POLY_OK;
 }
 
 poly_status poly_estimate_host(poly_plan p, const void* delta_x_host, double* out_host, void* stream) {
