@@ -75,6 +75,33 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
                           int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids, int16_t* rowf,
                           int16_t* colf, int64_t* slot, int16_t* lines, int32_t* line_off);
 
+/*
+ * The tensor-core contraction's host tables for a split-BF16 plan, computed on
+ * the host alone: which products of fields (rows: the first legs, as a pair for
+ * n >= 3; columns: the remaining legs) each block accumulates where, and where
+ * the reduction finds each bin.  N, order (2..4), edges, nshell and flags as in
+ * poly_plan_create; sms (the device's SM count), max_mt (M tiles per group) and
+ * cta_mult (the block budget is sms x cta_mult / 2) as poly_plan_set_config
+ * and the device would set them.
+ *   sizes[7] (required) receives the counts: bins, blocks, groups, M tiles,
+ *   runs, row factor records, column factor records.  Other pointers may be
+ *   NULL or caller-owned host buffers:
+ *   ctas   int64 [nblocks][3]: group, first chunk, end chunk (chunks of 32 cells);
+ *   groups int32 [ngroups][5]: first M tile, M tiles, first column record,
+ *          columns (a multiple of 16), accumulator columns;
+ *   mtiles int32 [][3]: first row record (128 rows), first run, runs;
+ *   runs   int32 [][4]: first local column n0, columns nn, first accumulator
+ *          column acc, M tile within the group: accumulator column acc + j of
+ *          that M tile's row r is the product of row r and column n0 + j;
+ *   rowf, colf int16 [][2]: 0-based field slots (-1: none);
+ *   binmap int32 [nbins][3]: first block, blocks, slot = accumulator column x
+ *          128 + row; bin b is the sum of that slot over those blocks.
+ * Returns a poly_status.
+ */
+int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms, int max_mt,
+                        int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups, int32_t* mtiles,
+                        int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -597,11 +597,19 @@ static std::vector<std::pair<int, int>> tc_runs(const std::set<int>& blocks) {
 
 // Build the groups: 32-row blocks of rows sorted by column span, 128-row M tiles,
 // 16-column blocks.
-poly_status ps_tc_prepare(PsPlan* p) {
-    if (p->is_double) return POLY_ERR_UNSUPPORTED;
-    TcState* t = new (std::nothrow) TcState();
-    if (!t) return POLY_ERR_ALLOC;
-    p->tc = t;
+// Host tables of the contraction: groups of M-tile instances, their accumulator
+// runs, the row and column factors, the blocks (group, chunk range) and the bin
+// map.  Fills t's host fields (ra, ca, nshell, ngroups, ctas, executed flops)
+// and h; touches no device.
+struct TcTables {
+    std::vector<TcGroup> groups;
+    std::vector<TcMTile> mtiles;
+    std::vector<int4> runs;
+    std::vector<short2> rowf, colf;
+    std::vector<int4> binmap;
+};
+
+static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     const int n = p->order;
     t->ra = n >= 3 ? 2 : 1;
     t->ca = n - t->ra;
@@ -738,11 +746,12 @@ poly_status ps_tc_prepare(PsPlan* p) {
         ngroups++;
     }
     t->ngroups = (int)gplans.size();
-    // device tables
-    std::vector<TcGroup> groups;
-    std::vector<TcMTile> mtiles;
-    std::vector<int4> runs;
-    std::vector<short2> rowf, colf;
+    // tables
+    std::vector<TcGroup>& groups = h.groups;
+    std::vector<TcMTile>& mtiles = h.mtiles;
+    std::vector<int4>& runs = h.runs;
+    std::vector<short2>& rowf = h.rowf;
+    std::vector<short2>& colf = h.colf;
     std::map<std::tuple<int, int, int, int>, std::pair<int, int>> slot_of;  // (row, col) keys -> (group, slot)
     std::vector<std::pair<int, int>> gcol_key(gcol.size());
     for (auto& kv : gcol) gcol_key[kv.second] = kv.first;
@@ -832,26 +841,39 @@ poly_status ps_tc_prepare(PsPlan* p) {
             t->ctas.push_back(c);
         }
     }
-    std::vector<int4> binmap(p->nbins);
+    std::vector<int4>& binmap = h.binmap;
+    binmap.resize(p->nbins);
     for (int64_t i = 0; i < p->nbins; i++) {
         auto rk = rkey(&p->bins[i * n]);
         auto ck = ckey(&p->bins[i * n]);
         auto gs = slot_of.at({rk.first, rk.second, ck.first, ck.second});
         binmap[i] = make_int4(first[gs.first], nsplit[gs.first], gs.second, 0);
     }
-    auto up = [&](void** d, const void* h, size_t bytes) -> poly_status {
+    return POLY_OK;
+}
+
+poly_status ps_tc_prepare(PsPlan* p) {
+    if (p->is_double) return POLY_ERR_UNSUPPORTED;
+    TcState* t = new (std::nothrow) TcState();
+    if (!t) return POLY_ERR_ALLOC;
+    p->tc = t;
+    TcTables h;
+    if (poly_status s0 = tc_build_tables(p, t, h)) return s0;
+    const std::vector<TcGroup>& groups = h.groups;
+    const int64_t ncell = (int64_t)p->N * p->N * p->N;
+    auto up = [&](void** d, const void* src, size_t bytes) -> poly_status {
         poly_status s = ps_alloc(p, d, bytes);
         if (s) return s;
-        return cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) ? POLY_ERR_CUDA : POLY_OK;
+        return cudaMemcpy(*d, src, bytes, cudaMemcpyHostToDevice) ? POLY_ERR_CUDA : POLY_OK;
     };
     poly_status s;
     if ((s = up(&t->d_ctas, t->ctas.data(), t->ctas.size() * sizeof(TcCta))) ||
         (s = up(&t->d_groups, groups.data(), groups.size() * sizeof(TcGroup))) ||
-        (s = up(&t->d_mtiles, mtiles.data(), mtiles.size() * sizeof(TcMTile))) ||
-        (s = up(&t->d_runs, runs.data(), std::max<size_t>(1, runs.size()) * sizeof(int4))) ||
-        (s = up(&t->d_rowf, rowf.data(), rowf.size() * sizeof(short2))) ||
-        (s = up(&t->d_colf, colf.data(), colf.size() * sizeof(short2))) ||
-        (s = up(&t->d_binmap, binmap.data(), std::max<size_t>(1, binmap.size()) * sizeof(int4))))
+        (s = up(&t->d_mtiles, h.mtiles.data(), h.mtiles.size() * sizeof(TcMTile))) ||
+        (s = up(&t->d_runs, h.runs.data(), std::max<size_t>(1, h.runs.size()) * sizeof(int4))) ||
+        (s = up(&t->d_rowf, h.rowf.data(), h.rowf.size() * sizeof(short2))) ||
+        (s = up(&t->d_colf, h.colf.data(), h.colf.size() * sizeof(short2))) ||
+        (s = up(&t->d_binmap, h.binmap.data(), std::max<size_t>(1, h.binmap.size()) * sizeof(int4))))
         return s;
     if ((s = ps_alloc(p, (void**)&t->d_partial, t->ctas.size() * (size_t)kTcAccMax * 128 * 8))) return s;
     if ((s = ps_alloc(p, (void**)&t->d_err, 16))) return s;
@@ -888,6 +910,58 @@ poly_status ps_tc_prepare(PsPlan* p) {
     t->window = p->order >= 4 ? 16 : 64;
     const char* w = getenv("POLY_TC_WINDOW");
     if (w && atoi(w) > 0) t->window = atoi(w);
+    return POLY_OK;
+}
+
+extern "C" int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms,
+                                   int max_mt, int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups,
+                                   int32_t* mtiles, int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap) {
+    if (!sizes || sms < 1 || max_mt < 1 || cta_mult < 1) return POLY_ERR_ARG;
+    PsPlan hp;  // host tables only: no device call, no device memory
+    std::vector<short> lines;
+    if (poly_status s = ps_plan_host_tables(&hp, N, 1.0, order, nshell, edges, POLY_SPLIT_BF16, flags, 0, lines))
+        return s;
+    hp.sms = sms;
+    hp.tc_max_mt = max_mt;
+    hp.tc_cta_mult = cta_mult;
+    TcState t;
+    TcTables h;
+    if (poly_status s = tc_build_tables(&hp, &t, h)) return s;
+    const int64_t n[7] = {hp.nbins, (int64_t)t.ctas.size(), (int64_t)h.groups.size(), (int64_t)h.mtiles.size(),
+                          (int64_t)h.runs.size(), (int64_t)h.rowf.size(), (int64_t)h.colf.size()};
+    for (int i = 0; i < 7; i++) sizes[i] = n[i];
+    for (size_t i = 0; ctas && i < t.ctas.size(); i++) {
+        ctas[3 * i] = t.ctas[i].group;
+        ctas[3 * i + 1] = t.ctas[i].c0;
+        ctas[3 * i + 2] = t.ctas[i].c1;
+    }
+    for (size_t i = 0; groups && i < h.groups.size(); i++) {
+        const TcGroup& g = h.groups[i];
+        const int32_t v[5] = {g.mt_off, g.nmt, g.col_off, g.ncol, g.acc_cols};
+        std::memcpy(groups + 5 * i, v, sizeof v);
+    }
+    for (size_t i = 0; mtiles && i < h.mtiles.size(); i++) {
+        mtiles[3 * i] = h.mtiles[i].row_off;
+        mtiles[3 * i + 1] = h.mtiles[i].run_off;
+        mtiles[3 * i + 2] = h.mtiles[i].nrun;
+    }
+    for (size_t i = 0; runs && i < h.runs.size(); i++) {
+        const int32_t v[4] = {h.runs[i].x, h.runs[i].y, h.runs[i].z, h.runs[i].w};
+        std::memcpy(runs + 4 * i, v, sizeof v);
+    }
+    for (size_t i = 0; rowf && i < h.rowf.size(); i++) {
+        rowf[2 * i] = h.rowf[i].x;
+        rowf[2 * i + 1] = h.rowf[i].y;
+    }
+    for (size_t i = 0; colf && i < h.colf.size(); i++) {
+        colf[2 * i] = h.colf[i].x;
+        colf[2 * i + 1] = h.colf[i].y;
+    }
+    for (size_t i = 0; binmap && i < h.binmap.size(); i++) {
+        binmap[3 * i] = h.binmap[i].x;
+        binmap[3 * i + 1] = h.binmap[i].y;
+        binmap[3 * i + 2] = h.binmap[i].z;
+    }
     return POLY_OK;
 }
 

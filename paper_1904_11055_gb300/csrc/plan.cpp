@@ -392,8 +392,8 @@ static void free_plan(PsPlan* p) {
 // The host part of plan creation: argument checks, the bins, the shell line tables
 // (slot nshell holds the union of all shells, used by the adjoint) and the
 // CUDA-core contraction tiles over the plain fields.  Touches no device.
-static poly_status plan_host_tables(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
-                                    poly_precision prec, unsigned flags, int ell, std::vector<short>& lines) {
+poly_status ps_plan_host_tables(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
+                               poly_precision prec, unsigned flags, int ell, std::vector<short>& lines) {
     if (!edges || nshell < 1 || nshell > 128) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
     if (ell < 0 || ell > 8 || (ell & 1)) return set_error(POLY_ERR_ARG, "ell must be even, in [0, 8]");
     if (ell > 0 && prec == POLY_SPLIT_BF16)
@@ -456,7 +456,7 @@ static poly_status plan_host_tables(PsPlan* p, int N, double L, int order, int n
 static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
                                poly_precision prec, unsigned flags, int ell) {
     std::vector<short> lines;
-    PS_TRY(plan_host_tables(p, N, L, order, nshell, edges, prec, flags, ell, lines));
+    PS_TRY(ps_plan_host_tables(p, N, L, order, nshell, edges, prec, flags, ell, lines));
     const int K = p->K;
     const std::vector<int>& off = p->line_off;
 
@@ -772,7 +772,7 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
     if (!sizes) return set_error(POLY_ERR_ARG, "NULL sizes");
     PsPlan h;  // host tables only: no device call, no device memory
     std::vector<short> ln;
-    PS_TRY(plan_host_tables(&h, N, 1.0, order, nshell, edges, POLY_FP64, flags, ell, ln));
+    PS_TRY(ps_plan_host_tables(&h, N, 1.0, order, nshell, edges, POLY_FP64, flags, ell, ln));
     if (ell > 0) {  // as poly_plan_create_multipole leaves them: the first leg on the weighted slots
         h.cc = CcTiles();
         build_cc_tiles(&h, h.cc, nshell);

@@ -147,3 +147,110 @@ def test_host_checks_match_plan_creation(lib, kwargs, status):
     kw = dict(edges=fieldgen.unit_edges(6), flags=0, ell=0) | kwargs
     rc, _ = host_tables(lib, kw["N"], kw["order"], kw["edges"], kw["flags"], kw["ell"])
     assert rc == status
+
+
+# ------------------------------------------------------------------ tensor-core contraction tables
+
+def tc_tables(lib, N, order, edges, sms=152, max_mt=4, cta_mult=4, flags=0):
+    fn = lib.poly_diag_tc_tables
+    P = ctypes.c_void_p
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
+                   ctypes.c_int] + [P] * 8
+    fn.restype = ctypes.c_int
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    sizes = np.zeros(7, dtype=np.int64)
+    args = (N, order, e.ctypes.data, e.size - 1, flags, sms, max_mt, cta_mult)
+    rc = fn(*args, sizes.ctypes.data, *([None] * 7))
+    if rc:
+        return rc, None
+    nb, nc, ng, nm, nr, nrow, ncol = (int(v) for v in sizes)
+    t = dict(ctas=np.zeros((nc, 3), np.int64), groups=np.zeros((ng, 5), np.int32), mtiles=np.zeros((nm, 3), np.int32),
+             runs=np.zeros((nr, 4), np.int32), rowf=np.zeros((nrow, 2), np.int16), colf=np.zeros((ncol, 2), np.int16),
+             binmap=np.zeros((nb, 3), np.int32))
+    ptrs = [t[k].ctypes.data for k in ("ctas", "groups", "mtiles", "runs", "rowf", "colf", "binmap")]
+    assert fn(*args, sizes.ctypes.data, *ptrs) == 0
+    return 0, t
+
+
+def check_tc_tables(t, bins, N, nshell, max_mt):
+    order = bins.shape[1]
+    ra = 2 if order >= 3 else 1
+    ctas, groups, mtiles, runs, rowf, colf, bm = (t[k] for k in ("ctas", "groups", "mtiles", "runs", "rowf", "colf",
+                                                                "binmap"))
+    ng, nchunks = len(groups), (N ** 3 + 31) // 32
+    # blocks: each group's blocks are contiguous and their chunk ranges tile [0, nchunks)
+    first, count = np.zeros(ng, np.int64), np.zeros(ng, np.int64)
+    for g in range(ng):
+        idx = np.nonzero(ctas[:, 0] == g)[0]
+        assert idx.size >= 1 and np.all(np.diff(idx) == 1)
+        first[g], count[g] = idx[0], idx.size
+        c = ctas[idx]
+        assert c[0, 1] == 0 and c[-1, 2] == nchunks and np.all(c[1:, 1] == c[:-1, 2]) and np.all(c[:, 2] > c[:, 1])
+    # accumulator columns of each group: which M tile and local column each one holds (no column twice)
+    owner = []
+    for g, (mt_off, nmt, col_off, ncol, acc_cols) in enumerate(groups):
+        assert 1 <= nmt <= max_mt and ncol % 16 == 0 and 0 < ncol <= 256 and 0 < acc_cols <= 256
+        tab = -np.ones((256, 2), np.int64)
+        for m in range(mt_off, mt_off + nmt):
+            row_off, run_off, nrun = mtiles[m]
+            assert 1 <= nrun <= 4
+            rf = rowf[row_off:row_off + 128]
+            assert np.all((rf[:, 0] >= 0) & (rf[:, 0] < nshell))  # padding rows repeat a real row
+            assert np.all(rf[:, 1] < nshell) and np.all((rf[:, 1] >= 0) == (ra == 2))
+            for n0, nn, acc, mloc in runs[run_off:run_off + nrun]:
+                assert mloc == m - mt_off and nn % 16 == 0 and n0 % 16 == 0 and n0 + nn <= ncol
+                assert acc + nn <= acc_cols and np.all(tab[acc:acc + nn, 0] < 0)
+                tab[acc:acc + nn, 0] = m
+                tab[acc:acc + nn, 1] = col_off + n0 + np.arange(nn)
+        owner.append(tab)
+    owner = np.stack(owner)
+    # every bin: one group's blocks, a slot inside it, the right row and column factors
+    g = ctas[bm[:, 0], 0]
+    assert np.all(bm[:, 0] == first[g]) and np.all(bm[:, 1] == count[g])
+    acc_col, row = bm[:, 2] // 128, bm[:, 2] % 128
+    assert np.all(acc_col < groups[g, 4])
+    m, col = owner[g, acc_col, 0], owner[g, acc_col, 1]
+    assert np.all(m >= 0)
+    assert np.all(col < groups[g, 2] + groups[g, 3])
+    rf = rowf[mtiles[m, 0] + row].astype(np.int64)
+    cf = colf[col].astype(np.int64)
+    legs = bins.astype(np.int64) - 1
+    pad = -np.ones(len(bins), np.int64)
+    want_row = np.stack([legs[:, 0], legs[:, 1] if ra == 2 else pad], 1)
+    rest = legs[:, ra:]
+    want_col = np.stack([rest[:, 0], rest[:, 1] if rest.shape[1] > 1 else pad], 1)
+    assert np.array_equal(rf, want_row) and np.array_equal(cf, want_col)
+    key = g * (256 * 128) + bm[:, 2]
+    assert np.unique(key).size == key.size
+
+
+@pytest.mark.parametrize("max_mt", [2, 3, 4])
+@pytest.mark.parametrize("cta_mult", [1, 2, 4, 6, 8])
+def test_tc_tables_bispectrum_256cube_64shells(lib, max_mt, cta_mult):
+    """The benchmark's plan (256^3, 64 unit shells) in every contraction shape the tuner may choose."""
+    e = fieldgen.unit_edges(64)
+    rc, t = tc_tables(lib, 256, 3, e, 152, max_mt, cta_mult)
+    assert rc == 0
+    check_tc_tables(t, oracle.enumerate_bins(e, 3), 256, 64, max_mt)
+
+
+@pytest.mark.parametrize("N,order,nshell,width", [(256, 4, 32, 1.5), (96, 4, 10, 2.0), (48, 3, 12, 1.0),
+                                                  (64, 2, 30, 1.0), (128, 3, 40, 1.0)])
+@pytest.mark.parametrize("sms", [152, 20])
+def test_tc_tables_other_plans(lib, N, order, nshell, width, sms):
+    """The trispectrum (its pair columns split into several instances), the power spectrum, small grids."""
+    e = fieldgen.unit_edges(nshell, width)
+    rc, t = tc_tables(lib, N, order, e, sms)
+    assert rc == 0
+    check_tc_tables(t, oracle.enumerate_bins(e, order), N, nshell, 4)
+
+
+@pytest.mark.parametrize("kwargs,status", [
+    (dict(order=5), STATUS["POLY_ERR_UNSUPPORTED"]),
+    (dict(sms=0), STATUS["POLY_ERR_ARG"]),
+    (dict(N=16), STATUS["POLY_ERR_ALIAS"]),
+])
+def test_tc_tables_refuse_what_plan_creation_refuses(lib, kwargs, status):
+    kw = dict(N=64, order=3, sms=152) | kwargs
+    rc, _ = tc_tables(lib, kw["N"], kw["order"], fieldgen.unit_edges(6), kw["sms"])
+    assert rc == status
