@@ -102,6 +102,33 @@ int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsig
                         int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups, int32_t* mtiles,
                         int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap);
 
+/*
+ * The adjoint's host tables (poly_backward), computed on the host alone.  The
+ * gradient of B_b with respect to the field D_m at a cell is the sum, over the
+ * positions of m in b, of the product of b's other fields there (Eq. estimator
+ * differentiated); the adjoint gathers these by entry: (m, the other shells
+ * sorted), each listing the bins that produce it.  N, order (2..4), edges,
+ * nshell, flags and prec as in poly_plan_create; sms as the device would set it.
+ *   sizes[10] (required): entries, entry-bin records, then for the tensor-core
+ *   form (order 3, split-BF16; 0 groups when it does not apply): groups, chunks,
+ *   K (shells padded to 32), accumulator columns per buffer, bytes of one B
+ *   array, cell ranges per pair of groups, shells without entries, largest
+ *   chunk count of a group.  Other pointers may be NULL or host buffers:
+ *   moff   int32 [nshell + 1]: entries of shell m are moff[m] .. moff[m+1]-1;
+ *   ent    int16 [nent][3]: the other shells, 0-based, ascending (-1: none);
+ *   eoff   int32 [nent + 1], ebins int32: entry e's bins at ebins[eoff[e] ..
+ *          eoff[e+1]-1], a bin once per position of m in it;
+ *   at_groups int32 [][6]: first chunk, chunks, first chunk of the second
+ *          half, B byte offset, K-block masks of the two column runs;
+ *   at_chunks int32: j block | m << 8 | (last chunk of m) << 16;
+ *   at_pos int32 [nent]: byte offset of entry e's weight in the B arrays
+ *          (column = chunk x 16 + j % 16 of its group, row = first other shell).
+ * Returns a poly_status.
+ */
+int poly_diag_adj_tables(int N, int order, const double* edges, int nshell, unsigned flags, int prec, int sms,
+                         int64_t* sizes, int32_t* moff, int16_t* ent, int32_t* eoff, int32_t* ebins,
+                         int32_t* at_groups, int32_t* at_chunks, int32_t* at_pos);
+
 #ifdef __cplusplus
 }
 #endif

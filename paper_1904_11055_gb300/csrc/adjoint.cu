@@ -111,7 +111,11 @@ struct AdjTables {
     std::vector<int> line_off;  // host copy of the plan's line offsets
 };
 
-static poly_status adj_prepare(PsPlan* p, AdjTables& A) {
+// The adjoint's entries: one per (m, sorted other shells) that some bin holds,
+// grouped by m (moff), each listing its bins once per position of m in the bin
+// (eoff / ebins).  Host only.
+void ps_adj_entries(const PsPlan* p, std::vector<int>& moff, std::vector<short4>& ent, std::vector<int>& eoff,
+                    std::vector<int>& ebins) {
     const int n = p->order;
     // entries keyed by (m, sorted other shells); value: contributing bins
     std::map<std::vector<int>, std::vector<int>> ents;
@@ -127,8 +131,10 @@ static poly_status adj_prepare(PsPlan* p, AdjTables& A) {
             ents[key].push_back((int)b);
         }
     }
-    std::vector<int> moff(p->nshell + 1, 0), eoff{0}, ebins;
-    std::vector<short4> ent;
+    moff.assign(p->nshell + 1, 0);
+    eoff.assign(1, 0);
+    ebins.clear();
+    ent.clear();
     for (auto& kv : ents) moff[kv.first[0] + 1]++;
     for (int m = 0; m < p->nshell; m++) moff[m + 1] += moff[m];
     for (auto& kv : ents) {  // std::map order: grouped by m ascending
@@ -141,6 +147,13 @@ static poly_status adj_prepare(PsPlan* p, AdjTables& A) {
         ebins.insert(ebins.end(), kv.second.begin(), kv.second.end());
         eoff.push_back((int)ebins.size());
     }
+}
+
+static poly_status adj_prepare(PsPlan* p, AdjTables& A) {
+    const int n = p->order;
+    std::vector<int> moff, eoff, ebins;
+    std::vector<short4> ent;
+    ps_adj_entries(p, moff, ent, eoff, ebins);
     A.nent = (int)ent.size();
     if (n == 3 && p->prec == POLY_SPLIT_BF16) {
         std::vector<int> ent_m(ent.size());

@@ -307,13 +307,13 @@ static size_t at_smem_bytes(int nc0, int nc1, int kp) {
            8 * (8 + kAtDBufs) + 16;
 }
 
+// Host tables of the tensor-core adjoint: the groups of m's with their chunks
+// (m, j block) and the B position of every entry.  Fills S's host fields and
+// chunks, pos and b_total (bytes of one B array); touches no device.
 // ent: the adjoint's entries in order (m ascending), each (m, f1, f2) with f1 <= f2.
-poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::vector<short4>& ent, AtState** out) {
-    *out = nullptr;
+static poly_status at_build_tables(const PsPlan* p, const std::vector<int>& ent_m, const std::vector<short4>& ent,
+                                   AtState* S, std::vector<int>& chunks, std::vector<int>& pos, size_t& b_total) {
     const int64_t ncell = (int64_t)p->N * p->N * p->N;
-    if (p->order != 3 || p->prec != POLY_SPLIT_BF16 || p->nshell > kAtMaxK || ncell % 32) return POLY_ERR_UNSUPPORTED;
-    AtState* S = new (std::nothrow) AtState();
-    if (!S) return POLY_ERR_ALLOC;
     const int ns = p->nshell;
     S->kp = (ns + 31) / 32 * 32;  // the A stores write 16 columns (32 shells) of hi and of lo at a time
     const int kp = S->kp;
@@ -333,16 +333,12 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
     const int chunk_cap = S->acap / kAtChunk;
     // a group fits when two groups of its size fit one block (the blocks take pairs of groups)
     auto fits = [&](int nchunk) { return nchunk <= chunk_cap && at_smem_bytes(nchunk, nchunk, kp) <= 227 * 1024; };
-    std::vector<int> chunks;
     std::map<std::pair<int, int>, std::pair<int, int>> chpos;  // (m, jb) -> (group, chunk)
-    size_t b_total = 0;
+    b_total = 0;
     for (int m = 0; m < ns;) {
         int nch = 0, m1 = m;
         while (m1 < ns && fits(nch + (int)mjb[m1].size())) nch += (int)mjb[m1++].size();
-        if (m1 == m) {
-            delete S;
-            return POLY_ERR_UNSUPPORTED;  // one shell's chunks do not fit
-        }
+        if (m1 == m) return POLY_ERR_UNSUPPORTED;  // one shell's chunks do not fit
         int split = m1, best = nch, pre = 0;
         for (int ms = m; ms <= m1; ms++) {
             const int worst = std::max(pre, nch - pre);
@@ -372,7 +368,7 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
         m = m1;
     }
     // B positions of the entries (column 16 chunk + j % 16, row k = f1) and the nonzero K blocks of each run
-    std::vector<int> pos(ent.size(), -1);
+    pos.assign(ent.size(), -1);
     for (size_t e = 0; e < ent.size(); e++) {
         const int j = ent[e].y, k = ent[e].x;
         const auto gp = chpos.at({ent_m[e], j / kAtChunk});
@@ -387,6 +383,21 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
     const int64_t ntile = (ncell + kAtCells - 1) / kAtCells;
     const int npairs = ((int)S->groups.size() + 1) / 2;
     S->ranges = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (2 * p->sms + npairs - 1) / npairs));
+    return POLY_OK;
+}
+
+poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::vector<short4>& ent, AtState** out) {
+    *out = nullptr;
+    const int64_t ncell = (int64_t)p->N * p->N * p->N;
+    if (p->order != 3 || p->prec != POLY_SPLIT_BF16 || p->nshell > kAtMaxK || ncell % 32) return POLY_ERR_UNSUPPORTED;
+    AtState* S = new (std::nothrow) AtState();
+    if (!S) return POLY_ERR_ALLOC;
+    std::vector<int> chunks, pos;
+    size_t b_total = 0;
+    if (poly_status s0 = at_build_tables(p, ent_m, ent, S, chunks, pos, b_total)) {
+        delete S;
+        return s0;
+    }
     auto up = [&](void** d, const void* h, size_t bytes) -> poly_status {
         poly_status s = ps_alloc(p, d, bytes);
         if (s) return s;
@@ -407,6 +418,53 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
         return POLY_ERR_CUDA;
     }
     *out = S;
+    return POLY_OK;
+}
+
+extern "C" int poly_diag_adj_tables(int N, int order, const double* edges, int nshell, unsigned flags, int prec,
+                                    int sms, int64_t* sizes, int32_t* moff, int16_t* ent, int32_t* eoff,
+                                    int32_t* ebins, int32_t* at_groups, int32_t* at_chunks, int32_t* at_pos) {
+    if (!sizes || sms < 1) return POLY_ERR_ARG;
+    PsPlan hp;  // host tables only: no device call, no device memory
+    std::vector<short> lines;
+    if (poly_status s = ps_plan_host_tables(&hp, N, 1.0, order, nshell, edges, (poly_precision)prec, flags, 0, lines))
+        return s;
+    hp.sms = sms;
+    std::vector<int> mo, eo, eb;
+    std::vector<short4> en;
+    ps_adj_entries(&hp, mo, en, eo, eb);
+    AtState S;
+    std::vector<int> chunks, pos;
+    size_t b_total = 0;
+    bool at = order == 3 && prec == POLY_SPLIT_BF16 && nshell <= kAtMaxK && ((int64_t)N * N * N) % 32 == 0;
+    if (at) {
+        std::vector<int> ent_m(en.size());
+        for (int m = 0; m < nshell; m++)
+            for (int e = mo[m]; e < mo[m + 1]; e++) ent_m[e] = m;
+        const poly_status s = at_build_tables(&hp, ent_m, en, &S, chunks, pos, b_total);
+        if (s && s != POLY_ERR_UNSUPPORTED) return s;
+        at = !s;
+    }
+    const int64_t n[10] = {(int64_t)en.size(), (int64_t)eb.size(), at ? (int64_t)S.groups.size() : 0,
+                           at ? (int64_t)chunks.size() : 0, S.kp, S.acap, (int64_t)b_total, S.ranges,
+                           (int64_t)S.empty_m.size(), S.max_nchunk};
+    for (int i = 0; i < 10; i++) sizes[i] = n[i];
+    if (moff) std::copy(mo.begin(), mo.end(), moff);
+    for (size_t i = 0; ent && i < en.size(); i++) {
+        ent[3 * i] = en[i].x;
+        ent[3 * i + 1] = en[i].y;
+        ent[3 * i + 2] = en[i].z;
+    }
+    if (eoff) std::copy(eo.begin(), eo.end(), eoff);
+    if (ebins) std::copy(eb.begin(), eb.end(), ebins);
+    if (!at) return POLY_OK;
+    for (size_t g = 0; at_groups && g < S.groups.size(); g++) {
+        const AtGroup& G = S.groups[g];
+        const int32_t v[6] = {G.chunk_off, G.nchunk, G.hsplit, G.b_off, G.kmask[0], G.kmask[1]};
+        std::copy(v, v + 6, at_groups + 6 * g);
+    }
+    if (at_chunks) std::copy(chunks.begin(), chunks.end(), at_chunks);
+    if (at_pos) std::copy(pos.begin(), pos.end(), at_pos);
     return POLY_OK;
 }
 

@@ -93,6 +93,9 @@ void ps_set_last_error(const std::string& msg);
 void enumerate_bins(int nshell, const std::vector<double>& edges, int order, bool all_sorted, std::vector<int32_t>& out);
 void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines);
 void build_cc_tiles(PsPlan* p, CcTiles& t, int first_shift = 0);
+// the adjoint's entry tables (adjoint.cu); host only
+void ps_adj_entries(const PsPlan* p, std::vector<int>& moff, std::vector<short4>& ent, std::vector<int>& eoff,
+                    std::vector<int>& ebins);
 // host part of plan creation (checks, bins, shell line tables, contraction tiles); no device call
 poly_status ps_plan_host_tables(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
                                poly_precision prec, unsigned flags, int ell, std::vector<short>& lines);

@@ -254,3 +254,97 @@ def test_tc_tables_refuse_what_plan_creation_refuses(lib, kwargs, status):
     kw = dict(N=64, order=3, sms=152) | kwargs
     rc, _ = tc_tables(lib, kw["N"], kw["order"], fieldgen.unit_edges(6), kw["sms"])
     assert rc == status
+
+
+# ------------------------------------------------------------------ adjoint tables
+
+def adj_tables(lib, N, order, edges, prec, sms=152):
+    fn = lib.poly_diag_adj_tables
+    P = ctypes.c_void_p
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int] + [P] * 8
+    fn.restype = ctypes.c_int
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    ns = e.size - 1
+    sizes = np.zeros(10, dtype=np.int64)
+    args = (N, order, e.ctypes.data, ns, 0, ps.PRECISIONS[prec], sms)
+    assert fn(*args, sizes.ctypes.data, *([None] * 7)) == 0
+    nent, neb, ng, nch = (int(v) for v in sizes[:4])
+    t = dict(moff=np.zeros(ns + 1, np.int32), ent=np.zeros((nent, 3), np.int16), eoff=np.zeros(nent + 1, np.int32),
+             ebins=np.zeros(neb, np.int32), groups=np.zeros((ng, 6), np.int32), chunks=np.zeros(nch, np.int32),
+             pos=np.zeros(nent if ng else 0, np.int32))
+    ptrs = [t[k].ctypes.data for k in ("moff", "ent", "eoff", "ebins", "groups", "chunks", "pos")]
+    assert fn(*args, sizes.ctypes.data, *ptrs) == 0
+    t["kp"], t["acap"], t["b_total"] = int(sizes[4]), int(sizes[5]), int(sizes[6])
+    return t
+
+
+def check_entries(t, bins, nshell):
+    """Every (bin, position of m) pair is listed exactly once, under the entry (m, other shells sorted)."""
+    order = bins.shape[1]
+    moff, ent, eoff, ebins = t["moff"], t["ent"], t["eoff"], t["ebins"]
+    assert moff[0] == 0 and moff[-1] == len(ent) and np.all(np.diff(moff) >= 0)
+    assert eoff[0] == 0 and eoff[-1] == len(ebins) and np.all(np.diff(eoff) >= 1)
+    got = {}
+    for m in range(nshell):
+        for e in range(moff[m], moff[m + 1]):
+            key = (m,) + tuple(int(v) for v in ent[e][:order - 1])
+            assert key not in got and np.all(ent[e][order - 1:] == -1)
+            got[key] = sorted(ebins[eoff[e]:eoff[e + 1]].tolist())
+    want = {}
+    for b, legs in enumerate(bins.astype(int) - 1):
+        for tpos in range(order):
+            rest = sorted(np.delete(legs, tpos).tolist())
+            want.setdefault((int(legs[tpos]),) + tuple(rest), []).append(b)
+    assert got == {k: sorted(v) for k, v in want.items()}
+
+
+def check_at_tables(t, nshell):
+    """Tensor-core adjoint: each group's chunks run over its m's in order, one chunk per (m, j block) that
+    holds an entry; every entry's weight sits at its own place of its group's B (K-major, 8 x 8 core
+    matrices), inside a K block that the group's mask marks."""
+    ent, moff, groups, chunks, pos, kp = t["ent"], t["moff"], t["groups"], t["chunks"], t["pos"], t["kp"]
+    assert kp % 32 == 0 and nshell <= kp and t["acap"] % 32 == 0
+    where = {}
+    next_off, ms_seen = 0, []
+    for g, (coff, nch, hsplit, boff, km0, km1) in enumerate(groups):
+        assert coff == (groups[g - 1, 0] + groups[g - 1, 1] if g else 0) and 0 < nch <= t["acap"] // 16
+        assert boff == next_off
+        next_off += nch * 16 * kp * 2
+        c = chunks[coff:coff + nch]
+        jb, m, last = c & 0xFF, (c >> 8) & 0xFF, (c >> 16) & 1
+        assert np.all(np.diff(m) >= 0)
+        assert np.array_equal(last.astype(bool), np.append(m[1:] != m[:-1], True))
+        assert 0 <= hsplit <= nch and (hsplit in (0, nch) or m[hsplit - 1] != m[hsplit])
+        ms_seen += sorted(set(m.tolist()))
+        for q in range(nch):
+            assert (int(m[q]), int(jb[q])) not in where
+            where[(int(m[q]), int(jb[q]))] = (g, q)
+    assert next_off == t["b_total"] and ms_seen == sorted(set(ms_seen))
+    m_of = np.repeat(np.arange(nshell), np.diff(moff))
+    need = {(int(m_of[e]), int(ent[e, 1]) // 16) for e in range(len(ent))}
+    assert set(where) == need  # a chunk for every (m, j block) with an entry, and no other
+    assert np.unique(pos).size == pos.size and np.all(pos % 2 == 0)
+    for e in range(len(ent)):
+        k, j = int(ent[e, 0]), int(ent[e, 1])
+        assert k <= j
+        g, q = where[(int(m_of[e]), j // 16)]
+        off = int(pos[e]) - int(groups[g, 3])
+        n = (off // (kp * 16)) * 8 + (off % 128) // 16
+        kk = ((off % (kp * 16)) // 128) * 8 + (off % 16) // 2
+        assert (n, kk) == (q * 16 + j % 16, k)
+        assert (int(groups[g, 4 + n // 256]) >> (k // 16)) & 1
+
+
+@pytest.mark.parametrize("N,order,nshell,width,prec", [
+    (256, 3, 64, 1.0, "split_bf16"), (96, 3, 30, 1.0, "split_bf16"), (48, 3, 14, 1.0, "split_bf16"),
+    (128, 3, 40, 1.0, "fp32"), (64, 2, 16, 1.0, "fp64"), (256, 4, 32, 1.5, "fp32"), (64, 4, 10, 1.5, "split_bf16"),
+])
+def test_adjoint_tables(lib, N, order, nshell, width, prec):
+    e = fieldgen.unit_edges(nshell, width)
+    t = adj_tables(lib, N, order, e, prec)
+    check_entries(t, oracle.enumerate_bins(e, order), nshell)
+    if order == 3 and prec == "split_bf16":
+        assert len(t["groups"]) > 0
+        check_at_tables(t, nshell)
+    else:
+        assert len(t["groups"]) == 0
