@@ -71,6 +71,16 @@ int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* s
  *             line_off[s + 1] - 1, and slot nshell holds the union of all shells.
  * Returns a poly_status.
  */
+/*
+ * The cells and weights the exact counts are summed over (count_b = N^-3 sum_x
+ * prod iota, App. A): the counting fields are invariant under the cube's 48
+ * symmetries, so the sum runs over 0 <= x <= y <= z <= N/2 with each cell
+ * weighted by the size of its orbit.  N even.  ncell (required) receives the
+ * number of cells; cells (int32, linear index (x N + y) N + z) and weights
+ * (double) are NULL or host buffers of that length.  Returns a poly_status.
+ */
+int poly_diag_count_wedge(int N, int64_t* ncell, int32_t* cells, double* weights);
+
 int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
                           int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids, int16_t* rowf,
                           int16_t* colf, int64_t* slot, int16_t* lines, int32_t* line_off);

@@ -256,6 +256,23 @@ static int choose_splits(int ntiles, int64_t nchunks, int sms) {
 //   0 <= x <= y <= z <= floor(N/2), weight = orbit size under coordinate
 //   permutations and sign flips (x_c -> N - x_c); sum_wedge w prod iota = sum_x prod iota.
 // ---------------------------------------------------------------------------
+// The counting fields are invariant under the 48 symmetries of the cube (axis
+// permutations, x -> -x mod N per axis: the shells are spheres), so the count sums
+// run over the wedge 0 <= x <= y <= z <= N/2 with each cell weighted by its orbit
+// size.  Even N.
+static void count_wedge(int N, std::vector<int32_t>& widx, std::vector<double>& wgt) {
+    const int h = N / 2;
+    for (int x = 0; x <= h; x++)
+        for (int y = x; y <= h; y++)
+            for (int z = y; z <= h; z++) {
+                int perms = (x == y && y == z) ? 1 : (x == y || y == z) ? 3 : 6;
+                double w = perms;
+                for (int v : {x, y, z}) w *= (v == 0 || 2 * v == N) ? 1.0 : 2.0;
+                widx.push_back((int32_t)(((int64_t)x * N + y) * N + z));
+                wgt.push_back(w);
+            }
+}
+
 static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
     CountKey key{p->N, p->order, p->flags & POLY_BINS_ALL_SORTED, p->edges};
     {
@@ -269,15 +286,7 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
     const int N = p->N, h = N / 2;
     std::vector<int32_t> widx;
     std::vector<double> wgt;
-    for (int x = 0; x <= h; x++)
-        for (int y = x; y <= h; y++)
-            for (int z = y; z <= h; z++) {
-                int perms = (x == y && y == z) ? 1 : (x == y || y == z) ? 3 : 6;
-                double w = perms;
-                for (int v : {x, y, z}) w *= (v == 0 || 2 * v == N) ? 1.0 : 2.0;
-                widx.push_back((int32_t)(((int64_t)x * N + y) * N + z));
-                wgt.push_back(w);
-            }
+    count_wedge(N, widx, wgt);
     const int64_t nw = (int64_t)widx.size();
     // device buffers (freed at the end of this function)
     std::vector<void*> tmp;
@@ -764,6 +773,17 @@ int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* s
     }
     leave(p, prev);
     return s;
+}
+
+int poly_diag_count_wedge(int N, int64_t* ncell, int32_t* cells, double* weights) {
+    if (!ncell || N < 2 || (N & 1)) return set_error(POLY_ERR_ARG, "N must be even");
+    std::vector<int32_t> widx;
+    std::vector<double> wgt;
+    count_wedge(N, widx, wgt);
+    *ncell = (int64_t)widx.size();
+    if (cells) std::memcpy(cells, widx.data(), widx.size() * sizeof(int32_t));
+    if (weights) std::memcpy(weights, wgt.data(), wgt.size() * sizeof(double));
+    return POLY_OK;
 }
 
 int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,

@@ -348,3 +348,43 @@ def test_adjoint_tables(lib, N, order, nshell, width, prec):
         check_at_tables(t, nshell)
     else:
         assert len(t["groups"]) == 0
+
+
+# ------------------------------------------------------------------ the count wedge
+
+def count_wedge(lib, N):
+    fn = lib.poly_diag_count_wedge
+    fn.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    n = ctypes.c_int64(0)
+    assert fn(N, ctypes.byref(n), None, None) == 0
+    cells, w = np.zeros(n.value, np.int32), np.zeros(n.value, np.float64)
+    assert fn(N, ctypes.byref(n), cells.ctypes.data, w.ctypes.data) == 0
+    return cells, w
+
+
+@pytest.mark.parametrize("N", [6, 16, 24, 32])
+def test_count_wedge_weights_are_orbit_sizes(lib, N):
+    """Each cell of the wedge stands for its orbit under the cube's 48 symmetries (per-axis x -> -x mod N,
+    axis permutations): the orbits partition the grid and the weights are their sizes."""
+    cells, w = count_wedge(lib, N)
+    g = np.indices((N, N, N)).reshape(3, -1)
+    rep = np.sort(np.minimum(g, N - g), axis=0)  # fold each axis, then order the axes
+    lin = (rep[0] * N + rep[1]) * N + rep[2]
+    u, cnt = np.unique(lin, return_counts=True)
+    order = np.argsort(cells)
+    assert np.array_equal(cells[order], u) and np.array_equal(w[order], cnt.astype(np.float64))
+    assert w.sum() == N ** 3
+
+
+def test_count_wedge_reproduces_the_full_count_sum(lib):
+    """The oracle's counting fields (16^3, 5 shells) summed over the wedge with its weights give the
+    same products as the sum over every cell, for every bin (the symmetry the wedge relies on)."""
+    N, e = 16, fieldgen.unit_edges(5)
+    iota, _ = oracle.shell_fields(N, e, np.arange(5))
+    cells, w = count_wedge(lib, N)
+    flat = iota.reshape(5, -1)
+    for b in oracle.enumerate_bins(e, 3, oracle.RULE_ALL_SORTED) - 1:
+        full = np.prod(flat[b], axis=0).sum()
+        wedge = (np.prod(flat[b][:, cells], axis=0) * w).sum()
+        assert abs(full - wedge) <= 1e-9 * max(1.0, abs(full))
