@@ -379,6 +379,7 @@ def run_ours(args):
         "metric": METRIC, "value": h["value"], "unit": "configs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3" if head_prec == "split_bf16" else "f32", "data": "synthetic",
+        "fields_per_s": 1e3 * world / h["ms_per_step"],
         "config": {"workload": WORKLOAD, "N": N, "N_max": NSHELL, "order": ORDER, "nbins": h["nbins"], "L": L,
                    "precision": head_prec, "l2": "256 MiB buffer written between timed steps (L2 flushed)",
                    "parallelism": f"replica per GPU x{world}" if world > 1 else "1 GPU",
