@@ -74,7 +74,10 @@ typedef enum {
  * of three), `nshell` shells with `nshell + 1`
  * strictly increasing edges (host array, units of k_F, edges[0] >= 0).
  * K = the largest integer with K^2 < edges[nshell]^2 must satisfy 2K+1 <= N,
- * and n*K < N unless POLY_ALLOW_ALIAS.  Plan creation enumerates the bins,
+ * and n*K < N unless POLY_ALLOW_ALIAS.  The sorted shell tuples the bins are
+ * drawn from, C(nshell + n - 1, n) of them, may number at most 2^26
+ * (POLY_ERR_UNSUPPORTED above; e.g. n = 5 with 120 shells).  Argument checks
+ * and the host tables come before any device call.  Plan creation enumerates the bins,
  * builds the shell tables and tiles, allocates the workspace (nshell * N^3
  * fields of the plan's precision plus small buffers) on the current CUDA
  * device and computes the exact counts (FP64 counting fields on the

@@ -421,9 +421,9 @@ poly_status ps_at_prepare(PsPlan* p, const std::vector<int>& ent_m, const std::v
     return POLY_OK;
 }
 
-extern "C" int poly_diag_adj_tables(int N, int order, const double* edges, int nshell, unsigned flags, int prec,
-                                    int sms, int64_t* sizes, int32_t* moff, int16_t* ent, int32_t* eoff,
-                                    int32_t* ebins, int32_t* at_groups, int32_t* at_chunks, int32_t* at_pos) {
+static int diag_adj_tables(int N, int order, const double* edges, int nshell, unsigned flags, int prec, int sms,
+                           int64_t* sizes, int32_t* moff, int16_t* ent, int32_t* eoff, int32_t* ebins,
+                           int32_t* at_groups, int32_t* at_chunks, int32_t* at_pos) {
     if (!sizes || sms < 1) return POLY_ERR_ARG;
     PsPlan hp;  // host tables only: no device call, no device memory
     std::vector<short> lines;
@@ -466,6 +466,17 @@ extern "C" int poly_diag_adj_tables(int N, int order, const double* edges, int n
     if (at_chunks) std::copy(chunks.begin(), chunks.end(), at_chunks);
     if (at_pos) std::copy(pos.begin(), pos.end(), at_pos);
     return POLY_OK;
+}
+
+extern "C" int poly_diag_adj_tables(int N, int order, const double* edges, int nshell, unsigned flags, int prec,
+                                    int sms, int64_t* sizes, int32_t* moff, int16_t* ent, int32_t* eoff,
+                                    int32_t* ebins, int32_t* at_groups, int32_t* at_chunks, int32_t* at_pos) {
+    try {
+        return diag_adj_tables(N, order, edges, nshell, flags, prec, sms, sizes, moff, ent, eoff, ebins, at_groups,
+                               at_chunks, at_pos);
+    } catch (const std::bad_alloc&) {
+        return POLY_ERR_ALLOC;
+    }
 }
 
 // G[m][x] for all m from the plan's fields and the entry weights w (FP32, entry order).

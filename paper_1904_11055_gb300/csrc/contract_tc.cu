@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <new>
 #include <set>
 #include <string>
 #include <vector>
@@ -913,9 +914,9 @@ poly_status ps_tc_prepare(PsPlan* p) {
     return POLY_OK;
 }
 
-extern "C" int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms,
-                                   int max_mt, int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups,
-                                   int32_t* mtiles, int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap) {
+static int diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms, int max_mt,
+                          int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups, int32_t* mtiles,
+                          int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap) {
     if (!sizes || sms < 1 || max_mt < 1 || cta_mult < 1) return POLY_ERR_ARG;
     PsPlan hp;  // host tables only: no device call, no device memory
     std::vector<short> lines;
@@ -963,6 +964,17 @@ extern "C" int poly_diag_tc_tables(int N, int order, const double* edges, int ns
         binmap[3 * i + 2] = h.binmap[i].z;
     }
     return POLY_OK;
+}
+
+extern "C" int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms,
+                                   int max_mt, int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups,
+                                   int32_t* mtiles, int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap) {
+    try {
+        return diag_tc_tables(N, order, edges, nshell, flags, sms, max_mt, cta_mult, sizes, ctas, groups, mtiles,
+                              runs, rowf, colf, binmap);
+    } catch (const std::bad_alloc&) {
+        return POLY_ERR_ALLOC;
+    }
 }
 
 poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {

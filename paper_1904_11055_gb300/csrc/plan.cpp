@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -398,6 +399,8 @@ static void free_plan(PsPlan* p) {
     delete p;
 }
 
+constexpr int64_t kMaxSortedTuples = int64_t(1) << 26;  // host tables of about a GB at order 6
+
 // The host part of plan creation: argument checks, the bins, the shell line tables
 // (slot nshell holds the union of all shells, used by the adjoint) and the
 // CUDA-core contraction tiles over the plain fields.  Touches no device.
@@ -439,6 +442,11 @@ poly_status ps_plan_host_tables(PsPlan* p, int N, double L, int order, int nshel
     if ((long long)order * K >= N && !(flags & POLY_ALLOW_ALIAS))
         return set_error(POLY_ERR_ALIAS, "n * K >= N: polygon closures would wrap around the grid");
 
+    // the enumeration walks every sorted tuple: C(nshell + order - 1, order) of them
+    double tuples = 1.0;
+    for (int i = 0; i < order; i++) tuples = tuples * (nshell + i) / (i + 1);
+    if (tuples > (double)kMaxSortedTuples)
+        return set_error(POLY_ERR_UNSUPPORTED, "too many bins: more than 2^26 sorted shell tuples");
     enumerate_bins(nshell, p->edges, order, (flags & POLY_BINS_ALL_SORTED) != 0, p->bins);
     p->nbins = (int64_t)p->bins.size() / order;
 
@@ -749,19 +757,18 @@ poly_status poly_trispectrum_disconnected(poly_plan p, const void* delta_x, doub
     return s;
 }
 
-int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* stream) {
+static int poly_diag_fields_impl(void* plan, const void* delta_x, void* fields_host, void* stream) {
     PsPlan* p = (PsPlan*)plan;
     if (!p || !delta_x || !fields_host) return set_error(POLY_ERR_ARG, "NULL argument");
+    const size_t n3 = (size_t)p->N * p->N * p->N, es = p->is_double ? 8 : 4, nf = (size_t)p->nfield;
+    std::vector<unsigned char> tiled(nf * n3 * es);  // before enter(): a failed allocation leaves the device as it was
     int prev;
     PS_TRY(enter(p, &prev));
     cudaStream_t st = (cudaStream_t)stream;
     poly_status s = ps_fields(p, delta_x, st);
-    const size_t n3 = (size_t)p->N * p->N * p->N, es = p->is_double ? 8 : 4, nf = (size_t)p->nfield;
-    std::vector<unsigned char> tiled;
     cudaError_t e;
     if (!s && (e = cudaStreamSynchronize(st))) s = cuda_error(e, "stream synchronise");
     if (!s) {
-        tiled.resize(nf * n3 * es);
         if ((e = cudaMemcpy(tiled.data(), p->d_fields, tiled.size(), cudaMemcpyDeviceToHost)))
             s = cuda_error(e, "device to host copy");
     }
@@ -775,7 +782,15 @@ int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* s
     return s;
 }
 
-int poly_diag_count_wedge(int N, int64_t* ncell, int32_t* cells, double* weights) {
+int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* stream) {
+    try {
+        return poly_diag_fields_impl(plan, delta_x, fields_host, stream);
+    } catch (const std::bad_alloc&) {
+        return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    }
+}
+
+static int poly_diag_count_wedge_impl(int N, int64_t* ncell, int32_t* cells, double* weights) {
     if (!ncell || N < 2 || (N & 1)) return set_error(POLY_ERR_ARG, "N must be even");
     std::vector<int32_t> widx;
     std::vector<double> wgt;
@@ -786,9 +801,18 @@ int poly_diag_count_wedge(int N, int64_t* ncell, int32_t* cells, double* weights
     return POLY_OK;
 }
 
-int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
-                          int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids, int16_t* rowf,
-                          int16_t* colf, int64_t* slot, int16_t* lines, int32_t* line_off) {
+int poly_diag_count_wedge(int N, int64_t* ncell, int32_t* cells, double* weights) {
+    try {
+        return poly_diag_count_wedge_impl(N, ncell, cells, weights);
+    } catch (const std::bad_alloc&) {
+        return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    }
+}
+
+static int poly_diag_host_tables_impl(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
+                                      int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids,
+                                      int16_t* rowf, int16_t* colf, int64_t* slot, int16_t* lines,
+                                      int32_t* line_off) {
     if (!sizes) return set_error(POLY_ERR_ARG, "NULL sizes");
     PsPlan h;  // host tables only: no device call, no device memory
     std::vector<short> ln;
@@ -810,6 +834,17 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
     if (lines) std::memcpy(lines, ln.data(), ln.size() * sizeof(short));
     if (line_off) std::memcpy(line_off, h.line_off.data(), h.line_off.size() * sizeof(int32_t));
     return POLY_OK;
+}
+
+int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
+                          int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids, int16_t* rowf,
+                          int16_t* colf, int64_t* slot, int16_t* lines, int32_t* line_off) {
+    try {
+        return poly_diag_host_tables_impl(N, order, edges, nshell, flags, ell, sizes, bins, tiles, field_ids, rowf, colf,
+                                          slot, lines, line_off);
+    } catch (const std::bad_alloc&) {
+        return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    }
 }
 
 poly_status poly_estimate_host(poly_plan p, const void* delta_x_host, double* out_host, void* stream) {

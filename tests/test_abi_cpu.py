@@ -55,6 +55,8 @@ def test_status_strings(lib):
     (dict(N=64, edges=np.arange(23) + 0.5), 2),                        # 3 * 22 >= 64: aliasing
     (dict(N=64, L=-1.0), 1),                                           # bad box size
     (dict(N=64, prec=2), 6),                                           # TF32x3 not implemented
+    (dict(N=256, order=5, edges=np.arange(121) + 0.5, flags=2), 6),    # C(124, 5) > 2^26 sorted tuples
+    (dict(N=256, order=6, edges=np.arange(61) + 0.5, flags=2), 6),     # C(65, 6) > 2^26 sorted tuples
 ])
 def test_argument_validation_before_device(lib, kwargs, status):
     args = dict(N=64, L=1000.0, order=3, edges=np.arange(17) + 0.5, prec=0, flags=0)

@@ -142,6 +142,7 @@ def test_line_tables_cover_each_shell_exactly(lib, N, layout):
     (dict(N=16, order=3), STATUS["POLY_ERR_ALIAS"]),
     (dict(N=64, order=3, ell=3), STATUS["POLY_ERR_ARG"]),
     (dict(N=64, order=3, edges=[0.5, 2.5, 1.5]), STATUS["POLY_ERR_ARG"]),
+    (dict(N=256, order=5, edges=fieldgen.unit_edges(120), flags=ps.POLY_ALLOW_ALIAS), STATUS["POLY_ERR_UNSUPPORTED"]),
 ])
 def test_host_checks_match_plan_creation(lib, kwargs, status):
     kw = dict(edges=fieldgen.unit_edges(6), flags=0, ell=0) | kwargs
