@@ -128,3 +128,31 @@ def test_binding_wrappers_marshal_without_a_device(lib):
         with pytest.raises(ps.PolyError) as ei:
             call()
         assert ei.value.status == 1
+
+
+def test_autotune_cache_tunes_once_per_signature(tmp_path):
+    """autotune() times the shapes once per plan signature and restores the recorded choice afterwards
+    (host logic only: a stand-in plan records the calls)."""
+    class FakePlan:
+        def __init__(self, sig):
+            self.sig, self.calls = sig, []
+
+        def signature(self):
+            return self.sig
+
+        def tune(self, delta):
+            self.calls.append("tune")
+            return 0x24, 7.5
+
+        def set_config(self, cfg):
+            self.calls.append(("set", cfg))
+
+    cache = str(tmp_path / "tune.json")
+    a = FakePlan("256/64/3/split")
+    assert ps.autotune(a, None, cache) == 0x24 and a.calls == ["tune"]
+    b = FakePlan("256/64/3/split")
+    assert ps.autotune(b, None, cache) == 0x24 and b.calls == [("set", 0x24)]
+    c = FakePlan("128/40/3/split")
+    assert ps.autotune(c, None, cache) == 0x24 and c.calls == ["tune"]
+    d = FakePlan("256/64/3/split")
+    assert ps.autotune(d, None, None) == 0x24 and d.calls == ["tune"]  # no cache file: always tunes
