@@ -1,9 +1,12 @@
 /*
  * polyspec_diag.h -- diagnostic entry points of the polyspectrum library.
  *
- * These exist to check, on the GPU, the hardware layouts the tensor-core
- * contraction relies on; they are not part of the estimator.  The paper has no
- * counterpart: they test this implementation, not the method.
+ * These exist to check this implementation, not the method, and are not part of
+ * the estimator (the paper has no counterpart): on the GPU, the hardware
+ * layouts the tensor-core contraction relies on, the limit of its device waits
+ * and the shell fields it computes; with no device, the host tables that plan
+ * creation builds (bins, shell lines, contraction tiles, adjoint entries, the
+ * cells the counts are summed over).
  */
 #ifndef POLYSPEC_DIAG_H
 #define POLYSPEC_DIAG_H

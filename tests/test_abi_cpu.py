@@ -156,3 +156,59 @@ def test_autotune_cache_tunes_once_per_signature(tmp_path):
     assert ps.autotune(c, None, cache) == 0x24 and c.calls == ["tune"]
     d = FakePlan("256/64/3/split")
     assert ps.autotune(d, None, None) == 0x24 and d.calls == ["tune"]  # no cache file: always tunes
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "polyspec.h"
+#include "polyspec_diag.h"
+
+int main(void) {
+    /* argument errors come back before any device call */
+    poly_plan plan = (poly_plan)1;
+    const double edges[7] = {0.5, 1.5, 2.5, 3.5, 4.5, 5.5, 6.5};
+    if (poly_plan_create(&plan, 32, 1000.0, 3, 6, NULL, POLY_FP32, 0) != POLY_ERR_ARG || plan != NULL) return 2;
+    printf("status %s\n", poly_status_string(POLY_ERR_ALIAS));
+    /* host tables through the diagnostic header */
+    int64_t sizes[7];
+    if (poly_diag_host_tables(32, 3, edges, 6, 0, 0, sizes, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL)) return 3;
+    int32_t* bins = malloc(sizeof(int32_t) * 3 * (size_t)sizes[0]);
+    if (poly_diag_host_tables(32, 3, edges, 6, 0, 0, sizes, bins, NULL, NULL, NULL, NULL, NULL, NULL, NULL)) return 4;
+    printf("nbins %lld\n", (long long)sizes[0]);
+    for (int64_t b = 0; b < sizes[0]; b++) printf("bin %d %d %d\n", bins[3 * b], bins[3 * b + 1], bins[3 * b + 2]);
+    free(bins);
+    int64_t ncell = 0;
+    if (poly_diag_count_wedge(16, &ncell, NULL, NULL)) return 5;
+    double* w = malloc(sizeof(double) * (size_t)ncell);
+    if (poly_diag_count_wedge(16, &ncell, NULL, w)) return 6;
+    double sum = 0.0;
+    for (int64_t i = 0; i < ncell; i++) sum += w[i];
+    printf("wedge %lld %.0f\n", (long long)ncell, sum);
+    free(w);
+    return 0;
+}
+"""
+
+
+def test_plain_c_client_links_and_calls_the_host_entry_points(lib, tmp_path):
+    """The boundary is a C ABI: a C99 program compiles against both headers (-Wall -Werror), links
+    libpolyspec.so and calls the entry points that need no device."""
+    import shutil
+    import subprocess
+
+    import oracle
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src, exe = tmp_path / "client.c", tmp_path / "client"
+    src.write_text(C_CLIENT)
+    libdir = os.path.dirname(ps.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe), "-L", libdir, "-lpolyspec", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    assert out[0] == "status " + ps.poly_status_string(2)
+    bins = np.array([[int(v) for v in line.split()[1:]] for line in out if line.startswith("bin ")])
+    assert out[1] == f"nbins {len(bins)}"
+    assert np.array_equal(bins, oracle.enumerate_bins(np.arange(7) + 0.5, 3))
+    assert out[-1].split()[2] == str(16 ** 3)
