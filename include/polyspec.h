@@ -113,6 +113,17 @@ poly_status poly_plan_bins(poly_plan plan, int32_t* idx);
 poly_status poly_plan_counts(poly_plan plan, int64_t* counts);
 
 /*
+ * Which bins may hold closures that wrap around the grid (the aliasing the
+ * paper avoids by asking N > n N_max, Sec. 4.3): wraps (host, nbins uint8)
+ * receives 1 where sum_t K_{k_t} >= N, K_k being the largest component |q_c|
+ * of a mode of shell k, else 0.  A bin marked 0 counts and sums exact closures
+ * q_1 + ... + q_n = 0 only; a bin marked 1 may also hold closures that sum to a
+ * nonzero multiple of N (the periodic estimator the FFT computes).  Without
+ * POLY_ALLOW_ALIAS every bin is 0.  Host only.
+ */
+poly_status poly_plan_bin_wraps(poly_plan plan, uint8_t* wraps);
+
+/*
  * Estimate B_b for one field.  delta_x: device, N^3 real (float for POLY_FP32 /
  * POLY_SPLIT_BF16, double for POLY_FP64).  out: device, nbins double, B_b.
  * scale_or_null: device, nbins double or NULL; if given, receives

@@ -84,6 +84,15 @@ int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* s
  */
 int poly_diag_count_wedge(int N, int64_t* ncell, int32_t* cells, double* weights);
 
+/*
+ * poly_plan_bin_wraps computed on the host alone for the plan that N, order,
+ * edges (nshell + 1), nshell and flags would give: nbins (required) receives
+ * the bin count, wraps (NULL or host, nbins uint8) the flags.  Returns a
+ * poly_status.
+ */
+int poly_diag_bin_wraps(int N, int order, const double* edges, int nshell, unsigned flags, int64_t* nbins,
+                        uint8_t* wraps);
+
 int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
                           int64_t* sizes, int32_t* bins, int32_t* tiles, int32_t* field_ids, int16_t* rowf,
                           int16_t* colf, int64_t* slot, int16_t* lines, int32_t* line_off);

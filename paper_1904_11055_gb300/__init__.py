@@ -32,7 +32,7 @@ ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_pl
                "poly_estimate_host", "poly_backward", "poly_estimate_batched", "poly_plan_sync", "poly_plan_destroy",
                "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
                "poly_plan_stats", "poly_estimate_noalloc", "poly_plan_tune", "poly_plan_set_config",
-               "poly_trispectrum_disconnected", "poly_plan_create_multipole")
+               "poly_trispectrum_disconnected", "poly_plan_create_multipole", "poly_plan_bin_wraps")
 
 
 class poly_stats(ctypes.Structure):
@@ -62,6 +62,7 @@ def load_library():
     L.poly_plan_nbins.argtypes = [P, ctypes.POINTER(i64)]
     L.poly_plan_bins.argtypes = [P, P]
     L.poly_plan_counts.argtypes = [P, P]
+    L.poly_plan_bin_wraps.argtypes = [P, P]
     L.poly_estimate.argtypes = [P, P, P, P, P]
     L.poly_estimate_host.argtypes = [P, P, P, P]
     L.poly_backward.argtypes = [P, P, P, P, P]
@@ -130,6 +131,13 @@ def poly_plan_counts(plan: int) -> np.ndarray:
     out = np.empty(poly_plan_nbins(plan), dtype=np.int64)
     _check(load_library().poly_plan_counts(plan, out.ctypes.data_as(ctypes.c_void_p)), "poly_plan_counts")
     return out
+
+
+def poly_plan_bin_wraps(plan: int) -> np.ndarray:
+    """Per bin, True where closures that wrap around the grid may add to the count (see the header)."""
+    out = np.empty(poly_plan_nbins(plan), dtype=np.uint8)
+    _check(load_library().poly_plan_bin_wraps(plan, out.ctypes.data_as(ctypes.c_void_p)), "poly_plan_bin_wraps")
+    return out.astype(bool)
 
 
 def poly_estimate(plan: int, delta_ptr: int, out_ptr: int, scale_ptr: int | None, stream: int | None) -> None:
@@ -287,6 +295,10 @@ class Plan:
 
     def set_config(self, config: int) -> None:
         poly_plan_set_config(self.handle, config)
+
+    def bin_wraps(self) -> np.ndarray:
+        """Per bin, True where closures that wrap around the grid may add to it (POLY_ALLOW_ALIAS plans)."""
+        return poly_plan_bin_wraps(self.handle)
 
     def signature(self) -> str:
         """Key for a tuning cache: everything the contraction shape depends on, plus the GPU model."""

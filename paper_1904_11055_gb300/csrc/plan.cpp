@@ -274,6 +274,19 @@ static void count_wedge(int N, std::vector<int32_t>& widx, std::vector<double>& 
             }
 }
 
+// Bins whose closures may wrap around the grid: a closed polygon q_1 + ... + q_n = 0
+// (mod N) can differ from an exact closure only where some component sum reaches
+// +-N, which needs sum_t K_t >= N with K_t the largest component of a mode of shell
+// b_t (the largest kz of the shell's lines: the shells are symmetric under axis
+// permutations).  Bins below that bound count exact closures only.
+static void bin_wraps(const PsPlan* p, uint8_t* out) {
+    for (int64_t b = 0; b < p->nbins; b++) {
+        int64_t k = 0;
+        for (int t = 0; t < p->order; t++) k += p->shell_kz[p->bins[b * p->order + t] - 1];
+        out[b] = k >= p->N ? 1 : 0;
+    }
+}
+
 static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
     CountKey key{p->N, p->order, p->flags & POLY_BINS_ALL_SORTED, p->edges};
     {
@@ -731,6 +744,12 @@ poly_status poly_plan_counts(poly_plan p, int64_t* counts) {
     return POLY_OK;
 }
 
+poly_status poly_plan_bin_wraps(poly_plan p, uint8_t* wraps) {
+    if (!p || !wraps) return set_error(POLY_ERR_ARG, "NULL argument");
+    bin_wraps(p, wraps);
+    return POLY_OK;
+}
+
 poly_status poly_estimate(poly_plan p, const void* delta_x, double* out, double* scale_or_null, void* stream) {
     if (!p || !delta_x || !out) return set_error(POLY_ERR_ARG, "NULL argument");
     if ((const void*)out == delta_x || (const void*)scale_or_null == delta_x || out == scale_or_null)
@@ -834,6 +853,26 @@ static int poly_diag_host_tables_impl(int N, int order, const double* edges, int
     if (lines) std::memcpy(lines, ln.data(), ln.size() * sizeof(short));
     if (line_off) std::memcpy(line_off, h.line_off.data(), h.line_off.size() * sizeof(int32_t));
     return POLY_OK;
+}
+
+static int poly_diag_bin_wraps_impl(int N, int order, const double* edges, int nshell, unsigned flags,
+                                    int64_t* nbins, uint8_t* wraps) {
+    if (!nbins) return set_error(POLY_ERR_ARG, "NULL nbins");
+    PsPlan h;  // host tables only: no device call, no device memory
+    std::vector<short> ln;
+    PS_TRY(ps_plan_host_tables(&h, N, 1.0, order, nshell, edges, POLY_FP64, flags, 0, ln));
+    *nbins = h.nbins;
+    if (wraps) bin_wraps(&h, wraps);
+    return POLY_OK;
+}
+
+int poly_diag_bin_wraps(int N, int order, const double* edges, int nshell, unsigned flags, int64_t* nbins,
+                        uint8_t* wraps) {
+    try {
+        return poly_diag_bin_wraps_impl(N, order, edges, nshell, flags, nbins, wraps);
+    } catch (const std::bad_alloc&) {
+        return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    }
 }
 
 int poly_diag_host_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,

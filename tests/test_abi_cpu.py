@@ -123,11 +123,13 @@ def test_binding_wrappers_marshal_without_a_device(lib):
         lambda: ps.poly_estimate(None, None, None, None, None),
         lambda: ps.poly_backward(None, None, None, None, None),
         lambda: ps.poly_trispectrum_disconnected(None, None, None, None, None),
+        lambda: ps.poly_plan_bin_wraps(None),
     ]
     for call in calls:
         with pytest.raises(ps.PolyError) as ei:
             call()
         assert ei.value.status == 1
+    assert lib.poly_plan_bin_wraps(None, None) == 1
 
 
 def test_autotune_cache_tunes_once_per_signature(tmp_path):

@@ -389,3 +389,47 @@ def test_count_wedge_reproduces_the_full_count_sum(lib):
         full = np.prod(flat[b], axis=0).sum()
         wedge = (np.prod(flat[b][:, cells], axis=0) * w).sum()
         assert abs(full - wedge) <= 1e-9 * max(1.0, abs(full))
+
+
+# ------------------------------------------------------------------ bins whose closures may wrap around the grid
+
+def bin_wraps(lib, N, order, edges, flags=ps.POLY_ALLOW_ALIAS):
+    fn = lib.poly_diag_bin_wraps
+    P = ctypes.c_void_p
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint, P, P]
+    fn.restype = ctypes.c_int
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = ctypes.c_int64(0)
+    assert fn(N, order, e.ctypes.data, e.size - 1, flags, ctypes.byref(nb), None) == 0
+    out = np.zeros(nb.value, np.uint8)
+    assert fn(N, order, e.ctypes.data, e.size - 1, flags, ctypes.byref(nb), out.ctypes.data) == 0
+    return out.astype(bool)
+
+
+@pytest.mark.parametrize("N,order,nshell,big", [(16, 3, 6, 32), (16, 4, 4, 32), (24, 3, 9, 48)])
+def test_bin_wraps_cover_every_bin_whose_periodic_count_differs(lib, N, order, nshell, big):
+    """The oracle's counts on the N grid (closures mod N) against those on a grid too large to wrap (exact
+    closures): they differ only in flagged bins, and the flag is not vacuous (some flagged bin differs)."""
+    e = fieldgen.unit_edges(nshell)
+    bins = oracle.enumerate_bins(e, order)
+    wraps = bin_wraps(lib, N, order, e)
+    periodic, exact = oracle.counts_exact(N, e, order, bins), oracle.counts_exact(big, e, order, bins)
+    differ = periodic != exact
+    assert not np.any(differ & ~wraps)
+    assert np.any(differ & wraps)
+
+
+def test_bin_wraps_of_the_96cube_mocks(lib):
+    """The 96^3 realisations of the mock workload (32 unit shells, n = 3 = N / 32): only (32, 32, 32) may
+    wrap, and it does (its periodic count exceeds the exact one)."""
+    e = fieldgen.unit_edges(32)
+    bins = oracle.enumerate_bins(e, 3)
+    wraps = bin_wraps(lib, 96, 3, e)
+    assert [tuple(b) for b in bins[wraps]] == [(32, 32, 32)]
+    b = bins[wraps]
+    assert oracle.counts_exact(96, e, 3, b)[0] > oracle.counts_exact(128, e, 3, b)[0]
+
+
+def test_no_wraps_without_the_alias_flag(lib):
+    e = fieldgen.unit_edges(20)
+    assert not bin_wraps(lib, 64, 3, e, 0).any()
