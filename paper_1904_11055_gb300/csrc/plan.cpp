@@ -46,6 +46,19 @@ poly_status cuda_error(cudaError_t e, const char* where) {
         if (s_ != POLY_OK) return s_;         \
     } while (0)
 
+// Runs f, turning a C++ exception from host containers into a status: no
+// exception crosses the C ABI.
+template <typename F>
+static poly_status guarded(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    } catch (const std::exception& ex) {
+        return set_error(POLY_ERR_ARG, ex.what());
+    }
+}
+
 // ---- counts cache (per process) -----------------------------------------
 struct CountKey {
     int N, order;
@@ -771,7 +784,7 @@ poly_status poly_trispectrum_disconnected(poly_plan p, const void* delta_x, doub
         return set_error(POLY_ERR_ARG, "output aliases an input");
     int prev;
     PS_TRY(enter(p, &prev));
-    poly_status s = ps_disconnected_impl(p, delta_x, out, shell_power_or_null, (cudaStream_t)stream);
+    poly_status s = guarded([&] { return ps_disconnected_impl(p, delta_x, out, shell_power_or_null, (cudaStream_t)stream); });
     leave(p, prev);
     return s;
 }
@@ -909,7 +922,7 @@ poly_status poly_backward(poly_plan p, const void* delta_x, const double* dL_dB,
     if (dL_ddelta == delta_x || dL_ddelta == (const void*)dL_dB) return set_error(POLY_ERR_ARG, "output aliases an input");
     int prev;
     PS_TRY(enter(p, &prev));
-    poly_status s = ps_backward_impl(p, delta_x, dL_dB, dL_ddelta, (cudaStream_t)stream);
+    poly_status s = guarded([&] { return ps_backward_impl(p, delta_x, dL_dB, dL_ddelta, (cudaStream_t)stream); });
     leave(p, prev);
     return s;
 }
@@ -919,7 +932,7 @@ poly_status poly_estimate_batched(const poly_plan* plans, const void* const* fie
     if (count < 0 || (count > 0 && (!plans || !fields || !outs))) return set_error(POLY_ERR_ARG, "bad batch");
     for (int i = 0; i < count; i++)
         if (!plans[i] || !fields[i] || !outs[i]) return set_error(POLY_ERR_ARG, "NULL entry in batch");
-    return ps_batched_impl(plans, fields, outs, count, (cudaStream_t)stream);
+    return guarded([&] { return ps_batched_impl(plans, fields, outs, count, (cudaStream_t)stream); });
 }
 
 poly_status poly_plan_sync(poly_plan p, void* stream) {
@@ -959,11 +972,19 @@ poly_status poly_plan_set_timing(poly_plan p, int enable) {
 // tunable shape of the tensor-core contraction
 // ---------------------------------------------------------------------------
 static poly_status apply_tc_config(PsPlan* p, int max_mt, int cta_mult) {
+    const int old_mt = p->tc_max_mt, old_mult = p->tc_cta_mult;
     p->tc_max_mt = max_mt;
     p->tc_cta_mult = cta_mult;
     ps_batched_forget(p);  // cached graphs hold the old tables
     ps_tc_free(p);
-    return ps_tc_prepare(p);
+    const poly_status s = guarded([&] { return ps_tc_prepare(p); });
+    if (s) {  // a shape that does not fit: rebuild the previous one, so the plan stays usable
+        ps_tc_free(p);
+        p->tc_max_mt = old_mt;
+        p->tc_cta_mult = old_mult;
+        if (guarded([&] { return ps_tc_prepare(p); })) ps_tc_free(p);  // then ps_tc_sums reports UNSUPPORTED
+    }
+    return s;
 }
 
 static bool decode_config(int config, int* max_mt, int* cta_mult) {
