@@ -193,7 +193,8 @@ poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, 
         AdjTables* A = new (std::nothrow) AdjTables();
         if (!A) return POLY_ERR_ALLOC;
         poly_status s = adj_prepare(p, *A);
-        if (s) {
+        if (s) {  // the tables' device buffers stay on the plan's list until it is destroyed
+            ps_at_free(A->at);
             delete A;
             return s;
         }

@@ -673,9 +673,16 @@ poly_status ps_estimate_impl(PsPlan* p, const void* delta, double* out, double* 
 
 // B_disc of every bin (order-4 plans): forward transform, shell powers, per-bin Wick pairings
 static poly_status ps_disconnected_impl(PsPlan* p, const void* delta, double* out, double* power, cudaStream_t st) {
+    // each buffer is recorded only once it is complete, so a failure here is retried on the next call
     if (!p->d_bins) {
-        PS_TRY(upload(p, (void**)&p->d_bins, p->bins));
-        PS_TRY(ps_alloc(p, (void**)&p->d_shell_power, (size_t)p->nshell * sizeof(double)));
+        void* d = nullptr;
+        PS_TRY(upload(p, &d, p->bins));
+        p->d_bins = (int32_t*)d;
+    }
+    if (!p->d_shell_power) {
+        void* d = nullptr;
+        PS_TRY(ps_alloc(p, &d, (size_t)p->nshell * sizeof(double)));
+        p->d_shell_power = (double*)d;
     }
     cudaError_t e;
     if ((e = ps_forward(p->N, p->is_double, delta, p->K, p->d_tw_fwd, p->d_W, p->d_fhat, p->d_spill, st)))
