@@ -222,6 +222,20 @@ def _stream_handle(stream):
     return s.cuda_stream
 
 
+def _require(t, dtype, numel: int, name: str, device=None) -> None:
+    """Check a tensor handed to the library before its pointer is: CUDA, dtype, contiguous, size, device."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, not {t.numel()}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} must be on {device}, not {t.device}")
+
+
 class Plan:
     """A plan for one (N, L, n, edges, precision); owns the library handle."""
 
@@ -248,9 +262,9 @@ class Plan:
         """delta: CUDA tensor [N,N,N] of the plan's real dtype.  Returns B (float64) [and scale]."""
         import torch
 
-        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
-        assert delta.numel() == self.N ** 3
+        _require(delta, self.real_dtype, self.N ** 3, "delta")
         out = torch.empty(self.nbins, dtype=torch.float64, device=delta.device) if out is None else out
+        _require(out, torch.float64, self.nbins, "out", delta.device)
         sc = torch.empty(self.nbins, dtype=torch.float64, device=delta.device) if scale else None
         poly_estimate(self.handle, delta.data_ptr(), out.data_ptr(), sc.data_ptr() if scale else None,
                       _stream_handle(stream))
@@ -258,7 +272,8 @@ class Plan:
 
     def estimate_host(self, delta: np.ndarray) -> np.ndarray:
         d = np.ascontiguousarray(delta, dtype=np.float64 if self.prec == POLY_FP64 else np.float32)
-        assert d.size == self.N ** 3
+        if d.size != self.N ** 3:
+            raise ValueError(f"delta must have {self.N ** 3} elements, not {d.size}")
         out = np.empty(self.nbins, dtype=np.float64)
         poly_estimate_host(self.handle, d, out, None)
         return out
@@ -266,9 +281,11 @@ class Plan:
     def backward(self, delta, dLdB, grad=None, stream=None):
         import torch
 
-        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
+        _require(delta, self.real_dtype, self.N ** 3, "delta")
         g = dLdB.to(device=delta.device, dtype=torch.float64).contiguous()
+        _require(g, torch.float64, self.nbins, "dLdB")
         grad = torch.empty_like(delta) if grad is None else grad
+        _require(grad, self.real_dtype, self.N ** 3, "grad", delta.device)
         poly_backward(self.handle, delta.data_ptr(), g.data_ptr(), grad.data_ptr(), _stream_handle(stream))
         return grad
 
@@ -277,9 +294,9 @@ class Plan:
         (subtract it from estimate() for the connected part).  Returns B_disc [and the shell powers]."""
         import torch
 
-        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
-        assert delta.numel() == self.N ** 3
+        _require(delta, self.real_dtype, self.N ** 3, "delta")
         out = torch.empty(self.nbins, dtype=torch.float64, device=delta.device) if out is None else out
+        _require(out, torch.float64, self.nbins, "out", delta.device)
         pw = torch.empty(len(self.edges) - 1, dtype=torch.float64, device=delta.device) if power else None
         poly_trispectrum_disconnected(self.handle, delta.data_ptr(), out.data_ptr(), pw.data_ptr() if power else None,
                                       _stream_handle(stream))
@@ -290,7 +307,7 @@ class Plan:
 
     def tune(self, delta, stream=None) -> tuple[int, float]:
         """Time the contraction shapes on this field's shells; keep the fastest (returns code, ms)."""
-        assert delta.is_cuda and delta.dtype == self.real_dtype and delta.is_contiguous()
+        _require(delta, self.real_dtype, self.N ** 3, "delta")
         return poly_plan_tune(self.handle, delta.data_ptr(), _stream_handle(stream))
 
     def set_config(self, config: int) -> None:

@@ -214,3 +214,35 @@ def test_plain_c_client_links_and_calls_the_host_entry_points(lib, tmp_path):
     assert out[1] == f"nbins {len(bins)}"
     assert np.array_equal(bins, oracle.enumerate_bins(np.arange(7) + 0.5, 3))
     assert out[-1].split()[2] == str(16 ** 3)
+
+
+def test_tensor_checks_run_before_any_library_call():
+    """The binding refuses a tensor it cannot hand over as a pointer: host memory, another dtype, a strided
+    view, a wrong size or another device (each reported by name), so no kernel reads past a buffer."""
+    torch = pytest.importorskip("torch")
+
+    class T:  # stand-in for a CUDA tensor (no device here)
+        def __init__(self, dtype=torch.float32, n=512, contiguous=True, device="cuda:0"):
+            self.is_cuda, self.dtype, self._n, self._c, self.device = True, dtype, n, contiguous, device
+
+        def is_contiguous(self):
+            return self._c
+
+        def numel(self):
+            return self._n
+
+    ps._require(T(), torch.float32, 512, "delta", "cuda:0")
+    for t, msg in [(torch.zeros(8, 8, 8), "CUDA tensor"), (T(dtype=torch.float64), "float32"),
+                   (T(contiguous=False), "contiguous"), (T(n=511), "512 elements"),
+                   (T(device="cuda:1"), "cuda:0")]:
+        with pytest.raises(ValueError, match=msg):
+            ps._require(t, torch.float32, 512, "delta", "cuda:0")
+    plan = ps.Plan.__new__(ps.Plan)  # no library handle: every check below fires before a call
+    plan.N, plan.nbins, plan.prec, plan.handle, plan.ell = 8, 5, ps.POLY_FP32, None, 0
+    plan.edges = np.arange(4) + 0.5
+    for call in (lambda: plan.estimate(torch.zeros(8, 8, 8)), lambda: plan.backward(torch.zeros(8, 8, 8), None),
+                 lambda: plan.disconnected(torch.zeros(8, 8, 8)), lambda: plan.tune(torch.zeros(8, 8, 8))):
+        with pytest.raises(ValueError, match="delta must be a CUDA tensor"):
+            call()
+    with pytest.raises(ValueError, match="512 elements"):
+        plan.estimate_host(np.zeros(500, np.float32))
