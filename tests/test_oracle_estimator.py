@@ -454,3 +454,14 @@ def test_gradient_matches_central_differences(order, nshell):
         dm[i] -= h
         fd = (loss(dp) - loss(dm)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * (abs(g[i]) + np.abs(g).max() * 1e-3)
+
+
+def test_nonzero_counts_are_the_polygon_rule_widened_by_one_shell():
+    """Unit-width shells centred on integers: a sorted triple has closed triangles exactly when
+    k1 <= k2 + k3 + 1 (the polygon inequality of App. B on the centres, widened by the shells' width), so
+    the nonzero-count set is that rule (25,424 triples at 64 shells) and every sorted triple outside it
+    counts zero."""
+    e = fieldgen.unit_edges(12)
+    b = oracle.enumerate_bins(e, 3, oracle.RULE_ALL_SORTED)
+    c = oracle.counts_exact(48, e, 3, b)
+    assert np.array_equal(c > 0, b[:, 0] <= b[:, 1] + b[:, 2] + 1)
