@@ -124,6 +124,16 @@ poly_status poly_plan_counts(poly_plan plan, int64_t* counts);
 poly_status poly_plan_bin_wraps(poly_plan plan, uint8_t* wraps);
 
 /*
+ * Device memory the plan holds now, in bytes (*bytes, host): its workspace
+ * (nfield x N^3 shell fields of the plan's real type, about 4.3 GB at 256^3
+ * with 64 FP32 fields, plus the transform buffers, tables and partial sums),
+ * and the adjoint's buffers once poly_backward has run (another nshell x N^3
+ * fields).  Plan creation's transient count buffers are freed before it
+ * returns and are not included.  Host only.
+ */
+poly_status poly_plan_device_bytes(poly_plan plan, int64_t* bytes);
+
+/*
  * Estimate B_b for one field.  delta_x: device, N^3 real (float for POLY_FP32 /
  * POLY_SPLIT_BF16, double for POLY_FP64).  out: device, nbins double, B_b.
  * scale_or_null: device, nbins double or NULL; if given, receives

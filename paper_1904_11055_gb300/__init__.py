@@ -32,7 +32,8 @@ ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_pl
                "poly_estimate_host", "poly_backward", "poly_estimate_batched", "poly_plan_sync", "poly_plan_destroy",
                "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
                "poly_plan_stats", "poly_estimate_noalloc", "poly_plan_tune", "poly_plan_set_config",
-               "poly_trispectrum_disconnected", "poly_plan_create_multipole", "poly_plan_bin_wraps")
+               "poly_trispectrum_disconnected", "poly_plan_create_multipole", "poly_plan_bin_wraps",
+               "poly_plan_device_bytes")
 
 
 class poly_stats(ctypes.Structure):
@@ -63,6 +64,7 @@ def load_library():
     L.poly_plan_bins.argtypes = [P, P]
     L.poly_plan_counts.argtypes = [P, P]
     L.poly_plan_bin_wraps.argtypes = [P, P]
+    L.poly_plan_device_bytes.argtypes = [P, ctypes.POINTER(i64)]
     L.poly_estimate.argtypes = [P, P, P, P, P]
     L.poly_estimate_host.argtypes = [P, P, P, P]
     L.poly_backward.argtypes = [P, P, P, P, P]
@@ -138,6 +140,13 @@ def poly_plan_bin_wraps(plan: int) -> np.ndarray:
     out = np.empty(poly_plan_nbins(plan), dtype=np.uint8)
     _check(load_library().poly_plan_bin_wraps(plan, out.ctypes.data_as(ctypes.c_void_p)), "poly_plan_bin_wraps")
     return out.astype(bool)
+
+
+def poly_plan_device_bytes(plan: int) -> int:
+    """Device memory the plan holds, in bytes."""
+    v = ctypes.c_int64(0)
+    _check(load_library().poly_plan_device_bytes(plan, ctypes.byref(v)), "poly_plan_device_bytes")
+    return v.value
 
 
 def poly_estimate(plan: int, delta_ptr: int, out_ptr: int, scale_ptr: int | None, stream: int | None) -> None:
@@ -312,6 +321,10 @@ class Plan:
 
     def set_config(self, config: int) -> None:
         poly_plan_set_config(self.handle, config)
+
+    def device_bytes(self) -> int:
+        """Device memory the plan holds, in bytes (its workspace; the adjoint's once backward has run)."""
+        return poly_plan_device_bytes(self.handle)
 
     def bin_wraps(self) -> np.ndarray:
         """Per bin, True where closures that wrap around the grid may add to it (POLY_ALLOW_ALIAS plans)."""

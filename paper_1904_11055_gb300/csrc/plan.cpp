@@ -97,6 +97,7 @@ poly_status ps_alloc(PsPlan* p, void** ptr, size_t bytes) {
                                              cudaGetErrorString(e));
     }
     p->allocations.push_back(*ptr);
+    p->allocation_bytes.push_back(bytes);
     return POLY_OK;
 }
 
@@ -105,6 +106,7 @@ void ps_free(PsPlan* p, void* ptr) {
     auto it = std::find(p->allocations.begin(), p->allocations.end(), ptr);
     if (it != p->allocations.end()) {
         cudaFree(ptr);
+        p->allocation_bytes.erase(p->allocation_bytes.begin() + (it - p->allocations.begin()));
         p->allocations.erase(it);
     }
 }
@@ -419,6 +421,7 @@ static void free_plan(PsPlan* p) {
     ps_adj_free(p);
     for (void* q : p->allocations) cudaFree(q);
     p->allocations.clear();
+    p->allocation_bytes.clear();
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
@@ -761,6 +764,14 @@ poly_status poly_plan_bins(poly_plan p, int32_t* idx) {
 poly_status poly_plan_counts(poly_plan p, int64_t* counts) {
     if (!p || !counts) return set_error(POLY_ERR_ARG, "NULL argument");
     std::memcpy(counts, p->counts.data(), p->counts.size() * sizeof(int64_t));
+    return POLY_OK;
+}
+
+poly_status poly_plan_device_bytes(poly_plan p, int64_t* bytes) {
+    if (!p || !bytes) return set_error(POLY_ERR_ARG, "NULL argument");
+    int64_t sum = 0;
+    for (size_t b : p->allocation_bytes) sum += (int64_t)b;
+    *bytes = sum;
     return POLY_OK;
 }
 

@@ -83,6 +83,7 @@ struct poly_plan_s {
     bool ev_recorded = false;
     // every device allocation owned by the plan
     std::vector<void*> allocations;
+    std::vector<size_t> allocation_bytes;  // size of each entry of allocations
 };
 typedef poly_plan_s PsPlan;
 

@@ -124,6 +124,7 @@ def test_binding_wrappers_marshal_without_a_device(lib):
         lambda: ps.poly_backward(None, None, None, None, None),
         lambda: ps.poly_trispectrum_disconnected(None, None, None, None, None),
         lambda: ps.poly_plan_bin_wraps(None),
+        lambda: ps.poly_plan_device_bytes(None),
     ]
     for call in calls:
         with pytest.raises(ps.PolyError) as ei:
