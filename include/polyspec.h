@@ -124,7 +124,9 @@ poly_status poly_plan_counts(poly_plan plan, int64_t* counts);
 poly_status poly_plan_bin_wraps(poly_plan plan, uint8_t* wraps);
 
 /*
- * Device memory the plan holds now, in bytes (*bytes, host): its workspace
+ * Device memory the plan holds now, in bytes (*bytes, host).  Sec. 1 sizes the
+ * method's memory as N_max fields of (n N_max)^3 cells, growing like
+ * n^3 N_max^4; here that is the workspace
  * (nfield x N^3 shell fields of the plan's real type, about 4.3 GB at 256^3
  * with 64 FP32 fields, plus the transform buffers, tables and partial sums),
  * and the adjoint's buffers once poly_backward has run (another nshell x N^3
