@@ -71,12 +71,6 @@ struct CountKey {
 std::mutex g_count_mu;
 std::map<CountKey, std::vector<int64_t>> g_count_cache;
 
-bool member(const double* edges, int s, long long q2) {
-    if (q2 == 0) return false;
-    const double d = (double)q2;
-    return edges[s] * edges[s] <= d && d < edges[s + 1] * edges[s + 1];
-}
-
 }  // namespace
 
 void ps_set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -147,20 +141,29 @@ void enumerate_bins(int nshell, const std::vector<double>& edges, int order, boo
 
 // ---------------------------------------------------------------------------
 // shell line tables: per shell, the (ky, kz >= 0) lines crossing it and the
-// |kx| run [a, b] on each line (membership is monotone in |kx|)
+// |kx| run [a, b] on each line.  |q|^2 = rho2 + kx^2 grows with |kx|, so the
+// shell's kx on a line form one run: a is the first |kx| with |q|^2 >= e_s^2,
+// b the last (<= K) with |q|^2 < e_{s+1}^2, found from a square root and then
+// settled by the exact comparisons e_s^2 <= |q|^2 < e_{s+1}^2 in double, |q|^2
+// converted exactly (q = 0 is in no shell).
 // ---------------------------------------------------------------------------
 void build_lines(const PsPlan* p, const double* e, int s, std::vector<short>& lines) {
     const int K = p->K;
+    const double lo2 = e[s] * e[s], hi2 = e[s + 1] * e[s + 1];
     for (int ky = -K; ky <= K; ky++)
         for (int kz = 0; kz <= K; kz++) {
             const long long rho2 = (long long)ky * ky + (long long)kz * kz;
-            int a = -1, b = -1;
-            for (int kx = 0; kx <= K; kx++)
-                if (member(e, s, rho2 + (long long)kx * kx)) {
-                    if (a < 0) a = kx;
-                    b = kx;
-                }
-            if (a >= 0) {
+            auto q2 = [&](long long kx) { return (double)(rho2 + kx * kx); };
+            long long a = lo2 > (double)rho2 ? (long long)std::sqrt(lo2 - (double)rho2) : 0;
+            if (a > K + 1) a = K + 1;
+            while (a > 0 && q2(a - 1) >= lo2) a--;
+            while (a <= K && q2(a) < lo2) a++;
+            if (a == 0 && rho2 == 0) a = 1;
+            long long b = hi2 > (double)rho2 ? (long long)std::sqrt(hi2 - (double)rho2) : -1;
+            if (b > K) b = K;
+            while (b >= 0 && q2(b) >= hi2) b--;
+            while (b < K && q2(b + 1) < hi2) b++;
+            if (a <= b) {
                 lines.push_back((short)ky);
                 lines.push_back((short)kz);
                 lines.push_back((short)a);

@@ -30,15 +30,14 @@ STATUS = {v: k for k, v in ps.STATUS.items()}
 @pytest.fixture(scope="module")
 def lib():
     psbuild.build()
-    L = ps.load_library()
-    P = ctypes.c_void_p
-    L.poly_diag_host_tables.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
-                                        P, P, P, P, P, P, P, P, P]
-    L.poly_diag_host_tables.restype = ctypes.c_int
-    return L
+    return ps.load_library()
 
 
 def host_tables(lib, N, order, edges, flags=0, ell=0):
+    P = ctypes.c_void_p
+    lib.poly_diag_host_tables.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
+                                          P, P, P, P, P, P, P, P, P]
+    lib.poly_diag_host_tables.restype = ctypes.c_int
     e = np.ascontiguousarray(edges, dtype=np.float64)
     ns = e.size - 1
     sizes = np.zeros(7, dtype=np.int64)
@@ -100,6 +99,8 @@ LAYOUTS = {
     "wide1.5x8": fieldgen.unit_edges(8, 1.5),
     "log9": np.concatenate([[0.5], np.geomspace(1.5, 14.0, 9)]),
 }
+# edges whose squares land on (or a rounding away from) integers |q|^2: ties decided by the exact comparison
+TIES = np.sqrt(np.array([1.0, 5.0, 9.0, 20.0, 33.0, 50.0, 51.0, 98.0]))
 
 
 @pytest.mark.parametrize("order", [2, 3, 4, 5, 6])
@@ -123,9 +124,12 @@ def test_multipole_tiles_read_the_weighted_first_leg(lib, order, ell):
     check_tiles(t, order, 7, 7)
 
 
-@pytest.mark.parametrize("N,layout", [(32, "unit12"), (48, "wide1.5x8"), (48, "log9")])
+@pytest.mark.parametrize("N,layout", [(32, "unit12"), (48, "wide1.5x8"), (48, "log9"), (32, "ties"),
+                                      (128, "unit40"), (96, "wide1.5x20"), (256, "unit64")])
 def test_line_tables_cover_each_shell_exactly(lib, N, layout):
-    e = LAYOUTS[layout]
+    e = {"ties": TIES, "unit40": fieldgen.unit_edges(40), "wide1.5x20": fieldgen.unit_edges(20, 1.5),
+         "unit64": fieldgen.unit_edges(64)}.get(layout, None)
+    e = LAYOUTS[layout] if e is None else e
     rc, t = host_tables(lib, N, 2, e)
     assert rc == 0
     ns, off = len(e) - 1, t["line_off"]
