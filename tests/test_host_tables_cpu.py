@@ -437,3 +437,42 @@ def test_bin_wraps_of_the_96cube_mocks(lib):
 def test_no_wraps_without_the_alias_flag(lib):
     e = fieldgen.unit_edges(20)
     assert not bin_wraps(lib, 64, 3, e, 0).any()
+
+
+def scanned_lines(edges, s, K):
+    """Shell s's line table by testing every |kx| of every (ky, kz >= 0) line (numpy, exact integer |q|^2)."""
+    ky, kz, kx = np.meshgrid(np.arange(-K, K + 1), np.arange(K + 1), np.arange(K + 1), indexing="ij")
+    q2 = (ky * ky + kz * kz + kx * kx).astype(np.float64)
+    m = (edges[s] * edges[s] <= q2) & (q2 < edges[s + 1] * edges[s + 1]) & (q2 != 0)
+    hit = m.any(axis=2)
+    a, b = m.argmax(axis=2), K - m[:, :, ::-1].argmax(axis=2)
+    sel = np.nonzero(hit.reshape(-1))[0]
+    return np.stack([ky[:, :, 0].reshape(-1)[sel], kz[:, :, 0].reshape(-1)[sel], a.reshape(-1)[sel],
+                     b.reshape(-1)[sel]], axis=1)
+
+
+def test_line_runs_equal_a_scan_of_every_kx_on_random_edges(lib):
+    """Each line's |kx| run is computed from its ends, not by testing every |kx|: the tables equal, line for
+    line, a scan of every |kx| on 60 random edge sets (unit shells at random offsets, squared edges on
+    integers, random widths, edges from 0)."""
+    rng = np.random.default_rng(2024)
+    for trial in range(60):
+        kind, ns = trial % 4, int(rng.integers(1, 8))
+        if kind == 0:
+            e = rng.uniform(0, 2) + np.arange(ns + 1)
+        elif kind == 1:
+            e = np.sqrt(np.cumsum(rng.integers(1, 40, ns + 1)).astype(np.float64))
+        elif kind == 2:
+            e = rng.uniform(0, 2) + np.cumsum(rng.uniform(0.05, 6.0, ns + 1))
+        else:
+            e = 0.5 * np.arange(ns + 1)
+        K = 0
+        while (K + 1) ** 2 < e[-1] ** 2:
+            K += 1
+        N = next(n for n in (16, 24, 32, 48, 64, 96, 128) if 2 * K + 1 <= n)
+        rc, t = host_tables(lib, N, 2, e, ps.POLY_ALLOW_ALIAS)
+        assert rc == 0
+        off = t["line_off"]
+        for s in range(ns):
+            got = t["lines"][off[s]:off[s + 1]].astype(np.int64)
+            assert np.array_equal(got, scanned_lines(e, s, K)), (trial, s)
