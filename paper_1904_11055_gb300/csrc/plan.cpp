@@ -274,11 +274,9 @@ static int choose_splits(int ntiles, int64_t nchunks, int sms) {
 // exact counts: FP64 counting fields on the symmetry wedge
 //   0 <= x <= y <= z <= floor(N/2), weight = orbit size under coordinate
 //   permutations and sign flips (x_c -> N - x_c); sum_wedge w prod iota = sum_x prod iota.
+// The counting fields are invariant under those 48 symmetries of the cube
+// because the shells are spheres.  Even N.
 // ---------------------------------------------------------------------------
-// The counting fields are invariant under the 48 symmetries of the cube (axis
-// permutations, x -> -x mod N per axis: the shells are spheres), so the count sums
-// run over the wedge 0 <= x <= y <= z <= N/2 with each cell weighted by its orbit
-// size.  Even N.
 static void count_wedge(int N, std::vector<int32_t>& widx, std::vector<double>& wgt) {
     const int h = N / 2;
     for (int x = 0; x <= h; x++)
