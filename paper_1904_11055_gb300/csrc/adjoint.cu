@@ -8,6 +8,7 @@
 // w_e = sum over the (bin, position) pairs that produce e of g_b / count_b; the
 // constant c_n / N^3 is applied when the transformed G_m are gathered.
 #include <algorithm>
+#include <array>
 #include <map>
 #include <new>
 #include <vector>
@@ -116,37 +117,46 @@ struct AdjTables {
 // (eoff / ebins).  Host only.
 void ps_adj_entries(const PsPlan* p, std::vector<int>& moff, std::vector<short4>& ent, std::vector<int>& eoff,
                     std::vector<int>& ebins) {
-    const int n = p->order;
-    // entries keyed by (m, sorted other shells); value: contributing bins
-    std::map<std::vector<int>, std::vector<int>> ents;
+    const int n = p->order;  // 2 .. 4
+    // one record per (bin, position t of m in it): key (m, the other shells sorted, -1 padded), bin; sorted
+    // stably by key, so each entry's bins keep the (bin, position) order they were produced in
+    struct Rec {
+        std::array<int, 4> key;
+        int bin;
+    };
+    std::vector<Rec> recs;
+    recs.reserve((size_t)p->nbins * n);
     for (int64_t b = 0; b < p->nbins; b++) {
         const int32_t* k = &p->bins[b * n];
         for (int t = 0; t < n; t++) {
-            std::vector<int> key{k[t] - 1};
-            std::vector<int> rest;
+            Rec r{{k[t] - 1, -1, -1, -1}, (int)b};
+            int c = 1;
             for (int u = 0; u < n; u++)
-                if (u != t) rest.push_back(k[u] - 1);
-            std::sort(rest.begin(), rest.end());
-            key.insert(key.end(), rest.begin(), rest.end());
-            ents[key].push_back((int)b);
+                if (u != t) r.key[c++] = k[u] - 1;
+            std::sort(r.key.begin() + 1, r.key.begin() + n);
+            recs.push_back(r);
         }
     }
+    std::stable_sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) { return x.key < y.key; });
     moff.assign(p->nshell + 1, 0);
     eoff.assign(1, 0);
     ebins.clear();
     ent.clear();
-    for (auto& kv : ents) moff[kv.first[0] + 1]++;
-    for (int m = 0; m < p->nshell; m++) moff[m + 1] += moff[m];
-    for (auto& kv : ents) {  // std::map order: grouped by m ascending
+    for (size_t i = 0; i < recs.size();) {  // key order: grouped by m ascending
+        const std::array<int, 4>& key = recs[i].key;
+        size_t j = i;
+        while (j < recs.size() && recs[j].key == key) ebins.push_back(recs[j++].bin);
+        moff[key[0] + 1]++;
         short4 f;
-        f.x = (short)kv.first[1];
-        f.y = (short)(n >= 3 ? kv.first[2] : -1);
-        f.z = (short)(n >= 4 ? kv.first[3] : -1);
+        f.x = (short)key[1];
+        f.y = (short)key[2];
+        f.z = (short)key[3];
         f.w = 0;
         ent.push_back(f);
-        ebins.insert(ebins.end(), kv.second.begin(), kv.second.end());
         eoff.push_back((int)ebins.size());
+        i = j;
     }
+    for (int m = 0; m < p->nshell; m++) moff[m + 1] += moff[m];
 }
 
 static poly_status adj_prepare(PsPlan* p, AdjTables& A) {

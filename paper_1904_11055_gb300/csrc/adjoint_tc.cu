@@ -425,6 +425,7 @@ static int diag_adj_tables(int N, int order, const double* edges, int nshell, un
                            int64_t* sizes, int32_t* moff, int16_t* ent, int32_t* eoff, int32_t* ebins,
                            int32_t* at_groups, int32_t* at_chunks, int32_t* at_pos) {
     if (!sizes || sms < 1) return POLY_ERR_ARG;
+    if (order > 4) return POLY_ERR_UNSUPPORTED;  // as poly_backward
     PsPlan hp;  // host tables only: no device call, no device memory
     std::vector<short> lines;
     if (poly_status s = ps_plan_host_tables(&hp, N, 1.0, order, nshell, edges, (poly_precision)prec, flags, 0, lines))
