@@ -36,6 +36,7 @@
 #include <new>
 #include <set>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -753,7 +754,12 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     std::vector<int4>& runs = h.runs;
     std::vector<short2>& rowf = h.rowf;
     std::vector<short2>& colf = h.colf;
-    std::map<std::tuple<int, int, int, int>, std::pair<int, int>> slot_of;  // (row, col) keys -> (group, slot)
+    // (row, col) keys -> (group, slot); shells (from 1, or -1 for none) packed one per byte
+    auto pack = [](int a, int b, int c, int d) {
+        return (uint32_t)(a + 1) | (uint32_t)(b + 1) << 8 | (uint32_t)(c + 1) << 16 | (uint32_t)(d + 1) << 24;
+    };
+    std::unordered_map<uint32_t, std::pair<int, int>> slot_of;
+    slot_of.reserve((size_t)p->nbins * 2);
     std::vector<std::pair<int, int>> gcol_key(gcol.size());
     for (auto& kv : gcol) gcol_key[kv.second] = kv.first;
     double work_cells = 0;
@@ -807,7 +813,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
                     auto ba = block_acc[lc / 16];
                     const int acc_col = ba.second + (lc - ba.first);
                     auto ck = gcol_key[c];
-                    slot_of[{rl[r].key.first, rl[r].key.second, ck.first, ck.second}] = {gi, acc_col * 128 + (int)(r - r0)};
+                    slot_of[pack(rl[r].key.first, rl[r].key.second, ck.first, ck.second)] = {gi, acc_col * 128 + (int)(r - r0)};
                 }
             mtiles.push_back(M);
         }
@@ -847,7 +853,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     for (int64_t i = 0; i < p->nbins; i++) {
         auto rk = rkey(&p->bins[i * n]);
         auto ck = ckey(&p->bins[i * n]);
-        auto gs = slot_of.at({rk.first, rk.second, ck.first, ck.second});
+        auto gs = slot_of.at(pack(rk.first, rk.second, ck.first, ck.second));
         binmap[i] = make_int4(first[gs.first], nsplit[gs.first], gs.second, 0);
     }
     return POLY_OK;
