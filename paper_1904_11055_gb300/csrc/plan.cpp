@@ -13,6 +13,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/polyspec.h"
@@ -210,7 +211,15 @@ void build_cc_tiles(PsPlan* p, CcTiles& t, int first_shift) {
     std::stable_sort(ri.begin(), ri.end(), [](const RowInfo& a, const RowInfo& b) {
         return std::make_pair(a.cols.front(), a.cols.back()) < std::make_pair(b.cols.front(), b.cols.back());
     });
-    std::map<std::pair<Key, Key>, int64_t> slot_of;  // (row key, col key) -> slot
+    // (row key, col key) -> slot; the six slots (from 1, or -1; at most 2 * 128) packed 10 bits each
+    auto pack = [](const Key& r, const Key& c) {
+        uint64_t v = 0;
+        for (int i = 0; i < 3; i++) v = v << 10 | (uint64_t)(r[i] + 1);
+        for (int i = 0; i < 3; i++) v = v << 10 | (uint64_t)(c[i] + 1);
+        return v;
+    };
+    std::unordered_map<uint64_t, int64_t> slot_of;
+    slot_of.reserve((size_t)p->nbins * 2);
     for (size_t g = 0; g < ri.size(); g += kCcTM) {
         const size_t g1 = std::min(ri.size(), g + kCcTM);
         std::vector<Key> cu;
@@ -255,13 +264,13 @@ void build_cc_tiles(PsPlan* p, CcTiles& t, int first_shift) {
                     if (it == cidx.end()) continue;
                     const int rr = (int)(r - g), cc = it->second;
                     tile.region_mask |= 1u << ((rr / 32) * 4 + cc / 16);
-                    slot_of[{ri[r].key, ck}] = (int64_t)tid * (kCcTM * kCcTN) + rr * kCcTN + cc;
+                    slot_of[pack(ri[r].key, ck)] = (int64_t)tid * (kCcTM * kCcTN) + rr * kCcTN + cc;
                 }
             t.tiles.push_back(tile);
         }
     }
     t.slot.resize(p->nbins);
-    for (int64_t i = 0; i < p->nbins; i++) t.slot[i] = slot_of.at({rkey(&p->bins[i * n]), ckey(&p->bins[i * n])});
+    for (int64_t i = 0; i < p->nbins; i++) t.slot[i] = slot_of.at(pack(rkey(&p->bins[i * n]), ckey(&p->bins[i * n])));
 }
 
 static int choose_splits(int ntiles, int64_t nchunks, int sms) {
