@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kAtThreads, 1)
             for (int k0 = 32 * h; k0 < kp; k0 += 64) {
                 uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int i = 0; i < 16; i++) tc::split2(sd[32 * (k0 + 2 * i)], sd[32 * (k0 + 2 * i + 1)], hi[i], lo[i]);
+                for (int i = 0; i < 16; i++) tc::split2_fast(sd[32 * (k0 + 2 * i)], sd[32 * (k0 + 2 * i + 1)], hi[i], lo[i]);
                 tc::tmem_st16(tmem + lane_base + a0 + (uint32_t)(k0 / 2), hi);
                 tc::tmem_st16(tmem + lane_base + a0 + (uint32_t)(kp / 2 + k0 / 2), lo);
             }

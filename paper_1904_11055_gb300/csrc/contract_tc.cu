@@ -109,15 +109,15 @@ __device__ __forceinline__ void tc_b_item(uint32_t D, int key1, int key2, uint32
                          : "=f"(y0.x), "=f"(y0.y), "=f"(y0.z), "=f"(y0.w) : "r"(D + (uint32_t)key2));
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(y1.x), "=f"(y1.y), "=f"(y1.z), "=f"(y1.w) : "r"(D + ((uint32_t)key2 ^ 16u)));
-            tc::split2_prod_x2(x0.x, y0.x, x0.y, y0.y, h[0], l[0]);
-            tc::split2_prod_x2(x0.z, y0.z, x0.w, y0.w, h[1], l[1]);
-            tc::split2_prod_x2(x1.x, y1.x, x1.y, y1.y, h[2], l[2]);
-            tc::split2_prod_x2(x1.z, y1.z, x1.w, y1.w, h[3], l[3]);
+            tc::split2_prod_fast(x0.x, y0.x, x0.y, y0.y, h[0], l[0]);
+            tc::split2_prod_fast(x0.z, y0.z, x0.w, y0.w, h[1], l[1]);
+            tc::split2_prod_fast(x1.x, y1.x, x1.y, y1.y, h[2], l[2]);
+            tc::split2_prod_fast(x1.z, y1.z, x1.w, y1.w, h[3], l[3]);
         } else {
-            tc::split2(x0.x, x0.y, h[0], l[0]);
-            tc::split2(x0.z, x0.w, h[1], l[1]);
-            tc::split2(x1.x, x1.y, h[2], l[2]);
-            tc::split2(x1.z, x1.w, h[3], l[3]);
+            tc::split2_fast(x0.x, x0.y, h[0], l[0]);
+            tc::split2_fast(x0.z, x0.w, h[1], l[1]);
+            tc::split2_fast(x1.x, x1.y, h[2], l[2]);
+            tc::split2_fast(x1.z, x1.w, h[3], l[3]);
         }
     }
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst_hi), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3])
@@ -145,11 +145,11 @@ __device__ __forceinline__ void tc_row_products(uint32_t D, uint32_t key1, uint3
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
                          : "r"(D + (key2 ^ (c * 16u))));
-            tc::split2_prod_x2(x.x, y.x, x.y, y.y, v[2 * c4], v[8 + 2 * c4]);
-            tc::split2_prod_x2(x.z, y.z, x.w, y.w, v[2 * c4 + 1], v[8 + 2 * c4 + 1]);
+            tc::split2_prod_fast(x.x, y.x, x.y, y.y, v[2 * c4], v[8 + 2 * c4]);
+            tc::split2_prod_fast(x.z, y.z, x.w, y.w, v[2 * c4 + 1], v[8 + 2 * c4 + 1]);
         } else {
-            tc::split2(x.x, x.y, v[2 * c4], v[8 + 2 * c4]);
-            tc::split2(x.z, x.w, v[2 * c4 + 1], v[8 + 2 * c4 + 1]);
+            tc::split2_fast(x.x, x.y, v[2 * c4], v[8 + 2 * c4]);
+            tc::split2_fast(x.z, x.w, v[2 * c4 + 1], v[8 + 2 * c4 + 1]);
         }
     }
 }

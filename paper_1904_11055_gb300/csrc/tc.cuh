@@ -233,5 +233,52 @@ PS_DEV void split2_prod_x2(float x0, float y0, float x1, float y1, uint32_t& hi,
         : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
 }
 
+// hi = RN_bf16 pair of (a, b); lo = RN_bf16 pair of the residuals (a, b) - hi, taken
+// with one packed FP32 subtraction (exact: hi is within a factor 2 of each value).
+PS_DEV void split2_fast(float a, float b, uint32_t& hi, uint32_t& lo) {
+    asm("{\n\t"
+        ".reg .b64 xa, ha, ra;\n\t"
+        ".reg .b32 h, h0, h1;\n\t"
+        ".reg .f32 r0, r1;\n\t"
+        "cvt.rn.bf16x2.f32 h, %3, %2;\n\t"
+        "shl.b32 h0, h, 16;\n\t"
+        "and.b32 h1, h, 0xffff0000;\n\t"
+        "mov.b64 xa, {%2, %3};\n\t"
+        "mov.b64 ha, {h0, h1};\n\t"
+        "sub.rn.f32x2 ra, xa, ha;\n\t"
+        "mov.b64 {r0, r1}, ra;\n\t"
+        "cvt.rn.bf16x2.f32 %1, r1, r0;\n\t"
+        "mov.b32 %0, h;\n\t"
+        "}"
+        : "=r"(hi), "=r"(lo)
+        : "f"(a), "f"(b));
+}
+
+// The same for the products (x0 y0, x1 y1), rounded to FP32 first: hi = RN_bf16 pair of
+// the products, lo = RN_bf16 pair of (product - hi).  Against the residual of the exact
+// product this drops the product's own FP32 rounding (2^-24 relative), far below the
+// bf16 rounding of lo (2^-17 of the product).
+PS_DEV void split2_prod_fast(float x0, float y0, float x1, float y1, uint32_t& hi, uint32_t& lo) {
+    asm("{\n\t"
+        ".reg .b64 xa, ya, pa, ha, ra;\n\t"
+        ".reg .f32 p0, p1, r0, r1;\n\t"
+        ".reg .b32 h, h0, h1;\n\t"
+        "mov.b64 xa, {%2, %3};\n\t"
+        "mov.b64 ya, {%4, %5};\n\t"
+        "mul.rn.f32x2 pa, xa, ya;\n\t"
+        "mov.b64 {p0, p1}, pa;\n\t"
+        "cvt.rn.bf16x2.f32 h, p1, p0;\n\t"
+        "shl.b32 h0, h, 16;\n\t"
+        "and.b32 h1, h, 0xffff0000;\n\t"
+        "mov.b64 ha, {h0, h1};\n\t"
+        "sub.rn.f32x2 ra, pa, ha;\n\t"
+        "mov.b64 {r0, r1}, ra;\n\t"
+        "cvt.rn.bf16x2.f32 %1, r1, r0;\n\t"
+        "mov.b32 %0, h;\n\t"
+        "}"
+        : "=r"(hi), "=r"(lo)
+        : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
+}
+
 }  // namespace tc
 }  // namespace ps

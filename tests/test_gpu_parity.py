@@ -41,7 +41,7 @@ def gpu_estimate(delta, L, edges, order, prec, flags=0, bins=None):
     dt = torch.float64 if prec == "fp64" else torch.float32
     d = torch.from_numpy(np.ascontiguousarray(delta)).to("cuda", dt)
     B = plan.estimate(d)
-    torch.cuda.synchronize()
+    plan.sync()  # a device-side timeout raises here instead of returning partial sums
     return plan, B.cpu().numpy()
 
 
