@@ -130,21 +130,23 @@ __device__ __forceinline__ void tc_b_item(uint32_t D, int key1, int key2, uint32
 // swizzle): k * 128 + ((c ^ (k & 7)) * 16) = row_key(k) ^ (c * 16).
 __device__ __forceinline__ uint32_t tc_row_key(int k) { return (uint32_t)(k * 128) ^ (uint32_t)((k & 7) * 16); }
 
+// The 16 products of one row in its 16-cell half of a chunk: v[0..7] = hi, v[8..15] = lo,
+// column j of each holding cells 2j, 2j + 1 of the half.  r1, r2 = stage base + the row
+// factors' keys with the half already folded in (key ^ 64 half): the stage base is
+// 1024-aligned and the swizzle only flips address bits 4-6, so the 16-byte chunk c4 of
+// the half lies at r ^ (16 c4), one XOR with an immediate per load.
 template <int RA>
-__device__ __forceinline__ void tc_row_products(uint32_t D, uint32_t key1, uint32_t key2, int half, uint32_t* v) {
-    // the 16 products of one row in cells [16 half, 16 half + 16) of a chunk: v[0..7] = hi,
-    // v[8..15] = lo, column j of each holding cells 16 half + 2j, 16 half + 2j + 1
+__device__ __forceinline__ void tc_row_products(uint32_t r1, uint32_t r2, uint32_t* v) {
 #pragma unroll
     for (int c4 = 0; c4 < 4; c4++) {
-        const uint32_t c = (uint32_t)(4 * half + c4);
         float4 x, y;
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w)
-                     : "r"(D + (key1 ^ (c * 16u))));
+                     : "r"(r1 ^ (uint32_t)(16 * c4)));
         if (RA == 2) {
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
-                         : "r"(D + (key2 ^ (c * 16u))));
+                         : "r"(r2 ^ (uint32_t)(16 * c4)));
             tc::split2_prod_fast(x.x, y.x, x.y, y.y, v[2 * c4], v[8 + 2 * c4]);
             tc::split2_prod_fast(x.z, y.z, x.w, y.w, v[2 * c4 + 1], v[8 + 2 * c4 + 1]);
         } else {
@@ -348,8 +350,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int m = 0; m < kTcMaxMT; m++) {
             const short2 f = s_rowf[m * 128 + row];
-            key1[m] = tc_row_key(f.x);
-            key2[m] = tc_row_key(RA == 2 ? f.y : 0);
+            key1[m] = tc_row_key(f.x) ^ (uint32_t)(64 * half);
+            key2[m] = tc_row_key(RA == 2 ? f.y : 0) ^ (uint32_t)(64 * half);
         }
         const int ttid = tid % (kTcTeamWarps * 32);
         // stages team, team + 2, team + 4 in turn; slots i mod nslots
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int m = 0; m < kTcMaxMT; m++) {
                 if (m < nmt) {
                     uint32_t v[16];
-                    tc_row_products<RA>(D, key1[m], key2[m], half, v);
+                    tc_row_products<RA>(D + key1[m], D + key2[m], v);
                     tc::tmem_st16(abase + (uint32_t)(m * 32), v);
                 }
                 if (m == 0 && ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, Bh + b_off, Bl + b_off);
