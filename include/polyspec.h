@@ -248,9 +248,8 @@ poly_status poly_plan_stats(poly_plan plan, poly_stats* out);
  *
  * The paper has no counterpart; this is for callers that cannot call
  * cudaMalloc at the moment they need an estimate: code running after its
- * device-memory budget has been fixed, code inside a framework that owns the
- * device allocator, or latency-critical loops that must not allocate (an
- * allocation can synchronise the device).  It computes what poly_estimate
+ * device-memory budget has been fixed, or code inside a framework that owns the
+ * device allocator.  It computes what poly_estimate
  * computes for a POLY_FP32 plan of order 3 with the default (polygon) bins,
  * with the same kernels, but keeps every intermediate in one static device
  * array of 32 MiB that belongs to the library.  Every GPU that loads the
@@ -267,9 +266,11 @@ poly_status poly_plan_stats(poly_plan plan, poly_stats* out);
  * message from poly_last_error(); e.g. N = 64 with 16 shells fits, 256^3 does
  * not.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current: make it before any stream
- * capture.  All calls share the array, and each overwrites it: calls whose
- * work overlaps on the GPU (other streams or host threads) race, so serialise
- * them.
+ * capture.  Every call copies its host tables and `counts` into the array from
+ * pageable host memory (cudaMemcpyAsync), so a call can wait for its stream
+ * before it returns.  All calls share the array, and each overwrites it: calls
+ * whose work overlaps on the GPU (other streams or host threads) race, so
+ * serialise them.
  */
 poly_status poly_estimate_noalloc(int N, double L, int nshell, const double* edges, const float* delta_x,
                                   const int64_t* counts, double* out, void* stream);

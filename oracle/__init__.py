@@ -66,6 +66,7 @@ def _load():
         L.orc_estimate.argtypes = [i32, f64, P, i32, P, i32, i64, P, P, P, P, P, P, P]
         L.orc_direct_sample.argtypes = [i32, P, i32, P, i32, i64, P, P, P]
         L.orc_counts_exact.argtypes = [i32, i32, P, i32, i64, P, P]
+        L.orc_counts_triangles.argtypes = [i32, i32, P, i64, P, P]
         L.orc_gradient.argtypes = [i32, f64, P, i32, P, i32, i64, P, P, P, P]
         L.orc_disconnected.argtypes = [i32, f64, P, i32, P, i64, P, P, P, P]
         L.orc_estimate_ell.argtypes = [i32, f64, P, i32, P, i32, i32, i64, P, P, P, P]
@@ -184,6 +185,17 @@ def counts_exact(N: int, edges, order: int, bins) -> np.ndarray:
     b = np.ascontiguousarray(bins, dtype=np.int32)
     cnt = np.empty(b.shape[0], dtype=np.int64)
     _check(_load().orc_counts_exact(int(N), e.size - 1, _p(e), int(order), b.shape[0], _p(b), _p(cnt)))
+    return cnt
+
+
+def counts_triangles(N: int, edges, bins) -> np.ndarray:
+    """Exact triangle counts (n = 3) for many bins at once: the pair convolutions of counts_exact, with the
+    sum over the third shell taken for every third shell in one pass per pair (one convolution per pair)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    b = np.ascontiguousarray(bins, dtype=np.int32)
+    assert b.ndim == 2 and b.shape[1] == 3
+    cnt = np.empty(b.shape[0], dtype=np.int64)
+    _check(_load().orc_counts_triangles(int(N), e.size - 1, _p(e), b.shape[0], _p(b), _p(cnt)))
     return cnt
 
 

@@ -462,6 +462,86 @@ static int pair_conv(int N, const double* Fa, const double* Fb, double* work, in
 }
 
 /* ------------------------------------------------------------------------- */
+/* exact triangle counts (n = 3) for many bins at once: the same definition   */
+/* and pair convolutions as above (count = sum_p P_12(p) 1_S3(-p)), with the  */
+/* sum over p taken for every third shell in one pass over the grid,          */
+/*   H_12(k) = sum_p P_12(p) [-p in S_k],  count(k1, k2, k3) = H_12(k3),      */
+/* so that each pair (k1, k2) costs one convolution and one pass whatever the */
+/* number of its bins.                                                        */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int N, nshell;
+    const int32_t* smap;
+    const int32_t* P;
+    int64_t* hist; /* [256][nshell + 1], indexed by 1-based shell */
+} hist_ctx;
+
+static void hist_range(void* vctx, int64_t begin, int64_t end, int tid) {
+    hist_ctx* c = (hist_ctx*)vctx;
+    const int N = c->N;
+    int64_t* h = c->hist + (size_t)tid * (size_t)(c->nshell + 1);
+    for (int64_t i = begin; i < end; i++) {
+        const int32_t v = c->P[i];
+        if (!v) continue;
+        const int a = (int)(i / ((int64_t)N * N)), b = (int)((i / N) % N), z = (int)(i % N);
+        const int64_t j = ((int64_t)((N - a) % N) * N + (N - b) % N) * N + (N - z) % N; /* -p */
+        const int32_t k = c->smap[j];
+        if (k >= 0) h[k + 1] += v;
+    }
+}
+
+int orc_counts_triangles(int N, int nshell, const double* edges, int64_t nbins, const int32_t* bins, int64_t* counts) {
+    if (N < 2 || nbins < 0) return fail(-1, "orc_counts_triangles: bad args");
+    const size_t n3 = (size_t)N * N * N;
+    int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
+    int* fslot = (int*)malloc(sizeof(int) * (size_t)(nshell + 1));
+    int64_t* hist = (int64_t*)calloc((size_t)256 * (size_t)(nshell + 1), sizeof(int64_t));
+    int64_t* tot = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nshell + 1));
+    int rc = (!smap || !fslot || !hist || !tot) ? fail(-2, "orc_counts_triangles: out of memory")
+                                                : orc_shell_map(N, nshell, edges, smap);
+    int nf = 0;
+    for (int s = 0; s <= nshell && fslot; s++) fslot[s] = -1;
+    for (int64_t b = 0; b < nbins && !rc; b++) {
+        const int32_t* k = bins + 3 * b;
+        for (int t = 0; t < 3; t++)
+            if (k[t] < 1 || k[t] > nshell) rc = fail(-1, "orc_counts_triangles: bin shell out of range");
+        for (int t = 0; t < 2 && !rc; t++)
+            if (fslot[k[t]] < 0) fslot[k[t]] = nf++;
+    }
+    double* F = rc || nf == 0 ? NULL : (double*)malloc(sizeof(double) * 2 * n3 * (size_t)nf);
+    double* work = rc || nf == 0 ? NULL : (double*)malloc(sizeof(double) * 2 * n3);
+    int32_t* P = rc || nf == 0 ? NULL : (int32_t*)malloc(sizeof(int32_t) * n3);
+    if (!rc && nf > 0 && (!F || !work || !P)) rc = fail(-2, "orc_counts_triangles: out of memory");
+    for (int s = 1; s <= nshell && !rc; s++)
+        if (fslot[s] >= 0) rc = shell_dft(N, smap, s - 1, F + 2 * n3 * (size_t)fslot[s]);
+    for (int64_t b = 0; b < nbins; b++) counts[b] = -1;
+    /* pairs in the order of first appearance; every bin of a pair is filled from its histogram */
+    for (int64_t b0 = 0; b0 < nbins && !rc; b0++) {
+        if (counts[b0] >= 0) continue;
+        const int k1 = bins[3 * b0], k2 = bins[3 * b0 + 1];
+        rc = pair_conv(N, F + 2 * n3 * (size_t)fslot[k1], F + 2 * n3 * (size_t)fslot[k2], work, P);
+        if (rc) break;
+        memset(hist, 0, sizeof(int64_t) * 256 * (size_t)(nshell + 1));
+        hist_ctx c = {N, nshell, smap, P, hist};
+        par_for((int64_t)n3, hist_range, &c);
+        for (int s = 0; s <= nshell; s++) {
+            tot[s] = 0;
+            for (int t = 0; t < 256; t++) tot[s] += hist[(size_t)t * (size_t)(nshell + 1) + s];
+        }
+        for (int64_t b = b0; b < nbins; b++)
+            if (bins[3 * b] == k1 && bins[3 * b + 1] == k2) counts[b] = tot[bins[3 * b + 2]];
+    }
+    free(smap);
+    free(fslot);
+    free(hist);
+    free(tot);
+    free(F);
+    free(work);
+    free(P);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* exact counts for n = 5, 6 by group convolutions: the bin's shells split    */
 /* into a first group of n - 3 (two for n = 5, three for n = 6) and a second  */
 /* group of three.  With the closure map of a group g of shells,              */

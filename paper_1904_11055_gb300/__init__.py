@@ -207,9 +207,22 @@ def poly_plan_stats(plan: int) -> dict:
 
 def poly_estimate_noalloc(N: int, L: float, edges, delta_ptr: int, counts: np.ndarray, out_ptr: int,
                           stream: int | None) -> None:
-    """B_b of a small order-3 FP32 problem with no device allocation (see include/polyspec.h)."""
+    """B_b of a small order-3 FP32 problem with no device allocation (see include/polyspec.h).
+
+    counts must hold one exact count per bin of these shells (the library copies nbins of them from host
+    memory): its length is checked against the bin count first."""
     e = np.ascontiguousarray(edges, dtype=np.float64)
     c = np.ascontiguousarray(counts, dtype=np.int64)
+    lib = load_library()
+    nb = ctypes.c_int64(0)
+    lib.poly_diag_bin_wraps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    lib.poly_diag_bin_wraps.restype = ctypes.c_int
+    if (lib.poly_diag_bin_wraps(int(N), 3, e.ctypes.data_as(ctypes.c_void_p), e.size - 1, 0, ctypes.byref(nb), None)
+            == POLY_OK and c.ndim == 1 and c.size != nb.value):
+        raise ValueError(f"counts holds {c.size} values; the bispectrum of these shells has {nb.value} bins")
+    if c.ndim != 1:
+        raise ValueError("counts must be one-dimensional")
     _check(load_library().poly_estimate_noalloc(int(N), float(L), e.size - 1, e.ctypes.data_as(ctypes.c_void_p),
                                                 delta_ptr, c.ctypes.data_as(ctypes.c_void_p), out_ptr, stream),
            "poly_estimate_noalloc")

@@ -757,6 +757,10 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     std::vector<short2>& rowf = h.rowf;
     std::vector<short2>& colf = h.colf;
     // (row, col) keys -> (group, slot); shells (from 1, or -1 for none) packed one per byte
+    // shells (from 1, or -1 for none) packed one per byte: shell + 1 < 256 (multipole plans, whose row
+    // factors would use the weighted slots nshell .. 2 nshell - 1, never reach the tensor-core tables)
+    static_assert(kPsMaxShells + 1 < 256, "a shell number + 1 must fit one byte of the packed key");
+    if (p->nshell > kPsMaxShells || p->ell != 0) return POLY_ERR_UNSUPPORTED;
     auto pack = [](int a, int b, int c, int d) {
         return (uint32_t)(a + 1) | (uint32_t)(b + 1) << 8 | (uint32_t)(c + 1) << 16 | (uint32_t)(d + 1) << 24;
     };

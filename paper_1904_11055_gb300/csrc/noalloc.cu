@@ -1,13 +1,18 @@
 // Bispectrum of a small field without allocating device memory.
 //
 // Some callers cannot call cudaMalloc when they need an estimate: code that
-// runs after a memory budget has been fixed and must not allocate any more,
-// code inside a framework whose device allocator belongs to someone else, or
-// latency-critical loops where an allocation (and the device synchronisation
-// it can cause) is not acceptable.  poly_estimate_noalloc serves them: it runs
-// the same kernels as poly_estimate, with every intermediate (twiddles, shell
-// tables, spectrum, shell fields, contraction partials, sums, counts) placed in
-// one static device array that belongs to this library.
+// runs after a memory budget has been fixed and must not allocate any more, or
+// code inside a framework whose device allocator belongs to someone else.
+// poly_estimate_noalloc serves them: it runs the same kernels as poly_estimate,
+// with every intermediate (twiddles, shell tables, spectrum, shell fields,
+// contraction partials, sums, counts) placed in one static device array that
+// belongs to this library.
+//
+// Each call builds its host tables (twiddles, shell line tables, contraction
+// tiles) in ordinary pageable host memory and copies them, and the counts, into
+// the array with cudaMemcpyAsync.  Copies from pageable memory are staged
+// through the driver, so a call can wait for its stream before it returns; it
+// is not a zero-latency call.
 //
 // The array costs kNoAllocBytes on every GPU that loads the library, until the
 // process exits.  Its device address is looked up once per device, on the first
@@ -21,6 +26,8 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -72,8 +79,8 @@ struct Carve {  // 256-byte aligned sub-ranges of the static array
 };
 }  // namespace
 
-extern "C" poly_status poly_estimate_noalloc(int N, double L, int nshell, const double* edges, const float* delta_x,
-                                             const int64_t* counts, double* out, void* stream) {
+static poly_status estimate_noalloc(int N, double L, int nshell, const double* edges, const float* delta_x,
+                                    const int64_t* counts, double* out, void* stream) {
     if (!edges || !delta_x || !counts || !out) return fail(POLY_ERR_ARG, "NULL argument");
     if (nshell < 1 || nshell > 128) return fail(POLY_ERR_ARG, "nshell must be in [1, 128]");
     if (!(L > 0) || !std::isfinite(L)) return fail(POLY_ERR_ARG, "L must be positive");
@@ -177,4 +184,15 @@ extern "C" poly_status poly_estimate_noalloc(int N, double L, int nshell, const 
     if ((e = ps_normalise((const double*)(B + o_S), (const int64_t*)(B + o_cnt), hp.nbins, norm, n3d, out, st)))
         return fail(POLY_ERR_CUDA, std::string("normalise: ") + cudaGetErrorString(e));
     return POLY_OK;
+}
+
+extern "C" poly_status poly_estimate_noalloc(int N, double L, int nshell, const double* edges, const float* delta_x,
+                                             const int64_t* counts, double* out, void* stream) {
+    try {  // the host tables are std::vectors: no C++ exception crosses the C ABI
+        return estimate_noalloc(N, L, nshell, edges, delta_x, counts, out, stream);
+    } catch (const std::bad_alloc&) {
+        return fail(POLY_ERR_ALLOC, "host allocation failed");
+    } catch (const std::exception& ex) {
+        return fail(POLY_ERR_ARG, ex.what());
+    }
 }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <stdexcept>
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -211,7 +212,9 @@ void build_cc_tiles(PsPlan* p, CcTiles& t, int first_shift) {
     std::stable_sort(ri.begin(), ri.end(), [](const RowInfo& a, const RowInfo& b) {
         return std::make_pair(a.cols.front(), a.cols.back()) < std::make_pair(b.cols.front(), b.cols.back());
     });
-    // (row key, col key) -> slot; the six slots (from 1, or -1; at most 2 * 128) packed 10 bits each
+    // (row key, col key) -> slot; the six slots (from 1, or -1; at most 2 * kPsMaxShells) packed 10 bits each
+    static_assert(2 * kPsMaxShells + 1 < 1024, "a field slot + 1 must fit 10 bits of the packed key");
+    if (p->nshell > kPsMaxShells) throw std::length_error("build_cc_tiles: more shells than the packed keys hold");
     auto pack = [](const Key& r, const Key& c) {
         uint64_t v = 0;
         for (int i = 0; i < 3; i++) v = v << 10 | (uint64_t)(r[i] + 1);
@@ -445,7 +448,7 @@ constexpr int64_t kMaxSortedTuples = int64_t(1) << 26;  // host tables of about 
 // CUDA-core contraction tiles over the plain fields.  Touches no device.
 poly_status ps_plan_host_tables(PsPlan* p, int N, double L, int order, int nshell, const double* edges,
                                poly_precision prec, unsigned flags, int ell, std::vector<short>& lines) {
-    if (!edges || nshell < 1 || nshell > 128) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
+    if (!edges || nshell < 1 || nshell > kPsMaxShells) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
     if (ell < 0 || ell > 8 || (ell & 1)) return set_error(POLY_ERR_ARG, "ell must be even, in [0, 8]");
     if (ell > 0 && prec == POLY_SPLIT_BF16)
         return set_error(POLY_ERR_UNSUPPORTED, "multipole plans run in FP32 or FP64 (CUDA-core contraction)");
@@ -847,6 +850,8 @@ int poly_diag_fields(void* plan, const void* delta_x, void* fields_host, void* s
         return poly_diag_fields_impl(plan, delta_x, fields_host, stream);
     } catch (const std::bad_alloc&) {
         return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    } catch (const std::exception& ex) {
+        return set_error(POLY_ERR_ARG, ex.what());
     }
 }
 
@@ -866,6 +871,8 @@ int poly_diag_count_wedge(int N, int64_t* ncell, int32_t* cells, double* weights
         return poly_diag_count_wedge_impl(N, ncell, cells, weights);
     } catch (const std::bad_alloc&) {
         return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    } catch (const std::exception& ex) {
+        return set_error(POLY_ERR_ARG, ex.what());
     }
 }
 
@@ -913,6 +920,8 @@ int poly_diag_bin_wraps(int N, int order, const double* edges, int nshell, unsig
         return poly_diag_bin_wraps_impl(N, order, edges, nshell, flags, nbins, wraps);
     } catch (const std::bad_alloc&) {
         return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    } catch (const std::exception& ex) {
+        return set_error(POLY_ERR_ARG, ex.what());
     }
 }
 
@@ -924,6 +933,8 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
                                           slot, lines, line_off);
     } catch (const std::bad_alloc&) {
         return set_error(POLY_ERR_ALLOC, "host allocation failed");
+    } catch (const std::exception& ex) {
+        return set_error(POLY_ERR_ARG, ex.what());
     }
 }
 

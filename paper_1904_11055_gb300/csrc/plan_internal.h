@@ -16,6 +16,10 @@ struct CcTiles {
     std::vector<int64_t> slot;  // per bin: tile * 64 * 64 + r * 64 + c
 };
 
+// Largest number of shells a plan takes.  Host tables pack shell and field-slot
+// numbers into fixed-width keys that rely on it (checked where they are packed).
+constexpr int kPsMaxShells = 128;
+
 struct TcState;     // tensor-core contraction state (contract_tc.cu)
 struct AdjTables;  // adjoint entry tables (adjoint.cu)
 

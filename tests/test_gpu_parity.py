@@ -51,7 +51,8 @@ def check_against_oracle(delta, L, edges, order, prec, sample=None, flags=0):
     idx = np.arange(plan.nbins) if sample is None else np.asarray(sample)
     ref = oracle.estimate(np.asarray(delta, dtype=np.float64), L, edges, order, bins=plan.bins[idx])
     assert np.array_equal(plan.counts[idx], ref["counts"]), "counts differ from the oracle"
-    err = np.abs(B[idx] - ref["B"]) / (norm(L, N, order) * ref["scale"])
+    with np.errstate(invalid="ignore", divide="ignore"):  # bins with no polygon have no scale (0 / 0)
+        err = np.abs(B[idx] - ref["B"]) / (norm(L, N, order) * ref["scale"])
     return plan, B, ref, err
 
 
@@ -62,6 +63,38 @@ def test_counts_match_golden_enumeration():
     plan = ps.Plan(16, 1.0, 3, fieldgen.unit_edges(6), "fp32", ps.POLY_BINS_ALL_SORTED | ps.POLY_ALLOW_ALIAS)
     assert np.array_equal(plan.bins, g[:, :3])
     assert np.array_equal(plan.counts, g[:, 3])
+
+
+def read_golden_counts(name):
+    rows = np.loadtxt(os.path.join(GOLDEN, name), dtype=np.int64, comments="#")
+    return rows[:, :-1].astype(np.int32), rows[:, -1]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_counts_of_the_256cube_benchmark_plan_match_the_golden_file(prec):
+    """Every one of the 24,432 triangle counts of the 256^3 / 64-shell plan, bit for bit, against the
+    oracle's exact pair-convolution counts (tests/golden/counts_n3_64shells.txt)."""
+    bins, counts = read_golden_counts("counts_n3_64shells.txt")
+    plan = ps.Plan(256, 1000.0, 3, fieldgen.unit_edges(64), prec)
+    assert plan.nbins == len(counts) == 24432
+    assert np.array_equal(plan.bins, bins)
+    assert np.array_equal(plan.counts, counts)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("N,order,nshell,seed", [(48, 3, 12, 51), (32, 4, 7, 52)])
+def test_all_sorted_bins_match_oracle(prec, N, order, nshell, seed):
+    """POLY_BINS_ALL_SORTED: every sorted tuple (Sec. 4.2 order), including those outside the polygon
+    rule; bins with no closed polygon have count 0 and must come out as exactly 0."""
+    e = fieldgen.unit_edges(nshell)
+    delta = fieldgen.field("lognormal", N, seed, np.float32)
+    plan, B, ref, err = check_against_oracle(delta, 1000.0, e, order, prec, flags=ps.POLY_BINS_ALL_SORTED)
+    assert np.array_equal(plan.bins, oracle.enumerate_bins(e, order, oracle.RULE_ALL_SORTED))
+    zero = ref["counts"] == 0
+    assert zero.any() and (~zero).any()
+    assert np.all(B[zero] == 0.0) and np.all(ref["B"][zero] == 0.0)
+    assert err[~zero].max() <= TOL[prec], err[~zero].max()
 
 
 @pytest.mark.parametrize("N,order,nshell,width,flags", [(32, 3, 10, 1.0, 0), (48, 3, 10, 1.5, 0), (32, 4, 7, 1.0, 0),

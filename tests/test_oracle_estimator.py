@@ -115,6 +115,36 @@ def test_exact_pair_convolution_counts_match_direct_enumeration(N, order, width,
     assert np.array_equal(exact, r["counts"])
 
 
+@pytest.mark.parametrize("N,width,nshell,rule", [(16, 1.0, 6, "all"), (15, 1.0, 4, "all"), (20, 1.5, 6, "all"),
+                                                 (24, 1.0, 10, "polygon")])
+def test_batched_triangle_counts_equal_the_pair_convolution_counts(N, width, nshell, rule):
+    """counts_triangles (one convolution and one histogram pass per pair) against direct enumeration
+    of the closed triangles and against counts_exact, bit for bit, including zero-count bins and
+    grids where closures wrap (16^3 with shells up to 6.5)."""
+    e = fieldgen.unit_edges(nshell, width)
+    bins = oracle.enumerate_bins(e, 3, oracle.RULE_ALL_SORTED if rule == "all" else oracle.RULE_POLYGON)
+    tri = oracle.counts_triangles(N, e, bins)
+    assert np.array_equal(tri, oracle.counts_exact(N, e, 3, bins))
+    if N <= 16:
+        _, cnt = oracle.direct_sample(None, e, 3, bins, N=N)
+        assert np.array_equal(tri, cnt)
+    if rule == "all":
+        assert (tri == 0).any() and (tri > 0).any()
+
+
+def test_golden_benchmark_counts_hold_on_the_256cube_grid():
+    """tests/golden/counts_n3_64shells.txt was computed on a 200^3 grid (no closure of shells up to
+    64.5 wraps on any grid above 192); re-derive the bins of two pairs on the 256^3 grid itself with
+    counts_exact."""
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "counts_n3_64shells.txt"),
+                      dtype=np.int64, comments="#")
+    sel = rows[((rows[:, 0] == 64) & (rows[:, 1] == 63)) | ((rows[:, 0] == 41) & (rows[:, 1] == 23))]
+    assert len(sel) > 60
+    e = fieldgen.unit_edges(64)
+    got = oracle.counts_exact(256, e, 3, sel[:, :3].astype(np.int32))
+    assert np.array_equal(got, sel[:, 3])
+
+
 def dp_counts(N, edges, bins):
     """Closed n-gon counts by dynamic programming over partial sums of grid modes (no FFT): the
     histogram of q_1 + ... + q_t (mod N) grows one shell at a time; the count is its value at 0."""
