@@ -163,6 +163,35 @@ poly_status poly_trispectrum_disconnected(poly_plan plan, const void* delta_x, d
                                           void* stream);
 
 /*
+ * Full-shape trispectrum of one shell quadruple (Eq. Tkfull, Sec. 2.1; the
+ * paper leaves it as future work): the closed quadrilaterals
+ * q1 + q2 + q3 + q4 = 0 (mod N), q_t in S_{k_t}, split by their diagonals
+ * p1 = q1 - q2 and p2 = q1 - q3 into bins j: dedges[j]^2 <= |p|^2 <
+ * dedges[j+1]^2 (components of p: differences of the signed representatives
+ * -N/2 .. N/2-1; p = 0 falls in bin 0 when dedges[0] = 0):
+ *   T[j1 * ndiag + j2] = c_4 sum Re prod_t dhat(q_t) / count[j1][j2]
+ * (0 where the count is 0), c_4 = V^3/N^12 as for B_b.  Summed over diagonal
+ * bins that cover every |p|, c_4^{-1} T * count and count give the
+ * angle-averaged trispectrum's sums and counts of that bin.
+ * Any plan (any order, precision and multipole) serves: its shells, grid and
+ * forward transform are used.  delta_x: device, N^3 real of the plan's input
+ * type, or NULL for counts only (then T_out and scale_or_null must be NULL).
+ * k: host, 4 shell numbers, 1-based, in [1, nshell], any order.  ndiag in
+ * [1, 128]; dedges: host, ndiag + 1 finite, non-negative, strictly increasing.
+ * T_out, counts_out (int64), scale_or_null: device, ndiag^2 each, or NULL (at
+ * least one given; none may alias another or delta_x).  scale_or_null
+ * receives c_4 sum prod_t |dhat(q_t)| / count (the scale of the rounding error
+ * of T).  Products and per-bin partial sums are in the plan's precision
+ * (FP32 for FP32 and split-BF16 plans), accumulation in FP64; counts are
+ * exact.  Work grows as |S_k1| |S_k2| |S_k3|: more than 4.4e12 triples is
+ * POLY_ERR_UNSUPPORTED.  Grows a per-plan scratch buffer on demand (freed
+ * with the plan) and overwrites the plan's spectrum workspace
+ * (stream-ordered with poly_estimate).  Asynchronous on `stream`.
+ */
+poly_status poly_trispectrum_full(poly_plan plan, const void* delta_x, const int32_t* k, int ndiag, const double* dedges,
+                                  double* T_out, int64_t* counts_out, double* scale_or_null, void* stream);
+
+/*
  * The same as poly_estimate with HOST buffers: copies delta_x (host, N^3 real)
  * to the device, estimates, copies B_b to out (host, nbins double) and
  * synchronises `stream` before returning.

@@ -70,7 +70,7 @@ def _load():
         L.orc_gradient.argtypes = [i32, f64, P, i32, P, i32, i64, P, P, P, P]
         L.orc_disconnected.argtypes = [i32, f64, P, i32, P, i64, P, P, P, P]
         L.orc_estimate_ell.argtypes = [i32, f64, P, i32, P, i32, i32, i64, P, P, P, P]
-        L.orc_trispectrum_full.argtypes = [i32, P, i32, P, P, i32, P, P, P]
+        L.orc_trispectrum_full.argtypes = [i32, P, i32, P, P, i32, P, P, P, P]
         _lib = L
     return _lib
 
@@ -215,23 +215,28 @@ def estimate_ell(delta, L: float, edges, order: int, ell: int, bins) -> dict:
 def trispectrum_full(delta, L: float, edges, k, dedges, N: int | None = None) -> dict:
     """Full-shape trispectrum of one bin k = (k1, k2, k3, k4) (Eq. Tkfull): the closed quadrilaterals split
     by their diagonals |q1 - q2| and |q1 - q3| into the bins of `dedges`.  Returns S and counts
-    [ndiag, ndiag] and T = (V^3/N^12) S / (N^3 count) (0 where count = 0).  delta=None: counts only."""
+    [ndiag, ndiag], T = (V^3/N^12) S / (N^3 count) (0 where count = 0) and `scale`, the same
+    normalisation of A = N^3 sum prod_t |dhat(q_t)| (the size rounding errors in T are measured
+    against).  delta=None: counts only."""
     e = np.ascontiguousarray(edges, dtype=np.float64)
     de = np.ascontiguousarray(dedges, dtype=np.float64)
     kk = np.ascontiguousarray(k, dtype=np.int32)
     nd = de.size - 1
     S = np.zeros((nd, nd))
+    A = np.zeros((nd, nd))
     C = np.zeros((nd, nd), dtype=np.int64)
     if delta is None:
         assert N is not None
-        _check(_load().orc_trispectrum_full(int(N), None, e.size - 1, _p(e), _p(kk), nd, _p(de), None, _p(C)))
+        _check(_load().orc_trispectrum_full(int(N), None, e.size - 1, _p(e), _p(kk), nd, _p(de), None, None, _p(C)))
     else:
         d = np.ascontiguousarray(delta, dtype=np.float64)
         N = d.shape[0]
-        _check(_load().orc_trispectrum_full(N, _p(d), e.size - 1, _p(e), _p(kk), nd, _p(de), _p(S), _p(C)))
+        _check(_load().orc_trispectrum_full(N, _p(d), e.size - 1, _p(e), _p(kk), nd, _p(de), _p(S), _p(A), _p(C)))
     n3 = float(N) ** 3
-    T = np.where(C > 0, (L ** 3) ** 3 / n3 ** 4 * S / (n3 * np.maximum(C, 1)), 0.0)
-    return {"S": S, "counts": C, "T": T}
+    norm = (L ** 3) ** 3 / n3 ** 4
+    T = np.where(C > 0, norm * S / (n3 * np.maximum(C, 1)), 0.0)
+    scale = np.where(C > 0, norm * A / (n3 * np.maximum(C, 1)), 0.0)
+    return {"S": S, "counts": C, "T": T, "scale": scale}
 
 
 def disconnected(delta, L: float, edges, bins, counts):

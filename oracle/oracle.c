@@ -1091,6 +1091,8 @@ int orc_direct_sample(int N, const double* delta /* NULL: counts only */, int ns
 /*   count[j1][j2] = the number of those quadrilaterals,                      */
 /* over q_t in S_{k_t} with q1 + q2 + q3 + q4 = 0 (mod N); the components of  */
 /* p are differences of the signed (-N/2 .. N/2 - 1) representatives.        */
+/*   A[j1][j2]     = N^3 sum prod_t |dhat(q_t)|  (the scale of rounding       */
+/*                   errors in S, for error bars; optional)                  */
 /* Summed over diagonal bins that cover every |p| they give S_b and count_b   */
 /* of the angle-averaged trispectrum.  Direct enumeration over q1, q2, q3.    */
 /* `delta` may be NULL (counts only).                                         */
@@ -1104,6 +1106,7 @@ typedef struct {
     int32_t nm[4];
     int k4;
     double* S;   /* [256][ndiag * ndiag] */
+    double* A;   /* [256][ndiag * ndiag] */
     int64_t* C;  /* [256][ndiag * ndiag] */
 } tfull_ctx;
 
@@ -1119,6 +1122,7 @@ static void tfull_range(void* vctx, int64_t begin, int64_t end, int tid) {
     tfull_ctx* c = (tfull_ctx*)vctx;
     const int N = c->N, nd = c->ndiag;
     double* S = c->S + (size_t)tid * nd * nd;
+    double* A = c->A + (size_t)tid * nd * nd;
     int64_t* C = c->C + (size_t)tid * nd * nd;
     for (int64_t a = begin; a < end; a++) {
         const int32_t i1 = c->modes[0][a];
@@ -1147,6 +1151,8 @@ static void tfull_range(void* vctx, int64_t begin, int64_t end, int tid) {
                     const double ar = f1.re * f2.re - f1.im * f2.im, ai = f1.re * f2.im + f1.im * f2.re;
                     const double br = f3.re * f4.re - f3.im * f4.im, bi = f3.re * f4.im + f3.im * f4.re;
                     S[j1 * nd + j2] += ar * br - ai * bi;
+                    A[j1 * nd + j2] += hypot(f1.re, f1.im) * hypot(f2.re, f2.im) * hypot(f3.re, f3.im) *
+                                       hypot(f4.re, f4.im);
                 }
             }
         }
@@ -1154,7 +1160,7 @@ static void tfull_range(void* vctx, int64_t begin, int64_t end, int tid) {
 }
 
 int orc_trispectrum_full(int N, const double* delta, int nshell, const double* edges, const int32_t* k, int ndiag,
-                         const double* dedges, double* S, int64_t* counts) {
+                         const double* dedges, double* S, double* A, int64_t* counts) {
     if (N < 2 || ndiag < 1 || !k) return fail(-1, "orc_trispectrum_full: bad args");
     for (int t = 0; t < 4; t++)
         if (k[t] < 1 || k[t] > nshell) return fail(-1, "orc_trispectrum_full: bin shell out of range");
@@ -1169,8 +1175,9 @@ int orc_trispectrum_full(int N, const double* delta, int nshell, const double* e
     int32_t* smap = (int32_t*)malloc(sizeof(int32_t) * n3);
     double* dhat = delta ? (double*)malloc(sizeof(double) * 2 * n3) : NULL;
     c.S = (double*)calloc((size_t)256 * ndiag * ndiag, sizeof(double));
+    c.A = (double*)calloc((size_t)256 * ndiag * ndiag, sizeof(double));
     c.C = (int64_t*)calloc((size_t)256 * ndiag * ndiag, sizeof(int64_t));
-    int rc = (!de2 || !smap || (delta && !dhat) || !c.S || !c.C) ? fail(-2, "orc_trispectrum_full: out of memory")
+    int rc = (!de2 || !smap || (delta && !dhat) || !c.S || !c.A || !c.C) ? fail(-2, "orc_trispectrum_full: out of memory")
                                                                  : orc_shell_map(N, nshell, edges, smap);
     for (int j = 0; j <= ndiag && !rc; j++) de2[j] = dedges[j] * dedges[j];
     if (!rc && delta) rc = orc_forward(N, delta, dhat);
@@ -1193,13 +1200,15 @@ int orc_trispectrum_full(int N, const double* delta, int nshell, const double* e
         c.k4 = k[3] - 1;
         par_for(c.nm[0], tfull_range, &c);
         for (int j = 0; j < ndiag * ndiag; j++) {
-            double sv = 0.0;
+            double sv = 0.0, av = 0.0;
             int64_t cv = 0;
             for (int t = 0; t < 256; t++) {
                 sv += c.S[(size_t)t * ndiag * ndiag + j];
+                av += c.A[(size_t)t * ndiag * ndiag + j];
                 cv += c.C[(size_t)t * ndiag * ndiag + j];
             }
             if (S) S[j] = (double)n3 * sv;
+            if (A) A[j] = (double)n3 * av;
             if (counts) counts[j] = cv;
         }
     }
@@ -1208,6 +1217,7 @@ int orc_trispectrum_full(int N, const double* delta, int nshell, const double* e
     free(smap);
     free(dhat);
     free(c.S);
+    free(c.A);
     free(c.C);
     return rc;
 }

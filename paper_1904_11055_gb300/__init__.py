@@ -33,7 +33,7 @@ ABI_SYMBOLS = ("poly_plan_create", "poly_plan_nbins", "poly_plan_bins", "poly_pl
                "poly_status_string", "poly_last_error", "poly_debug_fail_alloc_after", "poly_plan_set_timing",
                "poly_plan_stats", "poly_estimate_noalloc", "poly_plan_tune", "poly_plan_set_config",
                "poly_trispectrum_disconnected", "poly_plan_create_multipole", "poly_plan_bin_wraps",
-               "poly_plan_device_bytes")
+               "poly_plan_device_bytes", "poly_trispectrum_full")
 
 
 class poly_stats(ctypes.Structure):
@@ -81,6 +81,7 @@ def load_library():
     L.poly_plan_tune.argtypes = [P, P, ctypes.POINTER(i32), ctypes.POINTER(f64), P]
     L.poly_plan_set_config.argtypes = [P, i32]
     L.poly_trispectrum_disconnected.argtypes = [P, P, P, P, P]
+    L.poly_trispectrum_full.argtypes = [P, P, P, i32, P, P, P, P, P]
     L.poly_last_error.argtypes = []
     L.poly_debug_fail_alloc_after.argtypes = [i32]
     L.poly_debug_fail_alloc_after.restype = None
@@ -167,6 +168,17 @@ def poly_trispectrum_disconnected(plan: int, delta_ptr: int, out_ptr: int, power
                                   stream: int | None) -> None:
     _check(load_library().poly_trispectrum_disconnected(plan, delta_ptr, out_ptr, power_ptr, stream),
            "poly_trispectrum_disconnected")
+
+
+def poly_trispectrum_full(plan: int, delta_ptr: int | None, k, dedges, T_ptr: int | None, counts_ptr: int | None,
+                          scale_ptr: int | None, stream: int | None) -> None:
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    de = np.ascontiguousarray(dedges, dtype=np.float64)
+    if kk.shape != (4,) or de.ndim != 1 or de.size < 2:
+        raise ValueError("k must hold 4 shell numbers and dedges at least 2 edges")
+    _check(load_library().poly_trispectrum_full(plan, delta_ptr, kk.ctypes.data_as(ctypes.c_void_p), de.size - 1,
+                                                de.ctypes.data_as(ctypes.c_void_p), T_ptr, counts_ptr, scale_ptr,
+                                                stream), "poly_trispectrum_full")
 
 
 def poly_estimate_batched(plans, field_ptrs, out_ptrs, stream: int | None) -> None:
@@ -323,6 +335,26 @@ class Plan:
         poly_trispectrum_disconnected(self.handle, delta.data_ptr(), out.data_ptr(), pw.data_ptr() if power else None,
                                       _stream_handle(stream))
         return (out, pw) if power else out
+
+    def trispectrum_full(self, delta, k, dedges, scale: bool = False, stream=None):
+        """Full-shape trispectrum of the shell quadruple k (1-based) split by the diagonals |q1 - q2| and
+        |q1 - q3| into the bins of dedges (Eq. Tkfull).  Returns (T, counts) [and scale], each
+        [ndiag, ndiag] on the device; delta=None gives the counts alone."""
+        import torch
+
+        nd = len(dedges) - 1
+        dev = delta.device if delta is not None else torch.device("cuda", torch.cuda.current_device())
+        if delta is not None:
+            _require(delta, self.real_dtype, self.N ** 3, "delta")
+        T = torch.empty((nd, nd), dtype=torch.float64, device=dev) if delta is not None else None
+        C = torch.empty((nd, nd), dtype=torch.int64, device=dev)
+        sc = torch.empty((nd, nd), dtype=torch.float64, device=dev) if scale else None
+        poly_trispectrum_full(self.handle, delta.data_ptr() if delta is not None else None, k, dedges,
+                              T.data_ptr() if T is not None else None, C.data_ptr(),
+                              sc.data_ptr() if scale else None, _stream_handle(stream))
+        if delta is None:
+            return C
+        return (T, C, sc) if scale else (T, C)
 
     def sync(self, stream=None):
         poly_plan_sync(self.handle, _stream_handle(stream))

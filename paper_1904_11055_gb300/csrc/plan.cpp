@@ -820,6 +820,19 @@ poly_status poly_trispectrum_disconnected(poly_plan p, const void* delta_x, doub
     return s;
 }
 
+poly_status poly_trispectrum_full(poly_plan p, const void* delta_x, const int32_t* k, int ndiag, const double* dedges,
+                                  double* T_out, int64_t* counts_out, double* scale_or_null, void* stream) {
+    if (!p) return set_error(POLY_ERR_ARG, "NULL plan");
+    int prev;
+    PS_TRY(enter(p, &prev));
+    poly_status s = guarded([&] {
+        return ps_trispectrum_full_impl(p, delta_x, k, ndiag, dedges, T_out, counts_out, scale_or_null,
+                                        (cudaStream_t)stream);
+    });
+    leave(p, prev);
+    return s;
+}
+
 static int poly_diag_fields_impl(void* plan, const void* delta_x, void* fields_host, void* stream) {
     PsPlan* p = (PsPlan*)plan;
     if (!p || !delta_x || !fields_host) return set_error(POLY_ERR_ARG, "NULL argument");

@@ -76,6 +76,9 @@ struct poly_plan_s {
     // disconnected part of the trispectrum (allocated on first use)
     int32_t* d_bins = nullptr;     // nbins x order, 1-based shells
     double* d_shell_power = nullptr;
+    // full-shape trispectrum scratch (mode lists, diagonal table, accumulators; grown on demand)
+    void* d_tf = nullptr;
+    size_t tf_bytes = 0;
     // tensor-core contraction: state, and its tunable shape (poly_plan_tune)
     TcState* tc = nullptr;
     int tc_max_mt = 4;    // largest number of M tiles per CTA group
@@ -121,6 +124,9 @@ poly_status ps_check_device_error(PsPlan* p);
 // adjoint.cu
 void ps_adj_free(PsPlan* p);
 int ps_adj_device_error(PsPlan* p);  // nonzero: the tensor-core adjoint kernel timed out
+// trispectrum_full.cu
+poly_status ps_trispectrum_full_impl(PsPlan* p, const void* delta, const int32_t* k, int nd, const double* dedges,
+                                     double* T_out, int64_t* counts_out, double* scale_out, cudaStream_t st);
 poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, void* dL_ddelta, cudaStream_t st);
 // batched.cpp
 poly_status ps_batched_impl(const poly_plan* plans, const void* const* fields, double* const* outs, int count,

@@ -299,6 +299,7 @@ def test_full_shape_trispectrum_matches_enumeration():
     f = np.fft.fftfreq(N) * N
     modes = [np.argwhere(smap == s) for s in range(2)]
     S = np.zeros((5, 5))
+    A = np.zeros((5, 5))
     C = np.zeros((5, 5), dtype=np.int64)
     for q1 in modes[k[0] - 1]:
         for q2 in modes[k[1] - 1]:
@@ -314,9 +315,13 @@ def test_full_shape_trispectrum_matches_enumeration():
                     continue
                 C[j1, j2] += 1
                 S[j1, j2] += np.real(dh[tuple(q1)] * dh[tuple(q2)] * dh[tuple(q3)] * dh[tuple(q4)])
+                A[j1, j2] += np.abs(dh[tuple(q1)] * dh[tuple(q2)] * dh[tuple(q3)] * dh[tuple(q4)])
     r = oracle.trispectrum_full(d, L, e, k, de)
     assert np.array_equal(r["counts"], C)
     assert np.allclose(r["S"], N ** 3 * S, rtol=1e-10, atol=1e-10 * np.abs(N ** 3 * S).max())
+    norm = (L ** 3) ** 3 / float(N) ** 12
+    assert np.allclose(r["scale"], np.where(C > 0, norm * A / np.maximum(C, 1), 0.0), rtol=1e-10, atol=0.0)
+    assert np.all(np.abs(r["T"]) <= r["scale"] * (1 + 1e-12))
     assert C.sum() > 0 and np.count_nonzero(C) > 3
 
 
