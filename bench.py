@@ -23,6 +23,7 @@ import subprocess
 import sys
 import threading
 import time
+from types import SimpleNamespace
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -43,6 +44,12 @@ def set_workload(n: int, nshell: int, order: int, width: float = 1.0, ell: int =
 SAMPLE_SHELLS = (59, 60, 61, 62, 63, 64)  # CPU baseline sample: the bins among these shells
 
 
+TC_SOURCES = ["contract_tc.cu", "tc.cuh"]
+CC_SOURCES = ["contract_cc.cu"]
+FIELD_SOURCES = ["fields_impl.cuh", "fields_f32.cu", "fft.cuh"]
+ADJ_SOURCES = ["adjoint_tc.cu", "tc.cuh"]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -60,12 +67,17 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, src_files):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+def workload_key(n: int, nshell: int, order: int, width: float = 1.0, ell: int = 0, prec: str = "") -> str:
+    return f"n{order}-{n}cube-{nshell}x{width:g}" + (f"-ell{ell}" if ell else "") + (f"-{prec}" if prec else "")
+
+
+def traffic_for(kernel: str, src_files, key: str):
+    """DRAM bytes per launch from a committed ncu summary of this kernel on this workload, if it was
+    captured from the current source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f).get(kernel)
+            rec = json.load(f).get(f"{kernel}@{key}")
     except Exception:
         return None
     if not rec or rec.get("source_hash") != source_hash(*src_files):
@@ -146,9 +158,15 @@ def cpu_baseline(delta_f32):
     oracle.set_threads(1)
     d1, e1 = fieldgen.field("gaussian_cut16", 64, 1, np.float64), fieldgen.unit_edges(16)
     t1 = time.perf_counter()
-    nb1 = len(oracle.estimate(d1, L, e1, 3)["B"])
+    ref64 = oracle.estimate(d1, L, e1, 3)
+    nb1 = len(ref64["B"])
     dt1 = time.perf_counter() - t1
     oracle.set_threads(cores)
+    t2 = time.perf_counter()
+    oracle.estimate(d1, L, e1, 3)
+    dt2 = time.perf_counter() - t2
+    cpu_baseline.ref64 = ref64
+    cpu_baseline.rate64 = {"one_thread": nb1 / dt1, "all_cores": nb1 / dt2, "cores": cores}
     return {"value": len(sel) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(sel)} bins among shells {SAMPLE_SHELLS[0]}-{SAMPLE_SHELLS[-1]} of the 256^3 field "
                       f"(full forward FFT, 6 shell + 6 counting fields, FP64), {dt:.1f} s",
@@ -250,6 +268,181 @@ def time_precision(ps, torch, plan, d, args, flush_buf, dist_ok):
     return step_ms, mean, launches
 
 
+def _contract_roofline(prec, useful_flops, ms_contract, peaks, fma, peak_src, burst=False):
+    """Roofline of the contraction stage: tensor pipe (split-BF16) or CUDA-core FMA (FP32, FP64)."""
+    achieved = useful_flops / (ms_contract * 1e-3) / 1e12
+    if prec == "split_bf16":
+        key = "bf16_tflops" if burst else "bf16_tflops_sustained"
+        peak = peaks.get(key, peaks.get("bf16_tflops"))
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"bf16 dense {'burst' if burst else 'sustained'}, {peak_src}"}
+    f = fma["f64" if prec == "fp64" else "f32"]["tflops"]
+    return {"bound": "alu", "achieved": achieved, "peak": f, "unit": "TFLOP/s", "frac": achieved / f,
+            "peak_source": f"{'FP64' if prec == 'fp64' else 'FP32'} FMA, measured by poly_diag_fma_peak in this run"}
+
+
+def _median_ms(torch, fn, reps, warm=1):
+    for _ in range(warm):
+        fn()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def config1_record(ps, torch, np, peaks, fma, peak_src, flush_buf):
+    """64^3 Gaussian field (P ~ k^-1.5 cut above 16 k_F, seed 1), 16 unit shells, n = 3, all 508 bins: the
+    plain FP64 method and the FP32 / split-BF16 paths, each against the FP64 oracle on every bin."""
+    from types import SimpleNamespace
+
+    import fieldgen
+
+    e1 = fieldgen.unit_edges(16)
+    d1 = fieldgen.field("gaussian_cut16", 64, 1, np.float64)
+    ref = getattr(cpu_baseline, "ref64", None)
+    rec = {"workload": "bispectrum, 64^3 Gaussian field P~k^-1.5 cut above 16 k_F (seed 1), 16 unit shells, n=3, "
+                       "all polygon bins", "precisions": {},
+           "l2": "256 MiB buffer written between timed steps (L2 flushed)"}
+    c_n = (L ** 3) ** 2 / float(64 ** 3) ** 3
+    for prec in ("fp64", "fp32", "split_bf16"):
+        plan = ps.Plan(64, L, 3, e1, prec)
+        d = torch.from_numpy(d1).cuda().to(plan.real_dtype)
+        step_ms, stage, launches = time_precision(ps, torch, plan, d, SimpleNamespace(steps=10, warmup=3), flush_buf,
+                                                  False)
+        B = time_precision.last_out
+        ms = statistics.median(step_ms)
+        r = {"ms_per_step": ms, "value": plan.nbins / (ms * 1e-3), "unit": "configs/s", "stage_ms": stage,
+             "gpu_launches": launches, "steps": 10, "warmup": 3,
+             "roofline": _contract_roofline(prec, plan.nbins * 64 ** 3 * 3, stage["ms_contract"], peaks, fma,
+                                            peak_src, burst=True)}
+        if ref is not None:
+            r["error_vs_oracle"] = float(np.max(np.abs(B - ref["B"]) / (c_n * ref["scale"])))
+            r["counts_bit_exact"] = bool(np.array_equal(plan.counts, ref["counts"]))
+        rec["precisions"][prec] = r
+        rec["nbins"] = plan.nbins
+        plan.close()
+    if ref is not None:
+        rec["cpu_oracle"] = {"unit": "configs/s", "kind": "oracle", "sample": "all bins, counts included",
+                             **cpu_baseline.rate64}
+    return rec
+
+
+def config3_record(ps, torch, np, peaks, fma, peak_src, flush_buf, delta_np, d):
+    """The trispectrum as the paper defines it: 256^3 lognormal field, 32 shells of width 1.5 k_F, n = 4, split-BF16
+    and FP32 paths, error against the FP64 oracle on the bins among the two outermost shells; the disconnected part;
+    and the full-shape trispectrum (Eq. Tkfull) of bin (10, 10, 10, 10) with diagonal bins of width 1.5 k_F."""
+    from types import SimpleNamespace
+
+    import fieldgen
+    import oracle
+
+    e3 = fieldgen.unit_edges(32, 1.5)
+    allb = oracle.enumerate_bins(e3, 4)
+    sel = np.array([i for i, b in enumerate(allb) if set(b.tolist()) <= {31, 32}])
+    t0 = time.perf_counter()
+    oracle.set_threads(os.cpu_count() or 1)
+    ref = oracle.estimate(delta_np.astype(np.float64), L, e3, 4, bins=allb[sel])
+    t_or = time.perf_counter() - t0
+    c_n = (L ** 3) ** 3 / float(256 ** 3) ** 4
+    rec = {"workload": "trispectrum, 256^3 lognormal field (seed 2), 32 shells of width 1.5 k_F up to 48 k_F, n=4",
+           "precisions": {}, "l2": "256 MiB buffer written between timed steps (L2 flushed)",
+           "cpu_oracle": {"value": len(sel) / t_or, "unit": "configs/s", "kind": "oracle", "cores": os.cpu_count(),
+                          "sample": f"{len(sel)} bins among shells 31-32 (full forward FFT, FP64), {t_or:.1f} s"}}
+    kfull = (10, 10, 10, 10)
+    for prec, steps in (("split_bf16", 10), ("fp32", 3)):
+        torch.cuda.synchronize()
+        tp = time.perf_counter()
+        plan = ps.Plan(256, L, 4, e3, prec)
+        torch.cuda.synchronize()
+        plan_ms = (time.perf_counter() - tp) * 1e3
+        if prec == "split_bf16":
+            plan.tune(d)
+        step_ms, stage, launches = time_precision(ps, torch, plan, d, SimpleNamespace(steps=steps, warmup=3),
+                                                  flush_buf, False)
+        B = time_precision.last_out
+        ms = statistics.median(step_ms)
+        roof = _contract_roofline(prec, plan.nbins * 256 ** 3 * 4, stage["ms_contract"], peaks, fma, peak_src)
+        if prec == "split_bf16":
+            roof["traffic"] = traffic_for("tc_contract", TC_SOURCES, workload_key(256, 32, 4, 1.5))
+        r = {"ms_per_step": ms, "value": plan.nbins / (ms * 1e-3), "unit": "configs/s", "nbins": plan.nbins,
+             "steps": steps, "warmup": 3, "stage_ms": stage, "gpu_launches": launches, "roofline": roof,
+             "plan_ms": plan_ms,
+             "error_vs_oracle": float(np.max(np.abs(B[sel] - ref["B"]) / (c_n * ref["scale"]))),
+             "counts_bit_exact_on_sample": bool(np.array_equal(plan.counts[sel], ref["counts"]))}
+        if prec == "split_bf16":
+            r["disconnected_ms"] = _median_ms(torch, lambda: plan.disconnected(d), 3)
+            # full-shape trispectrum of one bin, diagonals |q1 - q2|, |q1 - q3| in bins of width 1.5 k_F
+            de = np.concatenate([[0.0], (np.arange(22) + 0.5) * 1.5])
+            out = {}
+
+            def full():
+                out["T"], out["C"], out["S"] = plan.trispectrum_full(d, kfull, de, scale=True)
+
+            fms = _median_ms(torch, full, 3)
+            C = out["C"].cpu().numpy()
+            T, S = out["T"].cpu().numpy(), out["S"].cpu().numpy()
+            b = int(np.flatnonzero((plan.bins == np.asarray(kfull)).all(axis=1))[0])
+            r["full_shape"] = {
+                "bin": list(kfull), "ndiag": int(len(de) - 1), "ms": fms, "quadrilaterals": int(C.sum()),
+                "quadrilaterals_per_s": float(C.sum()) / (fms * 1e-3),
+                "counts_sum_equals_count_b": bool(C.sum() == plan.counts[b]),
+                "sum_error_vs_estimate": float(abs((T * C).sum() - B[b] * plan.counts[b]) / (S * C).sum()),
+                "note": "poly_trispectrum_full on the same field and plan, device-timed median of 3; the sum over "
+                        "diagonal bins of T*count against B_b*count_b of the same step, in units of sum scale*count"}
+        rec["precisions"][prec] = r
+        plan.close()
+    return rec
+
+
+def config4_record(ps, torch, np):
+    """Checks of the hand-written adjoint at the sizes the oracle and finite differences reach: 64 voxels of a 64^3
+    field (16 unit shells, FP64 plan) by central differences, and the FP32 / split-BF16 / FP64 gradients of a 32^3
+    field (8 unit shells) against the FP64 oracle gradient."""
+    import fieldgen
+    import oracle
+
+    rec = {}
+    N, e = 64, fieldgen.unit_edges(16)
+    d = fieldgen.field("gaussian_cut16", N, 4, np.float64)
+    plan = ps.Plan(N, L, 3, e, "fp64")
+    w = np.random.default_rng(5).standard_normal(plan.nbins)
+    dev = torch.from_numpy(d).cuda()
+    wt = torch.from_numpy(w).cuda()
+    g = plan.backward(dev, wt).cpu().numpy().reshape(-1)
+    vox = np.random.default_rng(6).choice(N ** 3, size=64, replace=False)
+    h = 1e-3 * float(d.std())
+    flat = dev.view(-1)
+    worst = 0.0
+    for v in vox:
+        flat[v] += h
+        lp = float(torch.dot(plan.estimate(dev), wt))
+        flat[v] -= 2 * h
+        lm = float(torch.dot(plan.estimate(dev), wt))
+        flat[v] += h
+        worst = max(worst, abs((lp - lm) / (2 * h) - g[v]) / np.abs(g).max())
+    plan.close()
+    rec["finite_differences_64cube"] = {"voxels": 64, "max_error_over_max_grad": worst, "precision": "fp64"}
+    N, e = 32, fieldgen.unit_edges(8)
+    d = fieldgen.field("lognormal", N, 9, np.float64)
+    errs = {}
+    for prec in ("fp64", "fp32", "split_bf16"):
+        plan = ps.Plan(N, 500.0, 3, e, prec)
+        w = np.random.default_rng(7).standard_normal(plan.nbins)
+        if prec == "fp64":
+            ref = oracle.gradient(d, 500.0, e, 3, plan.bins, plan.counts, w)
+        dt = torch.from_numpy(d).cuda().to(plan.real_dtype)
+        g = plan.backward(dt, torch.from_numpy(w).cuda()).cpu().numpy().astype(np.float64)
+        errs[prec] = float(np.abs(g - ref).max() / np.abs(ref).max())
+        plan.close()
+    rec["oracle_gradient_32cube"] = {"max_error_over_max_grad": errs, "shells": 8}
+    return rec
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -269,6 +462,7 @@ def run_ours(args):
     if dist_ok:
         torch.distributed.barrier()
     peaks, peak_src = load_peaks()
+    fma = {"f32": ps.diag_fma_peak(False), "f64": ps.diag_fma_peak(True)}  # measured CUDA-core peaks
 
     delta_np = fieldgen.field("lognormal", N, sharding.field_seed(SEED, rank), np.float32)
     d = torch.from_numpy(delta_np).cuda()
@@ -291,7 +485,11 @@ def run_ours(args):
             raise
         # the contraction's launch shape, tuned once on this field (a user's plan.tune call; it reorders only
         # the final FP64 sums), outside the timed steps
-        tuned = plan.tune(d) if prec == "split_bf16" else (0, 0.0)
+        if prec == "split_bf16" and args.tc_config >= 0:
+            plan.set_config(args.tc_config)  # a fixed shape (0: the plan's default), e.g. for profiling runs
+            tuned = (args.tc_config, 0.0)
+        else:
+            tuned = plan.tune(d) if prec == "split_bf16" else (0, 0.0)
         step_ms, stage, launches = None, None, None
         with ClockSampler(local) as clk:
             step_ms, stage, launches = time_precision(ps, torch, plan, d, args, flush_buf, dist_ok)
@@ -314,22 +512,23 @@ def run_ours(args):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             achieved = useful_flops / (stage["ms_contract"] * 1e-3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": traffic_for("contract_tc", ["contract_tc.cu", "tc.cuh"]), "kernel": "tc_contract",
+                    "traffic": traffic_for("tc_contract", TC_SOURCES, workload_key(N, NSHELL, ORDER, WIDTH, ELL)),
+                    "kernel": "tc_contract",
                     "peak_source": f"bf16 dense sustained, {peak_src}"}
         else:
-            mhz = peaks.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+            peak = fma["f32"]["tflops"]
             achieved = useful_flops / (stage["ms_contract"] * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": traffic_for("contract_cc", ["contract_cc.cu"]), "kernel": "contract_cc_kernel",
-                    "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz ({peak_src} max clock)"}
+                    "traffic": traffic_for("contract_cc", CC_SOURCES, workload_key(N, NSHELL, ORDER, WIDTH, ELL, prec)),
+                    "kernel": "contract_cc_kernel",
+                    "peak_source": "FP32 FMA, measured by poly_diag_fma_peak in this run"}
         roof["executed_tflops"] = stage["contract_flops"] / (stage["ms_contract"] * 1e-3) / 1e12
         roof["useful_over_executed"] = useful_flops / stage["contract_flops"]
         field_bytes = NSHELL * n3 * 4 + n3 * 4
         fields_roof = {"bound": "hbm", "achieved": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9,
                        "peak": peaks["hbm_gbs"], "unit": "GB/s",
                        "frac": field_bytes / (stage["ms_fields"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                       "traffic": traffic_for("inv_plane", ["fields_impl.cuh", "fields_f32.cu", "fft.cuh"]),
+                       "traffic": traffic_for("fields", FIELD_SOURCES, workload_key(N, NSHELL, ORDER, WIDTH, ELL)),
                        "kernel": "fields stage: xpass_kernel + inv_plane_kernel (8- and 16-warp launches), bytes per step",
                        "peak_source": peak_src}
         # the adjoint (dL/d delta for L = sum_b w_b B_b), device-timed, on this rank's field
@@ -411,6 +610,15 @@ def run_ours(args):
             p: float(np.max(np.abs(r["B"][sel] - ref["B"]) / (c_n * ref["scale"]))) for p, r in results.items()
             if "B" in r}
         line["error_vs_oracle"]["bins"] = int(len(sel))
+    if world == 1 and not args.no_configs and (N, NSHELL, ORDER, WIDTH) == (256, 64, 3, 1.0) and ELL == 0:
+        line["configs"] = {
+            "1_bispectrum_64cube": config1_record(ps, torch, np, peaks, fma, peak_src, flush_buf),
+            "3_trispectrum_256cube": config3_record(ps, torch, np, peaks, fma, peak_src, flush_buf, delta_np, d),
+            "4_gradient": {"backward_ms_256cube": {p: r.get("backward_ms") for p, r in results.items()},
+                           **config4_record(ps, torch, np)},
+            "5_mocks": mocks_record(SimpleNamespace(steps=3, warmup=3)),
+        }
+    line["fma_peak_measured"] = fma
     print(json.dumps(line), flush=True)
     if dist_ok:
         torch.distributed.destroy_process_group()
@@ -424,6 +632,13 @@ MOCK_METRIC = ("mock realisations/s: 512 lognormal mocks (256 x 128^3, 128 x 96^
 
 def run_mocks(args):
     """Batched mixed-size mocks: one poly_estimate_batched (captured graph) per step."""
+    line = mocks_record(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def mocks_record(args):
+    """The batched-mocks workload; returns the JSON record on rank 0 (None on other ranks)."""
     import numpy as np
     import torch
 
@@ -490,8 +705,10 @@ def run_mocks(args):
     t_batch, t_seq = sharding.max_over_ranks(t_batch), sharding.max_over_ranks(t_seq)
     if world > 1:
         torch.distributed.destroy_process_group()
+    for p in plans.values():
+        p.close()
     if rank != 0:
-        return
+        return None
     line = {"metric": MOCK_METRIC, "value": rate_batch, "unit": "realisations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
@@ -503,7 +720,7 @@ def run_mocks(args):
             "sequential": {"value": rate_seq, "ms_per_step": t_seq},
             "speedup_vs_sequential": t_seq / t_batch, "bit_identical_to_sequential": identical,
             "clocks": clocks.summary()}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -514,6 +731,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "split_bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-config", type=int, default=-1,
+                    help="split-BF16 contraction shape code instead of tuning (0: the plan's default)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the sub-records of the other workloads (64^3 FP64, trispectrum, gradient, mocks)")
     ap.add_argument("--N", type=int, default=N, help="grid size (default: the metric workload)")
     ap.add_argument("--nshell", type=int, default=NSHELL)
     ap.add_argument("--order", type=int, default=ORDER)

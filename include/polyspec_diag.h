@@ -41,6 +41,17 @@ int poly_diag_tc_gemm(const uint16_t* A_host, const uint16_t* B_host, int N, flo
 int poly_diag_stalled_wait(double* ms_out);
 
 /*
+ * Peak FMA rate of the CUDA cores of the current device, measured: every
+ * thread of 16 blocks of 256 threads per SM runs 8 independent FMA chains
+ * (FP32, or FP64 when is_double) for `iters` steps; the kernel is timed with
+ * CUDA events after one untimed launch.  tflops_out receives
+ * 2 x threads x 8 x iters / time in TFLOP/s; ms_out (nullable) the kernel's
+ * duration.  iters in [1, 2^24].  Returns 0, 1 for bad arguments, 4 on a CUDA
+ * error.  Synchronises the device.
+ */
+int poly_diag_fma_peak(int is_double, int iters, double* tflops_out, double* ms_out);
+
+/*
  * The plan's shell fields of delta_x (device, N^3 real of the plan's type):
  * runs the forward transform and the shell-field stage exactly as
  * poly_estimate does, synchronises `stream`, and copies the fields to

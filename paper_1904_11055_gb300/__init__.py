@@ -240,6 +240,19 @@ def poly_estimate_noalloc(N: int, L: float, edges, delta_ptr: int, counts: np.nd
            "poly_estimate_noalloc")
 
 
+def diag_fma_peak(is_double: bool = False, iters: int | None = None) -> dict:
+    """Measured peak FMA rate of the CUDA cores (poly_diag_fma_peak in include/polyspec_diag.h)."""
+    lib = load_library()
+    lib.poly_diag_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.poly_diag_fma_peak.restype = ctypes.c_int
+    it = iters if iters is not None else (4096 if is_double else 131072)
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib.poly_diag_fma_peak(int(bool(is_double)), int(it), ctypes.byref(tf), ctypes.byref(ms)),
+           "poly_diag_fma_peak")
+    return {"tflops": tf.value, "ms": ms.value, "iters": it, "dtype": "f64" if is_double else "f32"}
+
+
 def poly_status_string(status: int) -> str:
     return load_library().poly_status_string(int(status)).decode()
 
