@@ -71,9 +71,10 @@ def workload_key(n: int, nshell: int, order: int, width: float = 1.0, ell: int =
     return f"n{order}-{n}cube-{nshell}x{width:g}" + (f"-ell{ell}" if ell else "") + (f"-{prec}" if prec else "")
 
 
-def traffic_for(kernel: str, src_files, key: str):
+def traffic_for(kernel: str, src_files, key: str, config: int | None = None):
     """DRAM bytes per launch from a committed ncu summary of this kernel on this workload, if it was
-    captured from the current source (else None)."""
+    captured from the current source and, for the tensor-core contraction, at the same launch shape
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -81,6 +82,8 @@ def traffic_for(kernel: str, src_files, key: str):
     except Exception:
         return None
     if not rec or rec.get("source_hash") != source_hash(*src_files):
+        return None
+    if config is not None and rec.get("contraction_config") not in (None, config):
         return None
     return rec.get("bytes_per_launch")
 
@@ -360,18 +363,17 @@ def config3_record(ps, torch, np, peaks, fma, peak_src, flush_buf, delta_np, d):
         plan = ps.Plan(256, L, 4, e3, prec)
         torch.cuda.synchronize()
         plan_ms = (time.perf_counter() - tp) * 1e3
-        if prec == "split_bf16":
-            plan.tune(d)
+        code = plan.tune(d)[0] if prec == "split_bf16" else 0
         step_ms, stage, launches = time_precision(ps, torch, plan, d, SimpleNamespace(steps=steps, warmup=3),
                                                   flush_buf, False)
         B = time_precision.last_out
         ms = statistics.median(step_ms)
         roof = _contract_roofline(prec, plan.nbins * 256 ** 3 * 4, stage["ms_contract"], peaks, fma, peak_src)
         if prec == "split_bf16":
-            roof["traffic"] = traffic_for("tc_contract", TC_SOURCES, workload_key(256, 32, 4, 1.5))
+            roof["traffic"] = traffic_for("tc_contract", TC_SOURCES, workload_key(256, 32, 4, 1.5), code)
         r = {"ms_per_step": ms, "value": plan.nbins / (ms * 1e-3), "unit": "configs/s", "nbins": plan.nbins,
              "steps": steps, "warmup": 3, "stage_ms": stage, "gpu_launches": launches, "roofline": roof,
-             "plan_ms": plan_ms,
+             "plan_ms": plan_ms, "contraction_shape": code,
              "error_vs_oracle": float(np.max(np.abs(B[sel] - ref["B"]) / (c_n * ref["scale"]))),
              "counts_bit_exact_on_sample": bool(np.array_equal(plan.counts[sel], ref["counts"]))}
         if prec == "split_bf16":
@@ -512,7 +514,8 @@ def run_ours(args):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             achieved = useful_flops / (stage["ms_contract"] * 1e-3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": traffic_for("tc_contract", TC_SOURCES, workload_key(N, NSHELL, ORDER, WIDTH, ELL)),
+                    "traffic": traffic_for("tc_contract", TC_SOURCES, workload_key(N, NSHELL, ORDER, WIDTH, ELL),
+                                           tuned[0]),
                     "kernel": "tc_contract",
                     "peak_source": f"bf16 dense sustained, {peak_src}"}
         else:
