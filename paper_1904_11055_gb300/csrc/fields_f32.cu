@@ -30,12 +30,12 @@ cudaError_t ps_inverse_f32(int n, int unity, const void* fhat, const void* lines
 
 cudaError_t ps_inverse_ranged_f32(int n, const void* fhat, const void* lines, const int* line_off, int s0, int ns, int K,
                                   const void* tw_inv, void* out, size_t out_stride, void* xpre, int max_lines,
-                                  int tile_ns, const int* kz_host, cudaStream_t st) {
+                                  int tile_ns, const int* kz_host, const int* kz_dev, cudaStream_t st) {
 #define PS_CASE(NN) \
     case NN:        \
         return inverse_ranged_n<float, NN>((const Cx<float>*)fhat, (const short4*)lines, line_off, s0, ns, K,      \
                                            (const Cx<double>*)tw_inv, (float*)out, out_stride, (Cx<float>*)xpre,    \
-                                           max_lines, tile_ns, kz_host, st);
+                                           max_lines, tile_ns, kz_host, kz_dev, st);
     switch (n) { PS_FOR_EACH_N(PS_CASE) }
 #undef PS_CASE
     return cudaErrorInvalidValue;

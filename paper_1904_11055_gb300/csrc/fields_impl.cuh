@@ -273,7 +273,8 @@ template <typename T, int N, bool SPILL, bool UNITY, bool XPRE, int WARPS, int M
 __global__ void __launch_bounds__(WARPS * 32, MINB) inv_plane_kernel(
     const Cx<T>* __restrict__ fhat, const short4* __restrict__ lines, const int* __restrict__ line_off, int s0,
     int K, int x0, const Cx<double>* __restrict__ g_tw, T* __restrict__ out, size_t out_shell_stride,
-    Cx<T>* __restrict__ spill, const Cx<T>* __restrict__ xpre, int tile_ns, int plane_s0) {
+    Cx<T>* __restrict__ spill, const Cx<T>* __restrict__ xpre, int tile_ns, int plane_s0,
+    const int* __restrict__ shell_kz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ls = line_stride<T>(N);
     constexpr int LPW = fft_lpw(N);
@@ -287,25 +288,39 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) inv_plane_kernel(
     __shared__ int s_kzmax;
     const int lb = line_off[s], le = line_off[s + 1];
     // the shell's largest kz: kz lines above it stay zero through the y pass and are skipped
-    if (threadIdx.x == 0) s_kzmax = 0;
+    // (from the plan's per-shell table when given, else from the shell's lines)
+    if (threadIdx.x == 0) s_kzmax = shell_kz ? shell_kz[s] : 0;
     load_twiddles(s_tw, g_tw, N);
     __syncthreads();
-    {
+    if (!shell_kz) {
         int kzm = 0;
         for (int li = lb + threadIdx.x; li < le; li += blockDim.x) kzm = max(kzm, (int)lines[li].y);
         if (kzm > 0) atomicMax(&s_kzmax, kzm);
+        __syncthreads();
     }
-    __syncthreads();
     const int Ks = s_kzmax;
     for (int e = threadIdx.x; e < (Ks + 1) * ls; e += blockDim.x) Hb[e] = cx<T>(0, 0);
     __syncthreads();
 
     if (XPRE) {
-        // the x pass already transformed each line: scatter this plane's values
+        // the x pass already transformed each line: scatter this plane's values (four lines per
+        // thread in flight: all loads first, then the stores)
         const Cx<T>* Tx = xpre + (size_t)lb * N + (size_t)x * (le - lb);
-        for (int li = threadIdx.x; li < le - lb; li += blockDim.x) {
-            const short4 L = lines[lb + li];
-            Hb[(size_t)L.y * ls + pad_idx<T>((L.x + N) % N)] = Tx[li];
+        const int nl = le - lb;
+        for (int l0 = threadIdx.x; l0 < nl; l0 += 4 * blockDim.x) {
+            short4 L[4];
+            Cx<T> v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int li = l0 + u * blockDim.x;
+                if (li < nl) {
+                    L[u] = lines[lb + li];
+                    v[u] = Tx[li];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (l0 + u * blockDim.x < nl) Hb[(size_t)L[u].y * ls + pad_idx<T>((L[u].x + N) % N)] = v[u];
         }
     }
     // gather along x
@@ -433,7 +448,7 @@ static cudaError_t inverse_n(const Cx<T>* fhat, const short4* lines, const int* 
         const size_t smw = plane_smem_n<T, N>(K, SP, W);                                                          \
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw))) return e;       \
         k<<<grid, W * 32, smw, st>>>(fhat, lines, line_off, s0, K, x0, tw_inv, out, out_stride,                   \
-                                     SP ? spill : nullptr, xpre, tile_ns, s0);                                    \
+                                     SP ? spill : nullptr, xpre, tile_ns, s0, nullptr);                           \
     }
     // 16 warps per block for FP32 when the plane still fits in shared memory (latency hiding), else 8
     const bool wide = sizeof(T) == 4 && !spill_on && plane_smem_n<T, N>(K, false, 16) <= kMaxSmem;
@@ -455,11 +470,11 @@ static cudaError_t inverse_n(const Cx<T>* fhat, const short4* lines, const int* 
 // its own largest kz needs: shells whose plane buffer fits twice per SM run as
 // 8-warp blocks, two per SM, so that one block's transform phases overlap the
 // other's; the rest run as one 16-warp block per SM.  kz_host[s] is shell s's
-// largest kz (host array).
+// largest kz (host array), kz_dev the same table on the device (or NULL).
 template <typename T, int N>
 static cudaError_t inverse_ranged_n(const Cx<T>* fhat, const short4* lines, const int* line_off, int s0, int ns, int K,
                                     const Cx<double>* tw_inv, T* out, size_t out_stride, Cx<T>* xpre, int max_lines,
-                                    int tile_ns, const int* kz_host, cudaStream_t st) {
+                                    int tile_ns, const int* kz_host, const int* kz_dev, cudaStream_t st) {
     if (plane_smem_n<T, N>(K, false, 16) > kMaxSmem || !xpre)
         return inverse_n<T, N, false>(fhat, lines, line_off, s0, ns, K, 0, N, tw_inv, out, out_stride, nullptr, xpre,
                                       max_lines, tile_ns, st);
@@ -483,13 +498,13 @@ static cudaError_t inverse_ranged_n(const Cx<T>* fhat, const short4* lines, cons
             const size_t sm = plane_smem_n<T, N>(kzm, false, 8);
             if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
             k<<<grid, 8 * 32, sm, st>>>(fhat, lines, line_off, r0, K, 0, tw_inv, out, out_stride, nullptr, xpre, tile_ns,
-                                        s0);
+                                        s0, kz_dev);
         } else {
             auto k = inv_plane_kernel<T, N, false, false, true, 16, 1>;
             const size_t sm = plane_smem_n<T, N>(kzm, false, 16);
             if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
             k<<<grid, 16 * 32, sm, st>>>(fhat, lines, line_off, r0, K, 0, tw_inv, out, out_stride, nullptr, xpre,
-                                         tile_ns, s0);
+                                         tile_ns, s0, kz_dev);
         }
         if ((e = cudaGetLastError())) return e;
         r0 = r1;

@@ -20,10 +20,11 @@ cudaError_t ps_inverse(int n, int is_double, int unity, const void* fhat, const 
                        int s0, int ns, int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride,
                        void* spill, void* xpre, int max_lines, int tile_ns, cudaStream_t st);
 // The FP32 estimate-path inverse in runs of shells sized by each shell's largest
-// kz (kz_host: host array indexed by shell); see inverse_ranged_n.
+// kz (kz_host: host array indexed by shell; kz_dev: the same on the device, or
+// NULL); see inverse_ranged_n.
 cudaError_t ps_inverse_ranged_f32(int n, const void* fhat, const void* lines, const int* line_off, int s0, int ns, int K,
                                   const void* tw_inv, void* out, size_t out_stride, void* xpre, int max_lines,
-                                  int tile_ns, const int* kz_host, cudaStream_t st);
+                                  int tile_ns, const int* kz_host, const int* kz_dev, cudaStream_t st);
 
 // ---- contract_cc.cu -----------------------------------------------------------
 // One GEMM tile of the CUDA-core contraction: up to 64 rows x 64 cols, each row

@@ -541,6 +541,7 @@ static poly_status create_plan(PsPlan* p, int N, double L, int order, int nshell
 
     PS_TRY(upload(p, &p->d_lines, lines));
     PS_TRY(upload(p, (void**)&p->d_line_off, off));
+    PS_TRY(upload(p, (void**)&p->d_shell_kz, p->shell_kz));
 
     // contraction tiles (CUDA-core path; the counts use them too)
     PS_TRY(upload(p, &p->d_cc_tiles, p->cc.tiles));
@@ -622,7 +623,7 @@ poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st) {
     else
         e = ps_inverse_ranged_f32(p->N, p->d_fhat, p->d_lines, p->d_line_off, 0, p->nshell, p->K, p->d_tw_inv,
                                   p->d_fields, (size_t)p->N * p->N * p->N, p->d_xpre, p->max_lines, p->nfield,
-                                  p->shell_kz.data(), st);
+                                  p->shell_kz.data(), p->d_shell_kz, st);
     if (e) return cuda_error(e, "shell fields");
     p->launches += 2;  // x pass + plane kernel
     if (p->ell > 0) {
@@ -639,7 +640,7 @@ poly_status ps_fields(PsPlan* p, const void* delta, cudaStream_t st) {
         else
             e = ps_inverse_ranged_f32(p->N, p->d_fhat_w, p->d_lines, p->d_line_off, 0, p->nshell, p->K, p->d_tw_inv,
                                       out_w, (size_t)p->N * p->N * p->N, p->d_xpre, p->max_lines, p->nfield,
-                                      p->shell_kz.data(), st);
+                                      p->shell_kz.data(), p->d_shell_kz, st);
         if (e) return cuda_error(e, "weighted shell fields");
         p->launches += 3;
     }

@@ -49,6 +49,7 @@ struct poly_plan_s {
     int* d_line_off = nullptr; // nshell + 2 offsets (last slot: union of all shells)
     std::vector<int> line_off; // host copy
     std::vector<int> shell_kz; // largest kz of each shell's lines (host)
+    int* d_shell_kz = nullptr; // the same on the device
     int max_lines = 0;         // largest line count of one shell (or of the union)
     void* d_xpre = nullptr;    // x-pass output of the inverse transform
     size_t xpre_lines = 0;     // lines the x-pass buffer holds (indexed by global line offset)
