@@ -98,8 +98,12 @@ poly_status poly_plan_nbins(poly_plan plan, int64_t* nbins);
  *   B^ell_b = (2 ell + 1) c_n sum_x D^ell_{k1}(x) prod_{t>1} D_{kt}(x) / (N^3 count_b),
  *   D^ell_k(x) = sum_{q in S_k} L_ell(q_z/|q|) dhat(q) e^{+2 pi i q.x/N}.
  * ell even in [0, 8] (POLY_ERR_ARG otherwise; odd multipoles of a real field
- * are not real); ell = 0 is poly_plan_create.  POLY_FP32 and POLY_FP64 only
- * (POLY_ERR_UNSUPPORTED for split-BF16).  The plan holds 2 * nshell fields;
+ * are not real); ell = 0 is poly_plan_create.  All three precisions; a
+ * split-BF16 plan runs the tensor-core contraction with the weighted fields as
+ * its rows' first factor (orders 2 to 4, as for monopole plans; 64 unit shells
+ * fit, the chunk stages 2 * nshell field rows, and a shell count whose stages
+ * leave no shared memory for accumulators is POLY_ERR_UNSUPPORTED).  The plan
+ * holds 2 * nshell fields;
  * counts are the plain polygon counts.  poly_backward and
  * poly_trispectrum_disconnected return POLY_ERR_UNSUPPORTED for ell > 0.
  */

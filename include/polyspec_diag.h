@@ -113,7 +113,10 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
  * the host alone: which products of fields (rows: the first legs, as a pair for
  * n >= 3; columns: the remaining legs) each block accumulates where, and where
  * the reduction finds each bin.  N, order (2..4), edges, nshell and flags as in
- * poly_plan_create; sms (the device's SM count), max_mt (M tiles per group) and
+ * poly_plan_create, ell as in poly_plan_create_multipole (for ell > 0 the rows'
+ * first factor is the weighted field slot k1 - 1 + nshell, and the groups are
+ * held to fewer accumulator columns: the chunk stages 2 nshell field rows);
+ * sms (the device's SM count), max_mt (M tiles per group) and
  * cta_mult (the block budget is sms x cta_mult / 2) as poly_plan_set_config
  * and the device would set them.
  *   sizes[7] (required) receives the counts: bins, blocks, groups, M tiles,
@@ -131,8 +134,8 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
  *          128 + row; bin b is the sum of that slot over those blocks.
  * Returns a poly_status.
  */
-int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms, int max_mt,
-                        int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups, int32_t* mtiles,
+int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell, int sms,
+                        int max_mt, int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups, int32_t* mtiles,
                         int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap);
 
 /*

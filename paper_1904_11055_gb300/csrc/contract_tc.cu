@@ -617,8 +617,11 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     const int n = p->order;
     t->ra = n >= 3 ? 2 : 1;
     t->ca = n - t->ra;
-    t->nshell = p->nshell;
+    t->nshell = p->nfield;  // field rows staged per chunk: nshell, or 2 nshell for a multipole plan
     const bool ra2 = t->ra == 2;
+    // a multipole plan's first leg reads the Legendre-weighted field of its shell (slot k1 - 1 + nshell)
+    const int shift = p->ell > 0 ? p->nshell : 0;
+
     const int max_mt = std::max(1, std::min(kTcMaxMT, p->tc_max_mt));  // M tiles per group (tunable)
     auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra2 ? b[1] : -1); };
     auto ckey = [&](const int32_t* b) { return std::make_pair(b[t->ra], t->ca == 2 ? b[t->ra + 1] : -1); };
@@ -630,6 +633,20 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     }
     std::map<std::pair<int, int>, int> gcol;
     for (auto& c : allcols) gcol[c] = (int)gcol.size();
+    // accumulator columns per group: a multipole plan stages twice the rows per chunk, so its groups
+    // are held to what still fits shared memory next to the TMA stages and three A/B slots (two if
+    // three leave no room)
+    int acc_budget = kTcAccMax;
+    if (p->ell > 0) {
+        const int stage = (p->nfield * 128 + 1023) / 1024 * 1024;
+        const int cols = std::min(kTcMaxCols, ((int)allcols.size() + 15) / 16 * 16);
+        for (int slots = 3; slots >= 2; slots--) {
+            const long room = 227L * 1024 - (long)tc_smem_bytes(stage, cols * kTcChunk * 2, slots, 0);
+            acc_budget = (int)std::min<long>(kTcAccMax, std::max<long>(0, room / (128 * 4)) / 16 * 16);
+            if (acc_budget >= 64) break;
+        }
+        if (acc_budget < 16) return POLY_ERR_UNSUPPORTED;
+    }
     struct Row {
         bool valid;
         std::pair<int, int> key;  // shells (from 1) of the row factors; in range also for padding rows
@@ -729,7 +746,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
             for (int c : inst[i].cols) cb.insert(lidx[c] / 16);
             for (auto& rr : tc_runs(cb)) g.acc += 16 * rr.second;
         }
-        return g.acc <= kTcAccMax && (m1 - m0) <= max_mt;
+        return g.acc <= acc_budget && (m1 - m0) <= max_mt;
     };
     // groups: the fewest that fit, with the instances spread evenly over them (each group
     // pays a fixed per-chunk cost for loading and synchronisation)
@@ -756,11 +773,10 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     std::vector<int4>& runs = h.runs;
     std::vector<short2>& rowf = h.rowf;
     std::vector<short2>& colf = h.colf;
-    // (row, col) keys -> (group, slot); shells (from 1, or -1 for none) packed one per byte
-    // shells (from 1, or -1 for none) packed one per byte: shell + 1 < 256 (multipole plans, whose row
-    // factors would use the weighted slots nshell .. 2 nshell - 1, never reach the tensor-core tables)
+    // (row, col) keys -> (group, slot); shells (from 1, or -1 for none) packed one per byte (the keys
+    // hold shell numbers, not field slots, so the weighted slots of a multipole plan do not enter them)
     static_assert(kPsMaxShells + 1 < 256, "a shell number + 1 must fit one byte of the packed key");
-    if (p->nshell > kPsMaxShells || p->ell != 0) return POLY_ERR_UNSUPPORTED;
+    if (p->nshell > kPsMaxShells) return POLY_ERR_UNSUPPORTED;
     auto pack = [](int a, int b, int c, int d) {
         return (uint32_t)(a + 1) | (uint32_t)(b + 1) << 8 | (uint32_t)(c + 1) << 16 | (uint32_t)(d + 1) << 24;
     };
@@ -798,7 +814,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
             const size_t r0 = (size_t)m * 128, r1 = r0 + 128;
             for (size_t r = r0; r < r1; r++) {
                 short2 f;
-                f.x = (short)(rl[r].key.first - 1);
+                f.x = (short)(rl[r].key.first - 1 + shift);
                 f.y = (short)(rl[r].key.second > 0 ? rl[r].key.second - 1 : -1);
                 rowf.push_back(f);
             }
@@ -891,19 +907,19 @@ poly_status ps_tc_prepare(PsPlan* p) {
     if ((s = ps_alloc(p, (void**)&t->d_partial, t->ctas.size() * (size_t)kTcAccMax * 128 * 8))) return s;
     if ((s = ps_alloc(p, (void**)&t->d_err, 16))) return s;
     if (cudaMemset(t->d_err, 0, 16)) return POLY_ERR_CUDA;
-    // tensor map over the cell-tiled fields [ncell/32 * nshell rows][32 cells] fp32: one box = one 32-cell
-    // chunk of every shell (a contiguous block), 128-byte swizzle
+    // tensor map over the cell-tiled fields [ncell/32 * nfield rows][32 cells] fp32: one box = one 32-cell
+    // chunk of every field slot (a contiguous block), 128-byte swizzle
     auto enc = get_encode();
     if (!enc) return POLY_ERR_UNSUPPORTED;
-    cuuint64_t gdim[2] = {(cuuint64_t)kTcChunk, (cuuint64_t)(ncell / kTcChunk) * (cuuint64_t)p->nshell};
+    cuuint64_t gdim[2] = {(cuuint64_t)kTcChunk, (cuuint64_t)(ncell / kTcChunk) * (cuuint64_t)p->nfield};
     cuuint64_t gstride[1] = {(cuuint64_t)kTcChunk * 4};
-    cuuint32_t box[2] = {(cuuint32_t)kTcChunk, (cuuint32_t)p->nshell};
+    cuuint32_t box[2] = {(cuuint32_t)kTcChunk, (cuuint32_t)p->nfield};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&t->fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->d_fields, gdim, gstride, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return POLY_ERR_CUDA;
-    t->stage_bytes = (p->nshell * 128 + 1023) / 1024 * 1024;
+    t->stage_bytes = (p->nfield * 128 + 1023) / 1024 * 1024;
     int maxcol = 16, maxacc = 16;
     for (auto& g : groups) {
         maxcol = std::max(maxcol, g.ncol);
@@ -926,13 +942,13 @@ poly_status ps_tc_prepare(PsPlan* p) {
     return POLY_OK;
 }
 
-static int diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms, int max_mt,
-                          int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups, int32_t* mtiles,
+static int diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell, int sms,
+                          int max_mt, int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups, int32_t* mtiles,
                           int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap) {
     if (!sizes || sms < 1 || max_mt < 1 || cta_mult < 1) return POLY_ERR_ARG;
     PsPlan hp;  // host tables only: no device call, no device memory
     std::vector<short> lines;
-    if (poly_status s = ps_plan_host_tables(&hp, N, 1.0, order, nshell, edges, POLY_SPLIT_BF16, flags, 0, lines))
+    if (poly_status s = ps_plan_host_tables(&hp, N, 1.0, order, nshell, edges, POLY_SPLIT_BF16, flags, ell, lines))
         return s;
     hp.sms = sms;
     hp.tc_max_mt = max_mt;
@@ -978,11 +994,11 @@ static int diag_tc_tables(int N, int order, const double* edges, int nshell, uns
     return POLY_OK;
 }
 
-extern "C" int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int sms,
-                                   int max_mt, int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups,
+extern "C" int poly_diag_tc_tables(int N, int order, const double* edges, int nshell, unsigned flags, int ell,
+                                   int sms, int max_mt, int cta_mult, int64_t* sizes, int64_t* ctas, int32_t* groups,
                                    int32_t* mtiles, int32_t* runs, int16_t* rowf, int16_t* colf, int32_t* binmap) {
     try {
-        return diag_tc_tables(N, order, edges, nshell, flags, sms, max_mt, cta_mult, sizes, ctas, groups, mtiles,
+        return diag_tc_tables(N, order, edges, nshell, flags, ell, sms, max_mt, cta_mult, sizes, ctas, groups, mtiles,
                               runs, rowf, colf, binmap);
     } catch (const std::bad_alloc&) {
         return POLY_ERR_ALLOC;

@@ -450,8 +450,6 @@ poly_status ps_plan_host_tables(PsPlan* p, int N, double L, int order, int nshel
                                poly_precision prec, unsigned flags, int ell, std::vector<short>& lines) {
     if (!edges || nshell < 1 || nshell > kPsMaxShells) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
     if (ell < 0 || ell > 8 || (ell & 1)) return set_error(POLY_ERR_ARG, "ell must be even, in [0, 8]");
-    if (ell > 0 && prec == POLY_SPLIT_BF16)
-        return set_error(POLY_ERR_UNSUPPORTED, "multipole plans run in FP32 or FP64 (CUDA-core contraction)");
     if (order < 2 || order > 6) return set_error(POLY_ERR_UNSUPPORTED, "order must be in [2, 6]");
     if (order > 4 && prec == POLY_SPLIT_BF16)
         return set_error(POLY_ERR_UNSUPPORTED, "split-BF16 plans support orders 2 to 4 (FP32 and FP64: up to 6)");

@@ -66,10 +66,11 @@ def test_argument_validation_before_device(lib, kwargs, status):
     assert ei.value.status == status
 
 
-@pytest.mark.parametrize("ell,prec,status", [(1, 0, 1), (10, 0, 1), (-2, 3, 1), (2, 1, 6)])
-def test_multipole_plans_validate_ell_and_precision(lib, ell, prec, status):
+@pytest.mark.parametrize("ell,prec,order,status", [(1, 0, 3, 1), (10, 0, 3, 1), (-2, 3, 3, 1), (2, 1, 5, 6)])
+def test_multipole_plans_validate_ell_and_precision(lib, ell, prec, order, status):
+    """Bad ell is an argument error; split-BF16 multipole plans stop at order 4, as the monopole ones."""
     with pytest.raises(ps.PolyError) as ei:
-        ps.poly_plan_create_multipole(64, 1000.0, 3, np.arange(17) + 0.5, prec, 0, ell)
+        ps.poly_plan_create_multipole(64, 1000.0, order, np.arange(17) + 0.5, prec, 0, ell)
     assert ei.value.status == status
 
 

@@ -170,7 +170,7 @@ def test_disconnected_part_is_refused_below_order_4():
 
 
 # ------------------------------------------------------------------ redshift-space multipoles (first leg L_ell)
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "split_bf16"])
 @pytest.mark.parametrize("N,order,nshell,ell,seed", [(32, 3, 8, 2, 41), (48, 3, 12, 4, 42), (32, 4, 6, 2, 43)])
 def test_multipoles_match_oracle(prec, N, order, nshell, ell, seed):
     e = fieldgen.unit_edges(nshell)
@@ -275,11 +275,12 @@ def test_order5_128cube_sampled():
     assert err.max() <= TOL["fp32"], err.max()
 
 
-def test_quadrupole_256cube_sampled(field256):
-    """ell = 2 multipole bispectrum at 256^3 with 64 unit shells (the size bench.py measures), FP32, on the
-    triangles among five shells."""
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_quadrupole_256cube_sampled(prec, field256):
+    """ell = 2 multipole bispectrum at 256^3 with 64 unit shells (the size bench.py measures), FP32 and
+    split-BF16, on the triangles among five shells."""
     e = fieldgen.unit_edges(64)
-    plan = ps.Plan(256, 1000.0, 3, e, "fp32", ell=2)
+    plan = ps.Plan(256, 1000.0, 3, e, prec, ell=2)
     B = plan.estimate(torch.from_numpy(field256).cuda()).cpu().numpy()
     shells = {64, 40, 33, 17, 2}
     idx = np.array([i for i, b in enumerate(plan.bins) if set(b.tolist()) <= shells])
@@ -287,7 +288,7 @@ def test_quadrupole_256cube_sampled(field256):
     ref = oracle.estimate_ell(field256.astype(np.float64), 1000.0, e, 3, 2, plan.bins[idx])
     assert np.array_equal(plan.counts[idx], ref["counts"])
     err = np.abs(B[idx] - ref["B"]) / (5 * norm(1000.0, 256, 3) * ref["scale"])
-    assert err.max() <= TOL["fp32"], err.max()
+    assert err.max() <= TOL[prec], err.max()
 
 
 def test_matches_an_independent_cufft_route():

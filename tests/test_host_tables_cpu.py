@@ -156,15 +156,15 @@ def test_host_checks_match_plan_creation(lib, kwargs, status):
 
 # ------------------------------------------------------------------ tensor-core contraction tables
 
-def tc_tables(lib, N, order, edges, sms=152, max_mt=4, cta_mult=4, flags=0):
+def tc_tables(lib, N, order, edges, sms=152, max_mt=4, cta_mult=4, flags=0, ell=0):
     fn = lib.poly_diag_tc_tables
     P = ctypes.c_void_p
     fn.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.c_int,
-                   ctypes.c_int] + [P] * 8
+                   ctypes.c_int, ctypes.c_int] + [P] * 8
     fn.restype = ctypes.c_int
     e = np.ascontiguousarray(edges, dtype=np.float64)
     sizes = np.zeros(7, dtype=np.int64)
-    args = (N, order, e.ctypes.data, e.size - 1, flags, sms, max_mt, cta_mult)
+    args = (N, order, e.ctypes.data, e.size - 1, flags, ell, sms, max_mt, cta_mult)
     rc = fn(*args, sizes.ctypes.data, *([None] * 7))
     if rc:
         return rc, None
@@ -177,7 +177,8 @@ def tc_tables(lib, N, order, edges, sms=152, max_mt=4, cta_mult=4, flags=0):
     return 0, t
 
 
-def check_tc_tables(t, bins, N, nshell, max_mt):
+def check_tc_tables(t, bins, N, nshell, max_mt, shift=0):
+    """shift: the first row factor's slot offset (nshell for a multipole plan's weighted fields)."""
     order = bins.shape[1]
     ra = 2 if order >= 3 else 1
     ctas, groups, mtiles, runs, rowf, colf, bm = (t[k] for k in ("ctas", "groups", "mtiles", "runs", "rowf", "colf",
@@ -200,7 +201,7 @@ def check_tc_tables(t, bins, N, nshell, max_mt):
             row_off, run_off, nrun = mtiles[m]
             assert 1 <= nrun <= 4
             rf = rowf[row_off:row_off + 128]
-            assert np.all((rf[:, 0] >= 0) & (rf[:, 0] < nshell))  # padding rows repeat a real row
+            assert np.all((rf[:, 0] >= shift) & (rf[:, 0] < nshell + shift))  # padding rows repeat a real row
             assert np.all(rf[:, 1] < nshell) and np.all((rf[:, 1] >= 0) == (ra == 2))
             for n0, nn, acc, mloc in runs[run_off:run_off + nrun]:
                 assert mloc == m - mt_off and nn % 16 == 0 and n0 % 16 == 0 and n0 + nn <= ncol
@@ -221,7 +222,7 @@ def check_tc_tables(t, bins, N, nshell, max_mt):
     cf = colf[col].astype(np.int64)
     legs = bins.astype(np.int64) - 1
     pad = -np.ones(len(bins), np.int64)
-    want_row = np.stack([legs[:, 0], legs[:, 1] if ra == 2 else pad], 1)
+    want_row = np.stack([legs[:, 0] + shift, legs[:, 1] if ra == 2 else pad], 1)
     rest = legs[:, ra:]
     want_col = np.stack([rest[:, 0], rest[:, 1] if rest.shape[1] > 1 else pad], 1)
     assert np.array_equal(rf, want_row) and np.array_equal(cf, want_col)
@@ -248,6 +249,18 @@ def test_tc_tables_other_plans(lib, N, order, nshell, width, sms):
     rc, t = tc_tables(lib, N, order, e, sms)
     assert rc == 0
     check_tc_tables(t, oracle.enumerate_bins(e, order), N, nshell, 4)
+
+
+@pytest.mark.parametrize("N,order,nshell,ell", [(256, 3, 64, 2), (48, 3, 12, 4), (32, 4, 6, 2), (64, 2, 20, 2)])
+@pytest.mark.parametrize("max_mt", [2, 4])
+def test_tc_tables_multipole_plans(lib, N, order, nshell, ell, max_mt):
+    """Multipole plans: each bin's row reads the weighted field of its first leg (slot k1 - 1 + nshell) and
+    the plain field of its second; columns and every other invariant as for the monopole."""
+    e = fieldgen.unit_edges(nshell)
+    rc, t = tc_tables(lib, N, order, e, 152, max_mt, 4, 0, ell)
+    assert rc == 0
+    check_tc_tables(t, oracle.enumerate_bins(e, order), N, nshell, max_mt, shift=nshell)
+    assert t["groups"][:, 4].max() <= 256
 
 
 @pytest.mark.parametrize("kwargs,status", [
