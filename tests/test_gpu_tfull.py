@@ -60,7 +60,8 @@ CASES = [
     (16, 300.0, 4, (4, 4, 4, 4), unit_diagonals(9), "fp32", 61),  # sums of three q wrap around the grid
     (24, 400.0, 5, (5, 4, 3, 2), unit_diagonals(10), "fp32", 62),
     (32, 500.0, 7, (7, 6, 5, 4), unit_diagonals(15), "fp32", 63),
-    (32, 500.0, 7, (5, 7, 4, 6), np.linspace(0.0, 15.0, 41), "fp32", 64),  # 40 bins: accumulators in global memory
+    (32, 500.0, 7, (5, 7, 4, 6), np.linspace(0.0, 15.0, 41), "fp32", 64),  # 40 diagonal bins
+    (24, 400.0, 5, (5, 4, 3, 2), np.linspace(0.0, 10.5, 101), "fp64", 74),  # tables too large for shared memory
     (32, 500.0, 7, (6, 6, 6, 6), np.array([1.0, 3.0, 4.5, 6.0, 9.0, 11.5]), "fp32", 65),  # ranges outside every bin
     (32, 500.0, 7, (7, 6, 5, 4), unit_diagonals(15), "split_bf16", 66),
     (32, 500.0, 5, (5, 5, 4, 3), unit_diagonals(11), "fp32", 73),  # 3K <= (N - 1) / 2: no sum needs reducing
