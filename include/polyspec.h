@@ -81,7 +81,12 @@ typedef enum {
  * builds the shell tables and tiles, allocates the workspace (nshell * N^3
  * fields of the plan's precision plus small buffers) on the current CUDA
  * device and computes the exact counts (FP64 counting fields on the
- * 1/48 symmetry wedge, cached per (N, edges, n, flags) in the process).
+ * 1/48 symmetry wedge, cached per (N, edges, n, flags) in the process).  Where
+ * those FP64 sums can no longer be rounded safely (large n = 5, 6 plans) the
+ * counts come from integer closure maps instead (the product of the first
+ * max(1, n - 3) legs' counting fields and of the rest, each transformed and
+ * rounded to its integer map, then summed in 64-bit integers); plans with
+ * POLY_ALLOW_ALIAS cannot take that route and return POLY_ERR_COUNT there.
  * It synchronises the device.  On failure *out is set to NULL.
  */
 poly_status poly_plan_create(poly_plan* out, int N, double L, int order, int nshell, const double* edges,

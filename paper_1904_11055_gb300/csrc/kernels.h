@@ -60,5 +60,14 @@ cudaError_t ps_normalise(const double* S, const int64_t* counts, int64_t nbins, 
 
 // ---- misc.cu -------------------------------------------------------------------
 // out[s * out_stride + w] = in[s * in_stride + idx[w]] for s < ns, w < nw
+// ---- counts_exact.cu ---------------------------------------------------------
+// out = F[s0] F[s1] F[s2] (slots -1: none), FP64 fields of n3 cells in natural layout
+cudaError_t ps_prod_fields(const double* F, size_t n3, int s0, int s1, int s2, double* out, cudaStream_t st);
+// G[i] = round(Re fhat[i] * inv_n3) for n complex FP64 values; *err = 1 if any is not near an integer
+cudaError_t ps_round_map(const void* fhat, size_t n, double inv_n3, long long* G, int* err, cudaStream_t st);
+// out[b] = sum over the half cube |p_c| <= Kp of w(kz) maps[which[b].x][i] maps[which[b].y][i]
+cudaError_t ps_dot_maps(const long long* maps, size_t mapsz, const int2* which, int nbins, int Kp,
+                        unsigned long long* out, cudaStream_t st);
+
 cudaError_t ps_gather_cells(int is_double, const void* in, size_t in_stride, int ns, const int32_t* idx, int64_t nw,
                             void* out, size_t out_stride, cudaStream_t st);

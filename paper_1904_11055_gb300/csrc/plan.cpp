@@ -315,6 +315,102 @@ static void bin_wraps(const PsPlan* p, uint8_t* out) {
     }
 }
 
+// Exact counts from integer closure maps (counts_exact.cu), for plans whose closures cannot wrap:
+// legs split into A (the first max(1, n - 3)) and B (the rest); per distinct group, the product of
+// its full-grid FP64 counting fields is forward transformed on the cube |p_c| <= K' = |A| K and
+// rounded to its integer closure map; count_b = sum_p G_A(p) G_B(p) in 64-bit integers.
+static poly_status exact_counts(PsPlan* p, cudaStream_t st, std::vector<int64_t>& counts) {
+    const int N = p->N, n = p->order, K = p->K;
+    const int a = std::max(1, n - 3);
+    const int Kp = a * K;
+    if (p->flags & POLY_ALLOW_ALIAS) return set_error(POLY_ERR_COUNT, "exact counts need closures that cannot wrap");
+    if (2 * Kp + 1 > N) return set_error(POLY_ERR_COUNT, "exact counts: the first legs' sums exceed the grid");
+    std::map<std::array<int, 3>, int> gid;
+    std::vector<std::array<int, 3>> groups;
+    std::vector<int2> which((size_t)p->nbins);
+    auto group_of = [&](const int32_t* k, int cnt) {
+        std::array<int, 3> g{-1, -1, -1};
+        for (int i = 0; i < cnt; i++) g[i] = k[i] - 1;
+        auto it = gid.find(g);
+        if (it != gid.end()) return it->second;
+        const int id = (int)groups.size();
+        gid[g] = id;
+        groups.push_back(g);
+        return id;
+    };
+    for (int64_t b = 0; b < p->nbins; b++) {
+        const int32_t* k = &p->bins[b * n];
+        which[b] = make_int2(group_of(k, a), group_of(k + a, n - a));
+    }
+    const size_t n3 = (size_t)N * N * N;
+    const size_t mapsz = (size_t)(2 * Kp + 1) * (2 * Kp + 1) * (Kp + 1);
+    std::vector<void*> tmp;
+    auto talloc = [&](void** ptr, size_t bytes) -> poly_status {
+        cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(POLY_ERR_ALLOC, "exact counts workspace allocation failed");
+        }
+        tmp.push_back(*ptr);
+        return POLY_OK;
+    };
+    const int sb = std::min(8, p->nshell);
+    const bool spill_inv = ps_plane_needs_spill(N, K, 1) == 1, spill_fwd = ps_plane_needs_spill(N, Kp, 1) == 1;
+    const size_t spill_elems = std::max(spill_inv ? ps_spill_elems(N, K, N * sb, 1) : 0,
+                                        spill_fwd ? ps_spill_elems(N, Kp, N, 1) : 0);
+    void *d_iota = nullptr, *d_prod = nullptr, *d_W = nullptr, *d_fh = nullptr, *d_spill = nullptr, *d_maps = nullptr,
+         *d_which = nullptr, *d_out = nullptr, *d_err = nullptr;
+    poly_status rc = POLY_OK;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((rc = talloc(&d_iota, (size_t)p->nshell * n3 * 8)) || (rc = talloc(&d_prod, n3 * 8)) ||
+            (rc = talloc(&d_W, (size_t)N * (2 * Kp + 1) * (Kp + 1) * 16)) || (rc = talloc(&d_fh, mapsz * 16)) ||
+            (spill_elems && (rc = talloc(&d_spill, spill_elems * 16))) ||
+            (rc = talloc(&d_maps, groups.size() * mapsz * 8)) || (rc = talloc(&d_which, which.size() * sizeof(int2))) ||
+            (rc = talloc(&d_out, which.size() * 8)) || (rc = talloc(&d_err, 4)))
+            break;
+        if ((e = cudaMemsetAsync(d_err, 0, 4, st)) ||
+            (e = cudaMemcpyAsync(d_which, which.data(), which.size() * sizeof(int2), cudaMemcpyHostToDevice, st))) {
+            rc = cuda_error(e, "exact counts upload");
+            break;
+        }
+        // full-grid FP64 counting fields, natural layout
+        for (int s0 = 0; s0 < p->nshell && !rc; s0 += sb) {
+            const int ns = std::min(sb, p->nshell - s0);
+            if ((e = ps_inverse(N, 1, 1, nullptr, p->d_lines, p->d_line_off, s0, ns, K, 0, N, p->d_tw_inv,
+                                (double*)d_iota + (size_t)s0 * n3, n3, d_spill, nullptr, 0, 0, st)))
+                rc = cuda_error(e, "exact counts: counting fields");
+        }
+        for (size_t g = 0; g < groups.size() && !rc; g++) {
+            const auto& G = groups[g];
+            if ((e = ps_prod_fields((const double*)d_iota, n3, G[0], G[1], G[2], (double*)d_prod, st)) ||
+                (e = ps_forward(N, 1, d_prod, Kp, p->d_tw_fwd, d_W, d_fh, d_spill, st)) ||
+                (e = ps_round_map(d_fh, mapsz, 1.0 / (double)n3, (long long*)d_maps + g * mapsz, (int*)d_err, st)))
+                rc = cuda_error(e, "exact counts: closure maps");
+        }
+        if (rc) break;
+        if ((e = ps_dot_maps((const long long*)d_maps, mapsz, (const int2*)d_which, (int)p->nbins, Kp,
+                             (unsigned long long*)d_out, st))) {
+            rc = cuda_error(e, "exact counts: sums");
+            break;
+        }
+        std::vector<unsigned long long> c(which.size());
+        int err = 0;
+        if ((e = cudaMemcpyAsync(c.data(), d_out, c.size() * 8, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(&err, d_err, 4, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st))) {
+            rc = cuda_error(e, "exact counts readback");
+            break;
+        }
+        if (err) {
+            rc = set_error(POLY_ERR_COUNT, "exact counts: a closure map is not an integer");
+            break;
+        }
+        counts.assign(c.begin(), c.end());
+    } while (0);
+    for (void* q : tmp) cudaFree(q);
+    return rc;
+}
+
 static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
     CountKey key{p->N, p->order, p->flags & POLY_BINS_ALL_SORTED, p->edges};
     {
@@ -401,7 +497,8 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
         p->counts.resize(p->nbins);
         // The FP64 sum lands next to the integer count; rounding is exact while its error is
         // below 0.5.  The largest deviation seen is ~1e-3 (256^3, n = 4, counts ~1e11); a
-        // deviation above 0.05 means the FP64 sum can no longer be trusted to round correctly.
+        // deviation above 0.05 means the FP64 sum can no longer be trusted to round correctly,
+        // and the plan's counts come from the integer closure maps instead.
         for (int64_t b = 0; b < p->nbins; b++) {
             const double v = S[b] / n3, r = std::nearbyint(v);
             if (std::fabs(v - r) > 0.05 || r < 0) {
@@ -414,6 +511,8 @@ static poly_status compute_counts(PsPlan* p, cudaStream_t st) {
         }
     } while (0);
     cleanup();
+    const char* force = getenv("POLY_COUNTS_EXACT");  // "1": always take the closure-map route (tests)
+    if (rc == POLY_ERR_COUNT || (rc == POLY_OK && force && force[0] == '1')) rc = exact_counts(p, st, p->counts);
     if (rc == POLY_OK) {
         std::lock_guard<std::mutex> lk(g_count_mu);
         g_count_cache[key] = p->counts;
