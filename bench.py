@@ -445,6 +445,65 @@ def config4_record(ps, torch, np):
     return rec
 
 
+def rows_f_record(ps, torch, np, peaks, fma, peak_src, flush_buf, delta_np, d):
+    """SURVEY row (f) measurements beside the configurations: the redshift-space quadrupole (ell = 2) of the
+    metric workload, split-BF16 and FP32, against the oracle on the triangles among five shells; and an
+    order-5 plan whose counts need the integer closure maps (128^3, 20 unit shells)."""
+    from types import SimpleNamespace
+
+    import fieldgen
+    import oracle
+
+    rec = {}
+    e = fieldgen.unit_edges(64)
+    c3 = 5 * (L ** 3) ** 2 / float(256 ** 3) ** 3
+    q = {"workload": "quadrupole (ell = 2, line of sight z) bispectrum, 256^3 lognormal field (seed 2), 64 unit "
+                     "shells, n=3", "precisions": {}}
+    sel_ref = None
+    for prec, steps in (("split_bf16", 10), ("fp32", 3)):
+        plan = ps.Plan(256, L, 3, e, prec, ell=2)
+        code = plan.tune(d)[0] if prec == "split_bf16" else 0
+        step_ms, stage, launches = time_precision(ps, torch, plan, d, SimpleNamespace(steps=steps, warmup=3),
+                                                  flush_buf, False)
+        B = time_precision.last_out
+        if sel_ref is None:
+            shells = {64, 40, 33, 17, 2}
+            idx = np.array([i for i, b in enumerate(plan.bins) if set(b.tolist()) <= shells])
+            sel_ref = (idx, oracle.estimate_ell(delta_np.astype(np.float64), L, e, 3, 2, plan.bins[idx]))
+        idx, ref = sel_ref
+        ms = statistics.median(step_ms)
+        q["precisions"][prec] = {
+            "ms_per_step": ms, "value": plan.nbins / (ms * 1e-3), "unit": "configs/s", "steps": steps, "warmup": 3,
+            "stage_ms": stage, "gpu_launches": launches, "contraction_shape": code,
+            "roofline": _contract_roofline(prec, plan.nbins * 256 ** 3 * 3, stage["ms_contract"], peaks, fma, peak_src),
+            "error_vs_oracle": float(np.max(np.abs(B[idx] - ref["B"]) / (c3 * ref["scale"]))),
+            "bins_checked": int(len(idx))}
+        plan.close()
+    rec["f3_quadrupole_256cube"] = q
+    # order 5 at 128^3 with 20 unit shells: counts up to 1e13 come from the integer closure maps
+    e5 = fieldgen.unit_edges(20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = ps.Plan(128, L, 5, e5, "fp32")
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    d5 = torch.from_numpy(fieldgen.field("lognormal", 128, 2, np.float32)).cuda()
+    step_ms, stage, launches = time_precision(ps, torch, plan, d5, SimpleNamespace(steps=3, warmup=3), flush_buf,
+                                              False)
+    top = np.argsort(plan.counts)[-3:]
+    ref = oracle.counts_exact(128, e5, 5, plan.bins[top])
+    ms = statistics.median(step_ms)
+    rec["f2_order5_128cube"] = {
+        "workload": "order-5 polyspectrum, 128^3 lognormal field (seed 2), 20 unit shells", "nbins": plan.nbins,
+        "precision": "fp32", "ms_per_step": ms, "value": plan.nbins / (ms * 1e-3), "unit": "configs/s",
+        "plan_ms": plan_ms, "max_count": int(plan.counts.max()),
+        "counts_bit_exact_on_largest_3": bool(np.array_equal(plan.counts[top], ref)),
+        "note": "plan creation includes the integer closure-map counts (the FP64 counting-field sums cannot be "
+                "rounded safely at these counts)"}
+    plan.close()
+    return rec
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -621,6 +680,7 @@ def run_ours(args):
                            **config4_record(ps, torch, np)},
             "5_mocks": mocks_record(SimpleNamespace(steps=3, warmup=3)),
         }
+        line["rows_f"] = rows_f_record(ps, torch, np, peaks, fma, peak_src, flush_buf, delta_np, d)
     line["fma_peak_measured"] = fma
     print(json.dumps(line), flush=True)
     if dist_ok:
@@ -726,6 +786,65 @@ def mocks_record(args):
     return line
 
 
+FULL_K, FULL_NSHELL, FULL_WIDTH = (10, 10, 10, 10), 32, 1.5
+FULL_METRIC = ("full-shape trispectrum quadrilaterals/s: bin (10,10,10,10) of 32 shells of width 1.5 k_F, 256^3, "
+               "22 x 22 diagonal bins of width 1.5 k_F (Eq. Tkfull)")
+
+
+def run_fullshape(args):
+    """One full-shape trispectrum bin per step (poly_trispectrum_full on the trispectrum workload's shells)."""
+    import numpy as np
+    import torch
+
+    import fieldgen
+    import paper_1904_11055_gb300 as ps
+    from paper_1904_11055_gb300 import build as psbuild
+
+    psbuild.build()
+    e = fieldgen.unit_edges(FULL_NSHELL, FULL_WIDTH)
+    de = np.concatenate([[0.0], (np.arange(22) + 0.5) * FULL_WIDTH])
+    K = 0
+    while (K + 1) ** 2 < e[-1] ** 2:
+        K += 1
+    order = 4 if 4 * K < N else 2  # a smaller grid (profiling) takes a power-spectrum plan: same shells
+    plan = ps.Plan(N, L, order, e, "split_bf16")
+    delta_np = fieldgen.field("lognormal", N, SEED, np.float32)
+    d = torch.from_numpy(delta_np).cuda()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def step():
+        out["T"], out["C"] = plan.trispectrum_full(d, FULL_K, de)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            flush_buf.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    quads = int(out["C"].sum().item())
+    t = sum(ms) / 1e3
+    match = np.flatnonzero((plan.bins == np.asarray(FULL_K)).all(axis=1)) if order == 4 else []
+    line = {"metric": FULL_METRIC, "value": quads * args.steps / t, "unit": "quadrilaterals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"full-shape trispectrum, {N}^3 lognormal field (seed 2)", "bin": list(FULL_K),
+                       "ndiag": int(len(de) - 1), "quadrilaterals_per_step": quads,
+                       "l2": "256 MiB buffer written between timed steps (L2 flushed)"},
+            "counts_sum_equals_count_b": bool(quads == plan.counts[match[0]]) if len(match) else None,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -743,8 +862,9 @@ def main():
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--width", type=float, default=1.0, help="shell width in k_F (the trispectrum workload: 1.5)")
     ap.add_argument("--ell", type=int, default=0, help="redshift-space multipole of the first leg (even; FP32/FP64)")
-    ap.add_argument("--workload", default="metric", choices=["metric", "mocks"],
-                    help="mocks: 512 mixed-size realisations through poly_estimate_batched")
+    ap.add_argument("--workload", default="metric", choices=["metric", "mocks", "fullshape"],
+                    help="mocks: 512 mixed-size realisations through poly_estimate_batched; fullshape: one bin of "
+                         "the full-shape trispectrum")
     args = ap.parse_args()
     set_workload(args.N, args.nshell, args.order, args.width, args.ell)
     if args.warmup < 3:
@@ -753,6 +873,8 @@ def main():
         run_reference(args)
     elif args.workload == "mocks":
         run_mocks(args)
+    elif args.workload == "fullshape":
+        run_fullshape(args)
     else:
         run_ours(args)
 

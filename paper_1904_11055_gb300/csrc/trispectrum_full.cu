@@ -454,22 +454,24 @@ poly_status fail(poly_status s, const std::string& msg) {
     return s;
 }
 
-void shell_modes(int K, double lo, double hi, std::vector<int4>& out) {
-    out.clear();
-    const double lo2 = lo * lo, hi2 = hi * hi;
-    for (int x = -K; x <= K; x++)
-        for (int y = -K; y <= K; y++)
-            for (int z = -K; z <= K; z++) {
-                const int r = x * x + y * y + z * z;
-                if (lo2 <= (double)r && (double)r < hi2) out.push_back(make_int4(x, y, z, r));
-            }
-}
-
 // largest |component| of a mode of a shell with outer edge hi: the largest integer c with c^2 < hi^2
 int shell_kmax(double hi) {
     int c = 0;
     while ((double)((long long)(c + 1) * (c + 1)) < hi * hi) c++;
     return c;
+}
+
+// the shell's modes, scanned over the cube that holds them (|q_c| <= the shell's largest component, <= K)
+void shell_modes(int K, double lo, double hi, std::vector<int4>& out) {
+    out.clear();
+    const double lo2 = lo * lo, hi2 = hi * hi;
+    const int c = std::min(K, shell_kmax(hi));
+    for (int x = -c; x <= c; x++)
+        for (int y = -c; y <= c; y++)
+            for (int z = -c; z <= c; z++) {
+                const int r = x * x + y * y + z * z;
+                if (lo2 <= (double)r && (double)r < hi2) out.push_back(make_int4(x, y, z, r));
+            }
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
