@@ -482,25 +482,42 @@ def rows_f_record(ps, torch, np, peaks, fma, peak_src, flush_buf, delta_np, d):
     rec["f3_quadrupole_256cube"] = q
     # order 5 at 128^3 with 20 unit shells: counts up to 1e13 come from the integer closure maps
     e5 = fieldgen.unit_edges(20)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    plan = ps.Plan(128, L, 5, e5, "fp32")
-    torch.cuda.synchronize()
-    plan_ms = (time.perf_counter() - t0) * 1e3
     d5 = torch.from_numpy(fieldgen.field("lognormal", 128, 2, np.float32)).cuda()
-    step_ms, stage, launches = time_precision(ps, torch, plan, d5, SimpleNamespace(steps=3, warmup=3), flush_buf,
-                                              False)
-    top = np.argsort(plan.counts)[-3:]
-    ref = oracle.counts_exact(128, e5, 5, plan.bins[top])
-    ms = statistics.median(step_ms)
-    rec["f2_order5_128cube"] = {
-        "workload": "order-5 polyspectrum, 128^3 lognormal field (seed 2), 20 unit shells", "nbins": plan.nbins,
-        "precision": "fp32", "ms_per_step": ms, "value": plan.nbins / (ms * 1e-3), "unit": "configs/s",
-        "plan_ms": plan_ms, "max_count": int(plan.counts.max()),
-        "counts_bit_exact_on_largest_3": bool(np.array_equal(plan.counts[top], ref)),
-        "note": "plan creation includes the integer closure-map counts (the FP64 counting-field sums cannot be "
-                "rounded safely at these counts)"}
-    plan.close()
+    f2 = {"workload": "order-5 polyspectrum, 128^3 lognormal field (seed 2), 20 unit shells", "precisions": {},
+          "note": "plan creation includes the integer closure-map counts (the FP64 counting-field sums cannot be "
+                  "rounded safely at these counts); the first plan computes them, the second reuses them"}
+    for prec in ("fp32", "split_bf16"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = ps.Plan(128, L, 5, e5, prec)
+        torch.cuda.synchronize()
+        plan_ms = (time.perf_counter() - t0) * 1e3
+        code = plan.tune(d5)[0] if prec == "split_bf16" else 0
+        step_ms, stage, launches = time_precision(ps, torch, plan, d5, SimpleNamespace(steps=3, warmup=3),
+                                                  flush_buf, False)
+        ms = statistics.median(step_ms)
+        r = {"ms_per_step": ms, "value": plan.nbins / (ms * 1e-3), "unit": "configs/s", "stage_ms": stage,
+             "plan_ms": plan_ms, "contraction_shape": code,
+             "roofline": _contract_roofline(prec, plan.nbins * 128 ** 3 * 5, stage["ms_contract"], peaks, fma,
+                                            peak_src)}
+        if prec == "fp32":
+            top = np.argsort(plan.counts)[-3:]
+            ref = oracle.counts_exact(128, e5, 5, plan.bins[top])
+            f2["nbins"] = plan.nbins
+            f2["max_count"] = int(plan.counts.max())
+            f2["counts_bit_exact_on_largest_3"] = bool(np.array_equal(plan.counts[top], ref))
+            B32 = time_precision.last_out
+        else:
+            # split-BF16 against the FP32 path on every bin, in units of the FP32 estimate's scale
+            sc = plan.estimate(d5, scale=True)[1].cpu().numpy()
+            B16 = time_precision.last_out
+            c5 = (L ** 3) ** 4 / float(128 ** 3) ** 5
+            with np.errstate(invalid="ignore", divide="ignore"):
+                rel = np.abs(B16 - B32) / (c5 * sc)
+            r["max_diff_vs_fp32_over_scale"] = float(np.nanmax(rel[plan.counts > 0]))
+        f2["precisions"][prec] = r
+        plan.close()
+    rec["f2_order5_128cube"] = f2
     return rec
 
 

@@ -31,6 +31,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <map>
 #include <new>
@@ -93,9 +94,11 @@ struct TcWindow {
 };
 
 // One B item: 8 cells of column factor(s) -> hi and lo 16-byte core-matrix rows.
-// key1 < 0 marks a padding column (zeros).
+// key1 < 0 marks a padding column (zeros).  With three factors (CA = 3) the first two are
+// multiplied in FP32 first.
 template <int CA>
-__device__ __forceinline__ void tc_b_item(uint32_t D, int key1, int key2, uint32_t dst_hi, uint32_t dst_lo) {
+__device__ __forceinline__ void tc_b_item(uint32_t D, int key1, int key2, int key3, uint32_t dst_hi,
+                                          uint32_t dst_lo) {
     uint32_t h[4] = {0u, 0u, 0u, 0u}, l[4] = {0u, 0u, 0u, 0u};
     if (key1 >= 0) {
         float4 x0, x1;
@@ -103,7 +106,22 @@ __device__ __forceinline__ void tc_b_item(uint32_t D, int key1, int key2, uint32
                      : "=f"(x0.x), "=f"(x0.y), "=f"(x0.z), "=f"(x0.w) : "r"(D + (uint32_t)key1));
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(x1.x), "=f"(x1.y), "=f"(x1.z), "=f"(x1.w) : "r"(D + ((uint32_t)key1 ^ 16u)));
-        if (CA == 2) {
+        if (CA == 3) {
+            float4 z0, z1;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(z0.x), "=f"(z0.y), "=f"(z0.z), "=f"(z0.w) : "r"(D + (uint32_t)key3));
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(z1.x), "=f"(z1.y), "=f"(z1.z), "=f"(z1.w) : "r"(D + ((uint32_t)key3 ^ 16u)));
+            x0.x *= z0.x;
+            x0.y *= z0.y;
+            x0.z *= z0.z;
+            x0.w *= z0.w;
+            x1.x *= z1.x;
+            x1.y *= z1.y;
+            x1.z *= z1.z;
+            x1.w *= z1.w;
+        }
+        if (CA >= 2) {
             float4 y0, y1;
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(y0.x), "=f"(y0.y), "=f"(y0.z), "=f"(y0.w) : "r"(D + (uint32_t)key2));
@@ -161,7 +179,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_contract_kernel(const __grid_constant__ CUtensorMap fmap, int nshell, int stage_bytes, int bbuf_bytes,
                        int slot_cap, int acc_max, int window, const TcCta* __restrict__ ctas, const TcGroup* __restrict__ groups,
                        const TcMTile* __restrict__ mtiles, const int4* __restrict__ runs,
-                       const short2* __restrict__ rowf, const short2* __restrict__ colf, double* __restrict__ partial,
+                       const short2* __restrict__ rowf, const short4* __restrict__ colf, double* __restrict__ partial,
                        int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -169,7 +187,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint8_t* s_b = s_d + kTcStages * stage_bytes;               // [slot][hi, lo] x bbuf_bytes
     float* s_acc = (float*)(s_b + 2 * slot_cap * bbuf_bytes);   // [acc_max cols][128 rows]
     short2* s_rowf = (short2*)(s_acc + (size_t)acc_max * 128);  // [kTcMaxMT][128]
-    short2* s_colf = s_rowf + kTcMaxMT * 128;                   // [kTcMaxCols]
+    short4* s_colf = (short4*)(s_rowf + kTcMaxMT * 128);        // [kTcMaxCols]
     uint64_t* bars = (uint64_t*)(s_colf + kTcMaxCols);
     uint64_t* full = bars;                                      // [kTcStages]
     uint64_t* empty = full + kTcStages;                         // [kTcStages]
@@ -212,7 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int m = i >> 7;
         s_rowf[i] = m < nmt ? rowf[mtiles[grp.mt_off + m].row_off + (i & 127)] : make_short2(0, 0);
     }
-    for (int i = tid; i < kTcMaxCols; i += kTcThreads) s_colf[i] = i < ncol ? colf[grp.col_off + i] : make_short2(-1, -1);
+    for (int i = tid; i < kTcMaxCols; i += kTcThreads) s_colf[i] = i < ncol ? colf[grp.col_off + i] : make_short4(-1, -1, -1, -1);
     for (int i = tid; i < acc_cols * 128; i += kTcThreads) s_acc[i] = 0.f;
     if (warp == kProdWarps) {
         tc::tmem_alloc(s_tmem, 512);
@@ -360,14 +378,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t sd0 = tc::smem_u32(s_d);
         // this thread's first B item (column n, 8-cell group kg), fixed for every chunk
         const int nbitems = ncol * (kTcChunk / 8);
-        int b_key1 = -1, b_key2 = 0;
+        int b_key1 = -1, b_key2 = 0, b_key3 = 0;
         uint32_t b_off = 0;
         if (ttid < nbitems) {
             const int kg = ttid / ncol, n = ttid - kg * ncol;
-            const short2 f = s_colf[n];
+            const short4 f = s_colf[n];
             if (f.x >= 0) {
                 b_key1 = (int)(tc_row_key(f.x) ^ (uint32_t)(2 * kg * 16));
-                b_key2 = (int)(tc_row_key(CA == 2 ? f.y : 0) ^ (uint32_t)(2 * kg * 16));
+                b_key2 = (int)(tc_row_key(CA >= 2 ? f.y : 0) ^ (uint32_t)(2 * kg * 16));
+                b_key3 = (int)(tc_row_key(CA == 3 ? f.z : 0) ^ (uint32_t)(2 * kg * 16));
             }
             b_off = (uint32_t)(n / 8) * kSBO + (uint32_t)kg * kLBO + (uint32_t)(n % 8) * 16;
         }
@@ -396,14 +415,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc_row_products<RA>(D + key1[m], D + key2[m], v);
                     tc::tmem_st16(abase + (uint32_t)(m * 32), v);
                 }
-                if (m == 0 && ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, Bh + b_off, Bl + b_off);
+                if (m == 0 && ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, b_key3, Bh + b_off, Bl + b_off);
             }
             for (int it = ttid + kTcTeamWarps * 32; it < nbitems; it += kTcTeamWarps * 32) {
                 const int kg = it / ncol, n = it - kg * ncol;
-                const short2 f = s_colf[n];
+                const short4 f = s_colf[n];
                 const uint32_t off = (uint32_t)(n / 8) * kSBO + (uint32_t)kg * kLBO + (uint32_t)(n % 8) * 16;
                 tc_b_item<CA>(D, f.x >= 0 ? (int)(tc_row_key(f.x) ^ (uint32_t)(2 * kg * 16)) : -1,
-                              (int)(tc_row_key(CA == 2 && f.x >= 0 ? f.y : 0) ^ (uint32_t)(2 * kg * 16)), Bh + off,
+                              (int)(tc_row_key(CA >= 2 && f.x >= 0 ? f.y : 0) ^ (uint32_t)(2 * kg * 16)),
+                              (int)(tc_row_key(CA == 3 && f.x >= 0 ? f.z : 0) ^ (uint32_t)(2 * kg * 16)), Bh + off,
                               Bl + off);
             }
             tc::fence_proxy_async_smem();
@@ -572,7 +592,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 static size_t tc_smem_bytes(int stage_bytes, int bbuf_bytes, int slots, int acc_max) {
     return 1024 + (size_t)kTcStages * stage_bytes + 2 * (size_t)slots * bbuf_bytes + (size_t)acc_max * 128 * 4 +
-           kTcMaxMT * 128 * 4 + kTcMaxCols * 4 + (2 * kTcStages + 2 * kTcMaxSlots + 3) * 8 + 64;
+           kTcMaxMT * 128 * 4 + kTcMaxCols * 8 + (2 * kTcStages + 2 * kTcMaxSlots + 3) * 8 + 64;
 }
 
 // Sorted 16-column blocks of one M tile -> runs (first block, block count), at most
@@ -609,7 +629,8 @@ struct TcTables {
     std::vector<TcGroup> groups;
     std::vector<TcMTile> mtiles;
     std::vector<int4> runs;
-    std::vector<short2> rowf, colf;
+    std::vector<short2> rowf;
+    std::vector<short4> colf;
     std::vector<int4> binmap;
 };
 
@@ -623,15 +644,18 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     const int shift = p->ell > 0 ? p->nshell : 0;
 
     const int max_mt = std::max(1, std::min(kTcMaxMT, p->tc_max_mt));  // M tiles per group (tunable)
+    using CKey = std::array<int, 3>;  // column factors (shells from 1; -1: none)
     auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra2 ? b[1] : -1); };
-    auto ckey = [&](const int32_t* b) { return std::make_pair(b[t->ra], t->ca == 2 ? b[t->ra + 1] : -1); };
-    std::map<std::pair<int, int>, std::set<std::pair<int, int>>> rows;
-    std::set<std::pair<int, int>> allcols;
+    auto ckey = [&](const int32_t* b) {
+        return CKey{b[t->ra], t->ca >= 2 ? b[t->ra + 1] : -1, t->ca == 3 ? b[t->ra + 2] : -1};
+    };
+    std::map<std::pair<int, int>, std::set<CKey>> rows;
+    std::set<CKey> allcols;
     for (int64_t i = 0; i < p->nbins; i++) {
         rows[rkey(&p->bins[i * n])].insert(ckey(&p->bins[i * n]));
         allcols.insert(ckey(&p->bins[i * n]));
     }
-    std::map<std::pair<int, int>, int> gcol;
+    std::map<CKey, int> gcol;
     for (auto& c : allcols) gcol[c] = (int)gcol.size();
     // accumulator columns per group: a multipole plan stages twice the rows per chunk, so its groups
     // are held to what still fits shared memory next to the TMA stages and three A/B slots (two if
@@ -659,7 +683,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     // Lanes without a row repeat the block's first row (their accumulator rows are
     // never read).
     const int ns = p->nshell;
-    std::map<int, std::vector<std::pair<std::pair<int, int>, const std::set<std::pair<int, int>>*>>> octets;
+    std::map<int, std::vector<std::pair<std::pair<int, int>, const std::set<CKey>*>>> octets;
     for (auto& kv : rows) {
         const int k1 = kv.first.first;
         octets[ra2 ? (k1 - 1) / kTcRowOctet : (k1 - 1) / 32].push_back({kv.first, &kv.second});
@@ -772,17 +796,18 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     std::vector<TcMTile>& mtiles = h.mtiles;
     std::vector<int4>& runs = h.runs;
     std::vector<short2>& rowf = h.rowf;
-    std::vector<short2>& colf = h.colf;
+    std::vector<short4>& colf = h.colf;
     // (row, col) keys -> (group, slot); shells (from 1, or -1 for none) packed one per byte (the keys
     // hold shell numbers, not field slots, so the weighted slots of a multipole plan do not enter them)
     static_assert(kPsMaxShells + 1 < 256, "a shell number + 1 must fit one byte of the packed key");
     if (p->nshell > kPsMaxShells) return POLY_ERR_UNSUPPORTED;
-    auto pack = [](int a, int b, int c, int d) {
-        return (uint32_t)(a + 1) | (uint32_t)(b + 1) << 8 | (uint32_t)(c + 1) << 16 | (uint32_t)(d + 1) << 24;
+    auto pack = [](int a, int b, const CKey& c) {
+        return (uint64_t)(a + 1) | (uint64_t)(b + 1) << 8 | (uint64_t)(c[0] + 1) << 16 | (uint64_t)(c[1] + 1) << 24 |
+               (uint64_t)(c[2] + 1) << 32;
     };
-    std::unordered_map<uint32_t, std::pair<int, int>> slot_of;
+    std::unordered_map<uint64_t, std::pair<int, int>> slot_of;
     slot_of.reserve((size_t)p->nbins * 2);
-    std::vector<std::pair<int, int>> gcol_key(gcol.size());
+    std::vector<CKey> gcol_key(gcol.size());
     for (auto& kv : gcol) gcol_key[kv.second] = kv.first;
     double work_cells = 0;
     std::vector<double> gwork;
@@ -797,13 +822,11 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
         std::map<int, int> lidx;
         for (size_t i = 0; i < gp.local.size(); i++) {
             lidx[gp.local[i]] = (int)i;
-            auto k = gcol_key[gp.local[i]];
-            short2 f;
-            f.x = (short)(k.first - 1);
-            f.y = (short)(k.second > 0 ? k.second - 1 : -1);
-            colf.push_back(f);
+            const CKey& k = gcol_key[gp.local[i]];
+            colf.push_back(make_short4((short)(k[0] - 1), (short)(k[1] > 0 ? k[1] - 1 : -1),
+                                       (short)(k[2] > 0 ? k[2] - 1 : -1), (short)-1));
         }
-        for (int i = (int)gp.local.size(); i < ncol; i++) colf.push_back(make_short2(-1, -1));
+        for (int i = (int)gp.local.size(); i < ncol; i++) colf.push_back(make_short4(-1, -1, -1, -1));
         int acc = 0;
         for (int ii = gp.m0; ii < gp.m1; ii++) {
             const Inst& in = inst[ii];
@@ -834,8 +857,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
                     const int lc = lidx[c];
                     auto ba = block_acc[lc / 16];
                     const int acc_col = ba.second + (lc - ba.first);
-                    auto ck = gcol_key[c];
-                    slot_of[pack(rl[r].key.first, rl[r].key.second, ck.first, ck.second)] = {gi, acc_col * 128 + (int)(r - r0)};
+                    slot_of[pack(rl[r].key.first, rl[r].key.second, gcol_key[c])] = {gi, acc_col * 128 + (int)(r - r0)};
                 }
             mtiles.push_back(M);
         }
@@ -875,7 +897,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     for (int64_t i = 0; i < p->nbins; i++) {
         auto rk = rkey(&p->bins[i * n]);
         auto ck = ckey(&p->bins[i * n]);
-        auto gs = slot_of.at(pack(rk.first, rk.second, ck.first, ck.second));
+        auto gs = slot_of.at(pack(rk.first, rk.second, ck));
         binmap[i] = make_int4(first[gs.first], nsplit[gs.first], gs.second, 0);
     }
     return POLY_OK;
@@ -901,7 +923,7 @@ poly_status ps_tc_prepare(PsPlan* p) {
         (s = up(&t->d_mtiles, h.mtiles.data(), h.mtiles.size() * sizeof(TcMTile))) ||
         (s = up(&t->d_runs, h.runs.data(), std::max<size_t>(1, h.runs.size()) * sizeof(int4))) ||
         (s = up(&t->d_rowf, h.rowf.data(), h.rowf.size() * sizeof(short2))) ||
-        (s = up(&t->d_colf, h.colf.data(), h.colf.size() * sizeof(short2))) ||
+        (s = up(&t->d_colf, h.colf.data(), h.colf.size() * sizeof(short4))) ||
         (s = up(&t->d_binmap, h.binmap.data(), std::max<size_t>(1, h.binmap.size()) * sizeof(int4))))
         return s;
     if ((s = ps_alloc(p, (void**)&t->d_partial, t->ctas.size() * (size_t)kTcAccMax * 128 * 8))) return s;
@@ -983,8 +1005,9 @@ static int diag_tc_tables(int N, int order, const double* edges, int nshell, uns
         rowf[2 * i + 1] = h.rowf[i].y;
     }
     for (size_t i = 0; colf && i < h.colf.size(); i++) {
-        colf[2 * i] = h.colf[i].x;
-        colf[2 * i + 1] = h.colf[i].y;
+        colf[3 * i] = h.colf[i].x;
+        colf[3 * i + 1] = h.colf[i].y;
+        colf[3 * i + 2] = h.colf[i].z;
     }
     for (size_t i = 0; binmap && i < h.binmap.size(); i++) {
         binmap[3 * i] = h.binmap[i].x;
@@ -1015,11 +1038,12 @@ poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {
         kern<<<(unsigned)t->ctas.size(), kTcThreads, t->smem_bytes, st>>>(
             t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->slot_cap, t->acc_max, t->window, (const TcCta*)t->d_ctas,
             (const TcGroup*)t->d_groups, (const TcMTile*)t->d_mtiles, (const int4*)t->d_runs,
-            (const short2*)t->d_rowf, (const short2*)t->d_colf, t->d_partial, t->d_err);
+            (const short2*)t->d_rowf, (const short4*)t->d_colf, t->d_partial, t->d_err);
         return cudaGetLastError();
     };
     if (t->ra == 2 && t->ca == 1) e = launch(tc_contract_kernel<2, 1>);
     else if (t->ra == 2 && t->ca == 2) e = launch(tc_contract_kernel<2, 2>);
+    else if (t->ra == 2 && t->ca == 3) e = launch(tc_contract_kernel<2, 3>);
     else e = launch(tc_contract_kernel<1, 1>);
     if (e) return POLY_ERR_CUDA;
     if (p->timing) cudaEventRecord(p->ev[3], st);

@@ -132,9 +132,11 @@ def test_matches_oracle(prec, N, order, nshell, kind, seed):
 
 # ------------------------------------------------------------------ orders 5 and 6 (CUDA-core path: pairs or
 # triples of fields against triples)
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "split_bf16"])
 @pytest.mark.parametrize("N,order,nshell,seed", [(32, 5, 5, 21), (48, 6, 6, 22), (48, 5, 8, 23)])
 def test_higher_orders_match_oracle(prec, N, order, nshell, seed):
+    if prec == "split_bf16" and order == 6:
+        pytest.skip("split-BF16 plans support orders 2 to 5")
     d = fieldgen.field("lognormal", N, seed, np.float32).astype(np.float64)
     plan, _, _, err = check_against_oracle(d, 1000.0, fieldgen.unit_edges(nshell), order, prec)
     assert plan.nbins > 50
@@ -197,9 +199,11 @@ def test_multipole_zero_is_the_plain_plan_and_refuses_the_adjoint():
 
 
 def test_higher_orders_refuse_split_bf16_and_the_adjoint():
+    """Split-BF16 plans stop at n = 5 (n = 6 would need rows of three fields); no order above 4 has an
+    adjoint."""
     e = fieldgen.unit_edges(4)
     with pytest.raises(ps.PolyError) as ei:
-        ps.Plan(32, 1000.0, 5, e, "split_bf16")
+        ps.Plan(48, 1000.0, 6, e, "split_bf16")
     assert ei.value.status == 6
     plan = ps.Plan(32, 1000.0, 5, e, "fp32")
     d = torch.from_numpy(fieldgen.field("lognormal", 32, 3, np.float32)).cuda()
@@ -259,12 +263,13 @@ def test_full_size_trispectrum_256cube_sampled(prec, field256, oracle256_n4):
     assert err.max() <= TOL[prec], err.max()
 
 
-def test_order5_128cube_sampled():
-    """n = 5 at the size bench.py measures it (128^3, 16 unit shells, 15,056 bins), FP32, on the bins among
-    five shells; counts bit-exact."""
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_order5_128cube_sampled(prec):
+    """n = 5 at the size bench.py measures it (128^3, 16 unit shells, 15,056 bins), FP32 and split-BF16, on the
+    bins among five shells; counts bit-exact."""
     e = fieldgen.unit_edges(16)
     d = fieldgen.field("lognormal", 128, 2, np.float32)
-    plan, B = gpu_estimate(d, 1000.0, e, 5, "fp32")
+    plan, B = gpu_estimate(d, 1000.0, e, 5, prec)
     assert plan.nbins == 15056
     shells = {16, 15, 9, 4, 1}
     idx = np.array([i for i, b in enumerate(plan.bins) if set(b.tolist()) <= shells])
@@ -272,7 +277,7 @@ def test_order5_128cube_sampled():
     ref = oracle.estimate(d.astype(np.float64), 1000.0, e, 5, bins=plan.bins[idx])
     assert np.array_equal(plan.counts[idx], ref["counts"])
     err = np.abs(B[idx] - ref["B"]) / (norm(1000.0, 128, 5) * ref["scale"])
-    assert err.max() <= TOL["fp32"], err.max()
+    assert err.max() <= TOL[prec], err.max()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
