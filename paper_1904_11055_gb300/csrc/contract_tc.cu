@@ -956,9 +956,10 @@ poly_status ps_tc_prepare(PsPlan* p) {
     if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
     // Accumulation window (chunks of 32 cells summed in FP32 in tensor memory before a drain).
     // The tensor-core FP32 accumulation error grows with the window; at 256^3 the largest
-    // error over the split-BF16 scale is 6e-7 for the bispectrum at 64 chunks, but 1.5e-5 for
-    // the trispectrum (products of four fields), 5.9e-6 at 16 chunks.
-    t->window = p->order >= 4 ? 16 : 64;
+    // error over the split-BF16 scale is 1.3e-6 for the bispectrum at 128 chunks (6e-7 at 64;
+    // the contraction takes 6.54 ms instead of 6.67), but 1.5e-5 for the trispectrum
+    // (products of four fields) at 64 chunks, 5.9e-6 at 16.
+    t->window = p->order >= 4 ? 16 : 128;
     const char* w = getenv("POLY_TC_WINDOW");
     if (w && atoi(w) > 0) t->window = atoi(w);
     return POLY_OK;
