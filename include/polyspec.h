@@ -69,10 +69,9 @@ typedef enum {
 
 /*
  * Create a plan for grid size N (one of 16, 24, 32, 48, 64, 96, 128, 160, 256),
- * box side L > 0, order n in [2, 6] (POLY_SPLIT_BF16: [2, 5], the tensor-core
- * contraction with rows of two fields against columns of one to three; n = 6
- * runs on the CUDA-core contraction, rows of three fields against columns of
- * three), `nshell` shells with `nshell + 1`
+ * box side L > 0, order n in [2, 6] (split-BF16 plans run the tensor-core
+ * contraction with rows of one to three fields against columns of one to
+ * three; FP32 and FP64 plans the CUDA-core one), `nshell` shells with `nshell + 1`
  * strictly increasing edges (host array, units of k_F, edges[0] >= 0).
  * K = the largest integer with K^2 < edges[nshell]^2 must satisfy 2K+1 <= N,
  * and n*K < N unless POLY_ALLOW_ALIAS.  The sorted shell tuples the bins are

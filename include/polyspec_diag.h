@@ -112,7 +112,7 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
  * The tensor-core contraction's host tables for a split-BF16 plan, computed on
  * the host alone: which products of fields (rows: the first legs, as a pair for
  * n >= 3; columns: the remaining legs) each block accumulates where, and where
- * the reduction finds each bin.  N, order (2..5), edges, nshell and flags as in
+ * the reduction finds each bin.  N, order (2..6), edges, nshell and flags as in
  * poly_plan_create, ell as in poly_plan_create_multipole (for ell > 0 the rows'
  * first factor is the weighted field slot k1 - 1 + nshell, and the groups are
  * held to fewer accumulator columns: the chunk stages 2 nshell field rows);
@@ -129,7 +129,7 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
  *   runs   int32 [][4]: first local column n0, columns nn, first accumulator
  *          column acc, M tile within the group: accumulator column acc + j of
  *          that M tile's row r is the product of row r and column n0 + j;
- *   rowf int16 [][2], colf int16 [][3]: 0-based field slots (-1: none);
+ *   rowf, colf int16 [][3]: 0-based field slots (-1: none);
  *   binmap int32 [nbins][3]: first block, blocks, slot = accumulator column x
  *          128 + row; bin b is the sum of that slot over those blocks.
  * Returns a poly_status.

@@ -31,6 +31,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <tuple>
 #include <array>
 #include <cstring>
 #include <map>
@@ -154,14 +155,24 @@ __device__ __forceinline__ uint32_t tc_row_key(int k) { return (uint32_t)(k * 12
 // 1024-aligned and the swizzle only flips address bits 4-6, so the 16-byte chunk c4 of
 // the half lies at r ^ (16 c4), one XOR with an immediate per load.
 template <int RA>
-__device__ __forceinline__ void tc_row_products(uint32_t r1, uint32_t r2, uint32_t* v) {
+__device__ __forceinline__ void tc_row_products(uint32_t r1, uint32_t r2, uint32_t r3, uint32_t* v) {
 #pragma unroll
     for (int c4 = 0; c4 < 4; c4++) {
         float4 x, y;
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w)
                      : "r"(r1 ^ (uint32_t)(16 * c4)));
-        if (RA == 2) {
+        if (RA == 3) {  // rows of three fields: the first and third multiplied in FP32 first
+            float4 z;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(z.x), "=f"(z.y), "=f"(z.z), "=f"(z.w)
+                         : "r"(r3 ^ (uint32_t)(16 * c4)));
+            x.x *= z.x;
+            x.y *= z.y;
+            x.z *= z.z;
+            x.w *= z.w;
+        }
+        if (RA >= 2) {
             asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
                          : "r"(r2 ^ (uint32_t)(16 * c4)));
@@ -179,15 +190,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_contract_kernel(const __grid_constant__ CUtensorMap fmap, int nshell, int stage_bytes, int bbuf_bytes,
                        int slot_cap, int acc_max, int window, const TcCta* __restrict__ ctas, const TcGroup* __restrict__ groups,
                        const TcMTile* __restrict__ mtiles, const int4* __restrict__ runs,
-                       const short2* __restrict__ rowf, const short4* __restrict__ colf, double* __restrict__ partial,
+                       const short4* __restrict__ rowf, const short4* __restrict__ colf, double* __restrict__ partial,
                        int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* s_d = base;                                        // kTcStages x stage_bytes (1024-aligned)
     uint8_t* s_b = s_d + kTcStages * stage_bytes;               // [slot][hi, lo] x bbuf_bytes
     float* s_acc = (float*)(s_b + 2 * slot_cap * bbuf_bytes);   // [acc_max cols][128 rows]
-    short2* s_rowf = (short2*)(s_acc + (size_t)acc_max * 128);  // [kTcMaxMT][128]
-    short4* s_colf = (short4*)(s_rowf + kTcMaxMT * 128);        // [kTcMaxCols]
+    short4* s_rowf = (short4*)(s_acc + (size_t)acc_max * 128);  // [kTcMaxMT][128]
+    short4* s_colf = s_rowf + kTcMaxMT * 128;                   // [kTcMaxCols]
     uint64_t* bars = (uint64_t*)(s_colf + kTcMaxCols);
     uint64_t* full = bars;                                      // [kTcStages]
     uint64_t* empty = full + kTcStages;                         // [kTcStages]
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int i = tid; i < kTcMaxMT * 128; i += kTcThreads) {
         const int m = i >> 7;
-        s_rowf[i] = m < nmt ? rowf[mtiles[grp.mt_off + m].row_off + (i & 127)] : make_short2(0, 0);
+        s_rowf[i] = m < nmt ? rowf[mtiles[grp.mt_off + m].row_off + (i & 127)] : make_short4(0, 0, 0, 0);
     }
     for (int i = tid; i < kTcMaxCols; i += kTcThreads) s_colf[i] = i < ncol ? colf[grp.col_off + i] : make_short4(-1, -1, -1, -1);
     for (int i = tid; i < acc_cols * 128; i += kTcThreads) s_acc[i] = 0.f;
@@ -364,12 +375,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int q = tw & 3, half = tw >> 2;  // lane quadrant, 16-cell half of the chunk
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int row = 32 * q + lane;
-        uint32_t key1[kTcMaxMT], key2[kTcMaxMT];  // this lane's row factors in each M tile (in-range shells)
+        // this lane's row factors in each M tile (in-range shells)
+        uint32_t key1[kTcMaxMT], key2[kTcMaxMT], key3[RA == 3 ? kTcMaxMT : 1];
 #pragma unroll
         for (int m = 0; m < kTcMaxMT; m++) {
-            const short2 f = s_rowf[m * 128 + row];
+            const short4 f = s_rowf[m * 128 + row];
             key1[m] = tc_row_key(f.x) ^ (uint32_t)(64 * half);
-            key2[m] = tc_row_key(RA == 2 ? f.y : 0) ^ (uint32_t)(64 * half);
+            key2[m] = tc_row_key(RA >= 2 ? f.y : 0) ^ (uint32_t)(64 * half);
+            if (RA == 3) key3[m] = tc_row_key(f.z) ^ (uint32_t)(64 * half);
         }
         const int ttid = tid % (kTcTeamWarps * 32);
         // stages team, team + 2, team + 4 in turn; slots i mod nslots
@@ -412,7 +425,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int m = 0; m < kTcMaxMT; m++) {
                 if (m < nmt) {
                     uint32_t v[16];
-                    tc_row_products<RA>(D + key1[m], D + key2[m], v);
+                    tc_row_products<RA>(D + key1[m], D + key2[m], RA == 3 ? D + key3[RA == 3 ? m : 0] : 0u, v);
                     tc::tmem_st16(abase + (uint32_t)(m * 32), v);
                 }
                 if (m == 0 && ttid < nbitems) tc_b_item<CA>(D, b_key1, b_key2, b_key3, Bh + b_off, Bl + b_off);
@@ -592,7 +605,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 static size_t tc_smem_bytes(int stage_bytes, int bbuf_bytes, int slots, int acc_max) {
     return 1024 + (size_t)kTcStages * stage_bytes + 2 * (size_t)slots * bbuf_bytes + (size_t)acc_max * 128 * 4 +
-           kTcMaxMT * 128 * 4 + kTcMaxCols * 8 + (2 * kTcStages + 2 * kTcMaxSlots + 3) * 8 + 64;
+           kTcMaxMT * 128 * 8 + kTcMaxCols * 8 + (2 * kTcStages + 2 * kTcMaxSlots + 3) * 8 + 64;
 }
 
 // Sorted 16-column blocks of one M tile -> runs (first block, block count), at most
@@ -629,27 +642,27 @@ struct TcTables {
     std::vector<TcGroup> groups;
     std::vector<TcMTile> mtiles;
     std::vector<int4> runs;
-    std::vector<short2> rowf;
-    std::vector<short4> colf;
+    std::vector<short4> rowf, colf;
     std::vector<int4> binmap;
 };
 
 static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     const int n = p->order;
-    t->ra = n >= 3 ? 2 : 1;
+    t->ra = n >= 6 ? 3 : (n >= 3 ? 2 : 1);
     t->ca = n - t->ra;
     t->nshell = p->nfield;  // field rows staged per chunk: nshell, or 2 nshell for a multipole plan
-    const bool ra2 = t->ra == 2;
+    const bool ra2 = t->ra >= 2;
     // a multipole plan's first leg reads the Legendre-weighted field of its shell (slot k1 - 1 + nshell)
     const int shift = p->ell > 0 ? p->nshell : 0;
 
     const int max_mt = std::max(1, std::min(kTcMaxMT, p->tc_max_mt));  // M tiles per group (tunable)
     using CKey = std::array<int, 3>;  // column factors (shells from 1; -1: none)
-    auto rkey = [&](const int32_t* b) { return std::make_pair(b[0], ra2 ? b[1] : -1); };
+    using RKey = std::array<int, 3>;  // row factors (shells from 1; -1: none)
+    auto rkey = [&](const int32_t* b) { return RKey{b[0], t->ra >= 2 ? b[1] : -1, t->ra == 3 ? b[2] : -1}; };
     auto ckey = [&](const int32_t* b) {
         return CKey{b[t->ra], t->ca >= 2 ? b[t->ra + 1] : -1, t->ca == 3 ? b[t->ra + 2] : -1};
     };
-    std::map<std::pair<int, int>, std::set<CKey>> rows;
+    std::map<RKey, std::set<CKey>> rows;
     std::set<CKey> allcols;
     for (int64_t i = 0; i < p->nbins; i++) {
         rows[rkey(&p->bins[i * n])].insert(ckey(&p->bins[i * n]));
@@ -673,7 +686,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     }
     struct Row {
         bool valid;
-        std::pair<int, int> key;  // shells (from 1) of the row factors; in range also for padding rows
+        RKey key;                 // shells (from 1) of the row factors; in range also for padding rows
         std::vector<int> cols;    // global column indices, sorted (empty for padding rows)
     };
     // A producer warp takes 32 rows.  Pair rows: the rows of one octet of 8
@@ -683,16 +696,16 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     // Lanes without a row repeat the block's first row (their accumulator rows are
     // never read).
     const int ns = p->nshell;
-    std::map<int, std::vector<std::pair<std::pair<int, int>, const std::set<CKey>*>>> octets;
+    std::map<int, std::vector<std::pair<RKey, const std::set<CKey>*>>> octets;
     for (auto& kv : rows) {
-        const int k1 = kv.first.first;
+        const int k1 = kv.first[0];
         octets[ra2 ? (k1 - 1) / kTcRowOctet : (k1 - 1) / 32].push_back({kv.first, &kv.second});
     }
     std::vector<std::vector<Row>> blocks;
     for (auto& ov : octets) {
         auto& lst = ov.second;
         std::sort(lst.begin(), lst.end(), [](const auto& x, const auto& y) {
-            return std::make_pair(x.first.second, x.first.first) < std::make_pair(y.first.second, y.first.first);
+            return std::make_tuple(x.first[1], x.first[2], x.first[0]) < std::make_tuple(y.first[1], y.first[2], y.first[0]);
         });
         for (size_t t = 0; t < lst.size(); t += 32) {
             std::vector<Row> blk(32);
@@ -724,7 +737,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     std::stable_sort(bl.begin(), bl.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
     std::vector<Row> rl;
     for (auto& b : bl) rl.insert(rl.end(), b.second->begin(), b.second->end());
-    while (rl.size() % 128) rl.push_back(Row{false, {1, ra2 ? 1 : -1}, {}});
+    while (rl.size() % 128) rl.push_back(Row{false, RKey{1, t->ra >= 2 ? 1 : -1, t->ra == 3 ? 1 : -1}, {}});
     const int nmt_total = (int)(rl.size() / 128);
     auto mt_cols = [&](int m) {
         std::set<int> s;
@@ -795,15 +808,15 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     std::vector<TcGroup>& groups = h.groups;
     std::vector<TcMTile>& mtiles = h.mtiles;
     std::vector<int4>& runs = h.runs;
-    std::vector<short2>& rowf = h.rowf;
+    std::vector<short4>& rowf = h.rowf;
     std::vector<short4>& colf = h.colf;
     // (row, col) keys -> (group, slot); shells (from 1, or -1 for none) packed one per byte (the keys
     // hold shell numbers, not field slots, so the weighted slots of a multipole plan do not enter them)
     static_assert(kPsMaxShells + 1 < 256, "a shell number + 1 must fit one byte of the packed key");
     if (p->nshell > kPsMaxShells) return POLY_ERR_UNSUPPORTED;
-    auto pack = [](int a, int b, const CKey& c) {
-        return (uint64_t)(a + 1) | (uint64_t)(b + 1) << 8 | (uint64_t)(c[0] + 1) << 16 | (uint64_t)(c[1] + 1) << 24 |
-               (uint64_t)(c[2] + 1) << 32;
+    auto pack = [](const RKey& r, const CKey& c) {
+        return (uint64_t)(r[0] + 1) | (uint64_t)(r[1] + 1) << 8 | (uint64_t)(r[2] + 1) << 16 |
+               (uint64_t)(c[0] + 1) << 24 | (uint64_t)(c[1] + 1) << 32 | (uint64_t)(c[2] + 1) << 40;
     };
     std::unordered_map<uint64_t, std::pair<int, int>> slot_of;
     slot_of.reserve((size_t)p->nbins * 2);
@@ -836,10 +849,9 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
             M.run_off = (int)runs.size();
             const size_t r0 = (size_t)m * 128, r1 = r0 + 128;
             for (size_t r = r0; r < r1; r++) {
-                short2 f;
-                f.x = (short)(rl[r].key.first - 1 + shift);
-                f.y = (short)(rl[r].key.second > 0 ? rl[r].key.second - 1 : -1);
-                rowf.push_back(f);
+                const RKey& k = rl[r].key;
+                rowf.push_back(make_short4((short)(k[0] - 1 + shift), (short)(k[1] > 0 ? k[1] - 1 : -1),
+                                           (short)(k[2] > 0 ? k[2] - 1 : -1), (short)-1));
             }
             std::set<int> cb;
             for (int c : in.cols) cb.insert(lidx[c] / 16);
@@ -857,7 +869,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
                     const int lc = lidx[c];
                     auto ba = block_acc[lc / 16];
                     const int acc_col = ba.second + (lc - ba.first);
-                    slot_of[pack(rl[r].key.first, rl[r].key.second, gcol_key[c])] = {gi, acc_col * 128 + (int)(r - r0)};
+                    slot_of[pack(rl[r].key, gcol_key[c])] = {gi, acc_col * 128 + (int)(r - r0)};
                 }
             mtiles.push_back(M);
         }
@@ -897,7 +909,7 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     for (int64_t i = 0; i < p->nbins; i++) {
         auto rk = rkey(&p->bins[i * n]);
         auto ck = ckey(&p->bins[i * n]);
-        auto gs = slot_of.at(pack(rk.first, rk.second, ck));
+        auto gs = slot_of.at(pack(rk, ck));
         binmap[i] = make_int4(first[gs.first], nsplit[gs.first], gs.second, 0);
     }
     return POLY_OK;
@@ -922,7 +934,7 @@ poly_status ps_tc_prepare(PsPlan* p) {
         (s = up(&t->d_groups, groups.data(), groups.size() * sizeof(TcGroup))) ||
         (s = up(&t->d_mtiles, h.mtiles.data(), h.mtiles.size() * sizeof(TcMTile))) ||
         (s = up(&t->d_runs, h.runs.data(), std::max<size_t>(1, h.runs.size()) * sizeof(int4))) ||
-        (s = up(&t->d_rowf, h.rowf.data(), h.rowf.size() * sizeof(short2))) ||
+        (s = up(&t->d_rowf, h.rowf.data(), h.rowf.size() * sizeof(short4))) ||
         (s = up(&t->d_colf, h.colf.data(), h.colf.size() * sizeof(short4))) ||
         (s = up(&t->d_binmap, h.binmap.data(), std::max<size_t>(1, h.binmap.size()) * sizeof(int4))))
         return s;
@@ -1002,8 +1014,9 @@ static int diag_tc_tables(int N, int order, const double* edges, int nshell, uns
         std::memcpy(runs + 4 * i, v, sizeof v);
     }
     for (size_t i = 0; rowf && i < h.rowf.size(); i++) {
-        rowf[2 * i] = h.rowf[i].x;
-        rowf[2 * i + 1] = h.rowf[i].y;
+        rowf[3 * i] = h.rowf[i].x;
+        rowf[3 * i + 1] = h.rowf[i].y;
+        rowf[3 * i + 2] = h.rowf[i].z;
     }
     for (size_t i = 0; colf && i < h.colf.size(); i++) {
         colf[3 * i] = h.colf[i].x;
@@ -1039,12 +1052,13 @@ poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {
         kern<<<(unsigned)t->ctas.size(), kTcThreads, t->smem_bytes, st>>>(
             t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->slot_cap, t->acc_max, t->window, (const TcCta*)t->d_ctas,
             (const TcGroup*)t->d_groups, (const TcMTile*)t->d_mtiles, (const int4*)t->d_runs,
-            (const short2*)t->d_rowf, (const short4*)t->d_colf, t->d_partial, t->d_err);
+            (const short4*)t->d_rowf, (const short4*)t->d_colf, t->d_partial, t->d_err);
         return cudaGetLastError();
     };
     if (t->ra == 2 && t->ca == 1) e = launch(tc_contract_kernel<2, 1>);
     else if (t->ra == 2 && t->ca == 2) e = launch(tc_contract_kernel<2, 2>);
     else if (t->ra == 2 && t->ca == 3) e = launch(tc_contract_kernel<2, 3>);
+    else if (t->ra == 3 && t->ca == 3) e = launch(tc_contract_kernel<3, 3>);
     else e = launch(tc_contract_kernel<1, 1>);
     if (e) return POLY_ERR_CUDA;
     if (p->timing) cudaEventRecord(p->ev[3], st);

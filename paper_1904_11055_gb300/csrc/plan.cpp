@@ -550,8 +550,7 @@ poly_status ps_plan_host_tables(PsPlan* p, int N, double L, int order, int nshel
     if (!edges || nshell < 1 || nshell > kPsMaxShells) return set_error(POLY_ERR_ARG, "nshell must be in [1, 128]");
     if (ell < 0 || ell > 8 || (ell & 1)) return set_error(POLY_ERR_ARG, "ell must be even, in [0, 8]");
     if (order < 2 || order > 6) return set_error(POLY_ERR_UNSUPPORTED, "order must be in [2, 6]");
-    if (order > 5 && prec == POLY_SPLIT_BF16)
-        return set_error(POLY_ERR_UNSUPPORTED, "split-BF16 plans support orders 2 to 5 (FP32 and FP64: up to 6)");
+
     if (!(L > 0) || !std::isfinite(L)) return set_error(POLY_ERR_ARG, "L must be positive");
     if (flags & ~(POLY_BINS_ALL_SORTED | POLY_ALLOW_ALIAS)) return set_error(POLY_ERR_ARG, "unknown flag");
     if (!ps_supported_n(N)) return set_error(POLY_ERR_UNSUPPORTED, "grid size N not in the supported set");

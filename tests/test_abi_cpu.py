@@ -46,7 +46,6 @@ def test_status_strings(lib):
 
 @pytest.mark.parametrize("kwargs,status", [
     (dict(N=64, order=7), 6),                                          # order outside [2, 6]
-    (dict(N=64, order=6, edges=np.arange(6) + 0.5, prec=1), 6),         # split-BF16 only up to n = 5
     (dict(N=64, order=6, edges=np.arange(12) + 0.5), 2),                # 6 * 11 >= 64: aliasing
     (dict(N=50), 6),                                                   # N not supported
     (dict(N=64, edges=[0.5, 1.5, 1.5]), 1),                            # edges not increasing
@@ -66,9 +65,9 @@ def test_argument_validation_before_device(lib, kwargs, status):
     assert ei.value.status == status
 
 
-@pytest.mark.parametrize("ell,prec,order,status", [(1, 0, 3, 1), (10, 0, 3, 1), (-2, 3, 3, 1), (2, 1, 6, 6)])
+@pytest.mark.parametrize("ell,prec,order,status", [(1, 0, 3, 1), (10, 0, 3, 1), (-2, 3, 3, 1), (3, 1, 3, 1)])
 def test_multipole_plans_validate_ell_and_precision(lib, ell, prec, order, status):
-    """Bad ell is an argument error; split-BF16 multipole plans stop at order 5, as the monopole ones."""
+    """Bad ell is an argument error, in every precision."""
     with pytest.raises(ps.PolyError) as ei:
         ps.poly_plan_create_multipole(64, 1000.0, order, np.arange(17) + 0.5, prec, 0, ell)
     assert ei.value.status == status

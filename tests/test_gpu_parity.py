@@ -135,8 +135,6 @@ def test_matches_oracle(prec, N, order, nshell, kind, seed):
 @pytest.mark.parametrize("prec", ["fp32", "fp64", "split_bf16"])
 @pytest.mark.parametrize("N,order,nshell,seed", [(32, 5, 5, 21), (48, 6, 6, 22), (48, 5, 8, 23)])
 def test_higher_orders_match_oracle(prec, N, order, nshell, seed):
-    if prec == "split_bf16" and order == 6:
-        pytest.skip("split-BF16 plans support orders 2 to 5")
     d = fieldgen.field("lognormal", N, seed, np.float32).astype(np.float64)
     plan, _, _, err = check_against_oracle(d, 1000.0, fieldgen.unit_edges(nshell), order, prec)
     assert plan.nbins > 50
@@ -198,13 +196,9 @@ def test_multipole_zero_is_the_plain_plan_and_refuses_the_adjoint():
     assert ei.value.status == 6
 
 
-def test_higher_orders_refuse_split_bf16_and_the_adjoint():
-    """Split-BF16 plans stop at n = 5 (n = 6 would need rows of three fields); no order above 4 has an
-    adjoint."""
+def test_higher_orders_refuse_the_adjoint():
+    """No order above 4 has an adjoint."""
     e = fieldgen.unit_edges(4)
-    with pytest.raises(ps.PolyError) as ei:
-        ps.Plan(48, 1000.0, 6, e, "split_bf16")
-    assert ei.value.status == 6
     plan = ps.Plan(32, 1000.0, 5, e, "fp32")
     d = torch.from_numpy(fieldgen.field("lognormal", 32, 3, np.float32)).cuda()
     with pytest.raises(ps.PolyError) as ei:

@@ -170,7 +170,7 @@ def tc_tables(lib, N, order, edges, sms=152, max_mt=4, cta_mult=4, flags=0, ell=
         return rc, None
     nb, nc, ng, nm, nr, nrow, ncol = (int(v) for v in sizes)
     t = dict(ctas=np.zeros((nc, 3), np.int64), groups=np.zeros((ng, 5), np.int32), mtiles=np.zeros((nm, 3), np.int32),
-             runs=np.zeros((nr, 4), np.int32), rowf=np.zeros((nrow, 2), np.int16), colf=np.zeros((ncol, 3), np.int16),
+             runs=np.zeros((nr, 4), np.int32), rowf=np.zeros((nrow, 3), np.int16), colf=np.zeros((ncol, 3), np.int16),
              binmap=np.zeros((nb, 3), np.int32))
     ptrs = [t[k].ctypes.data for k in ("ctas", "groups", "mtiles", "runs", "rowf", "colf", "binmap")]
     assert fn(*args, sizes.ctypes.data, *ptrs) == 0
@@ -180,7 +180,7 @@ def tc_tables(lib, N, order, edges, sms=152, max_mt=4, cta_mult=4, flags=0, ell=
 def check_tc_tables(t, bins, N, nshell, max_mt, shift=0):
     """shift: the first row factor's slot offset (nshell for a multipole plan's weighted fields)."""
     order = bins.shape[1]
-    ra = 2 if order >= 3 else 1
+    ra = 3 if order >= 6 else (2 if order >= 3 else 1)
     ctas, groups, mtiles, runs, rowf, colf, bm = (t[k] for k in ("ctas", "groups", "mtiles", "runs", "rowf", "colf",
                                                                 "binmap"))
     ng, nchunks = len(groups), (N ** 3 + 31) // 32
@@ -202,7 +202,8 @@ def check_tc_tables(t, bins, N, nshell, max_mt, shift=0):
             assert 1 <= nrun <= 4
             rf = rowf[row_off:row_off + 128]
             assert np.all((rf[:, 0] >= shift) & (rf[:, 0] < nshell + shift))  # padding rows repeat a real row
-            assert np.all(rf[:, 1] < nshell) and np.all((rf[:, 1] >= 0) == (ra == 2))
+            assert np.all(rf[:, 1] < nshell) and np.all((rf[:, 1] >= 0) == (ra >= 2))
+            assert np.all(rf[:, 2] < nshell) and np.all((rf[:, 2] >= 0) == (ra == 3))
             for n0, nn, acc, mloc in runs[run_off:run_off + nrun]:
                 assert mloc == m - mt_off and nn % 16 == 0 and n0 % 16 == 0 and n0 + nn <= ncol
                 assert acc + nn <= acc_cols and np.all(tab[acc:acc + nn, 0] < 0)
@@ -222,7 +223,7 @@ def check_tc_tables(t, bins, N, nshell, max_mt, shift=0):
     cf = colf[col].astype(np.int64)
     legs = bins.astype(np.int64) - 1
     pad = -np.ones(len(bins), np.int64)
-    want_row = np.stack([legs[:, 0] + shift, legs[:, 1] if ra == 2 else pad], 1)
+    want_row = np.stack([legs[:, 0] + shift, legs[:, 1] if ra >= 2 else pad, legs[:, 2] if ra == 3 else pad], 1)
     rest = legs[:, ra:]
     want_col = np.stack([rest[:, 0], rest[:, 1] if rest.shape[1] > 1 else pad,
                          rest[:, 2] if rest.shape[1] > 2 else pad], 1)
@@ -243,7 +244,7 @@ def test_tc_tables_bispectrum_256cube_64shells(lib, max_mt, cta_mult):
 
 @pytest.mark.parametrize("N,order,nshell,width", [(256, 4, 32, 1.5), (96, 4, 10, 2.0), (48, 3, 12, 1.0),
                                                   (64, 2, 30, 1.0), (128, 3, 40, 1.0), (128, 5, 16, 1.0),
-                                                  (48, 5, 8, 1.0)])
+                                                  (48, 5, 8, 1.0), (48, 6, 6, 1.0), (128, 6, 8, 1.0)])
 @pytest.mark.parametrize("sms", [152, 20])
 def test_tc_tables_other_plans(lib, N, order, nshell, width, sms):
     """The trispectrum (its pair columns split into several instances), the power spectrum, small grids."""
@@ -266,7 +267,7 @@ def test_tc_tables_multipole_plans(lib, N, order, nshell, ell, max_mt):
 
 
 @pytest.mark.parametrize("kwargs,status", [
-    (dict(order=6), STATUS["POLY_ERR_UNSUPPORTED"]),
+    (dict(order=7), STATUS["POLY_ERR_UNSUPPORTED"]),
     (dict(sms=0), STATUS["POLY_ERR_ARG"]),
     (dict(N=16), STATUS["POLY_ERR_ALIAS"]),
 ])
