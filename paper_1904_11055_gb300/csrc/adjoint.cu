@@ -107,6 +107,8 @@ void ps_at_free(AtState* S);
 
 struct AdjTables {
     int nent = 0;
+    void* d_Wall = nullptr;      // batched forward transforms of the G_m: intermediates and spectra, or NULL
+    void* d_fhat_all = nullptr;
     AtState* at = nullptr;  // tensor-core form of the per-cell contraction (bispectrum, split-BF16)
     void *d_moff = nullptr, *d_ent = nullptr, *d_eoff = nullptr, *d_ebins = nullptr, *d_w = nullptr;
     std::vector<int> line_off;  // host copy of the plan's line offsets
@@ -191,6 +193,13 @@ static poly_status adj_prepare(PsPlan* p, AdjTables& A) {
     const size_t nl = (size_t)(2 * p->K + 1) * (p->K + 1) * (2 * p->K + 1);
     if ((s = ps_alloc(p, &p->d_G, (size_t)p->nshell * n3 * es))) return s;
     if ((s = ps_alloc(p, &p->d_ghat, nl * 2 * es))) return s;
+    // the G_m's forward transforms in one batch when their planes fit shared memory (no spill buffer)
+    if (ps_plane_needs_spill(p->N, p->K, p->is_double) == 0) {
+        const size_t wsz = (size_t)p->N * (2 * p->K + 1) * (p->K + 1);
+        if ((s = ps_alloc(p, &A.d_Wall, (size_t)p->nshell * wsz * 2 * es)) ||
+            (s = ps_alloc(p, &A.d_fhat_all, (size_t)p->nshell * nl * 2 * es)))
+            return s;
+    }
     return POLY_OK;
 }
 
@@ -245,23 +254,39 @@ poly_status ps_backward_impl(PsPlan* p, const void* delta, const double* dL_dB, 
     const size_t es = dbl ? 8 : 4;
     if ((e = cudaMemsetAsync(p->d_ghat, 0, nl * 2 * es, st))) return POLY_ERR_CUDA;
     const double scale = ps_norm(p) / (double)ncell;
+    // forward transforms of all G_m: one batched launch pair when the per-field outputs fit (A.d_Wall), else
+    // one field at a time through the plan's workspace
+    const size_t wsz = (size_t)p->N * (2 * p->K + 1) * (p->K + 1);
+    const bool batched = A.d_Wall != nullptr;
+    if (batched) {
+        if ((e = ps_forward_batched(p->N, dbl, p->d_G, p->nshell, p->K, p->d_tw_fwd, A.d_Wall, A.d_fhat_all, nullptr,
+                                    st)))
+            return POLY_ERR_CUDA;
+        p->launches += 2;
+    }
     for (int m = 0; m < p->nshell; m++) {
         const void* Gm = (const char*)p->d_G + (size_t)m * ncell * es;
-        if ((e = ps_forward(p->N, dbl, Gm, p->K, p->d_tw_fwd, p->d_W, p->d_fhat, p->d_spill, st))) return POLY_ERR_CUDA;
+        const void* Fm = batched ? (const void*)((const char*)A.d_fhat_all + (size_t)m * nl * 2 * es) : p->d_fhat;
+        if (!batched) {
+            if ((e = ps_forward(p->N, dbl, Gm, p->K, p->d_tw_fwd, p->d_W, p->d_fhat, p->d_spill, st)))
+                return POLY_ERR_CUDA;
+            p->launches += 2;
+        }
         const int lb = A.line_off[m], le = A.line_off[m + 1];
         if (le > lb) {
             dim3 blk(32, 8);
             const unsigned nb = (unsigned)std::min(1024, (le - lb + 7) / 8);
             if (dbl)
-                shell_gather_kernel<double><<<nb, blk, 0, st>>>((const Cx<double>*)p->d_fhat, (const short4*)p->d_lines,
+                shell_gather_kernel<double><<<nb, blk, 0, st>>>((const Cx<double>*)Fm, (const short4*)p->d_lines,
                                                                lb, le, p->K, scale, (Cx<double>*)p->d_ghat);
             else
-                shell_gather_kernel<float><<<nb, blk, 0, st>>>((const Cx<float>*)p->d_fhat, (const short4*)p->d_lines,
+                shell_gather_kernel<float><<<nb, blk, 0, st>>>((const Cx<float>*)Fm, (const short4*)p->d_lines,
                                                               lb, le, p->K, (float)scale, (Cx<float>*)p->d_ghat);
             if ((e = cudaGetLastError())) return POLY_ERR_CUDA;
         }
-        p->launches += 3;
+        p->launches += 1;
     }
+    (void)wsz;
     // one inverse transform over the union of the shells
     if (!ps_xpre_fits(p, p->nshell, 1)) return POLY_ERR_ARG;
     if ((e = ps_inverse(p->N, dbl, 0, p->d_ghat, p->d_lines, p->d_line_off, p->nshell, 1, p->K, 0, p->N, p->d_tw_inv,

@@ -4,9 +4,9 @@
 #include "kernels.h"
 
 cudaError_t ps_forward_f32(int n, const void* delta, int K, const void* tw_fwd, void* W, void* fhat, void* spill,
-                           cudaStream_t st);
+                           cudaStream_t st, int nfields);
 cudaError_t ps_forward_f64(int n, const void* delta, int K, const void* tw_fwd, void* W, void* fhat, void* spill,
-                           cudaStream_t st);
+                           cudaStream_t st, int nfields);
 cudaError_t ps_inverse_f32(int n, int unity, const void* fhat, const void* lines, const int* line_off, int s0, int ns,
                            int K, int x0, int nx, const void* tw_inv, void* out, size_t out_stride, void* spill,
                            void* xpre, int max_lines, int tile_ns, cudaStream_t st);
@@ -41,8 +41,14 @@ int ps_supported_n(int n) {
 
 cudaError_t ps_forward(int n, int is_double, const void* delta, int K, const void* tw_fwd, void* W, void* fhat,
                        void* spill, cudaStream_t st) {
-    return is_double ? ps_forward_f64(n, delta, K, tw_fwd, W, fhat, spill, st)
-                     : ps_forward_f32(n, delta, K, tw_fwd, W, fhat, spill, st);
+    return ps_forward_batched(n, is_double, delta, 1, K, tw_fwd, W, fhat, spill, st);
+}
+
+cudaError_t ps_forward_batched(int n, int is_double, const void* delta, int nfields, int K, const void* tw_fwd, void* W,
+                               void* fhat, void* spill, cudaStream_t st) {
+    if (nfields < 1 || nfields > 65535) return cudaErrorInvalidValue;
+    return is_double ? ps_forward_f64(n, delta, K, tw_fwd, W, fhat, spill, st, nfields)
+                     : ps_forward_f32(n, delta, K, tw_fwd, W, fhat, spill, st, nfields);
 }
 
 cudaError_t ps_inverse(int n, int is_double, int unity, const void* fhat, const void* lines, const int* line_off, int s0,

@@ -4,11 +4,11 @@
 using namespace ps;
 
 cudaError_t ps_forward_f32(int n, const void* delta, int K, const void* tw_fwd, void* W, void* fhat, void* spill,
-                            cudaStream_t st) {
+                            cudaStream_t st, int nfields) {
 #define PS_CASE(NN)                                                                                             \
     case NN:                                                                                                    \
         return forward_n<float, NN>((const float*)delta, K, (const Cx<double>*)tw_fwd, (Cx<float>*)W, (Cx<float>*)fhat,  \
-                                 (Cx<float>*)spill, st);
+                                 (Cx<float>*)spill, st, nfields);
     switch (n) { PS_FOR_EACH_N(PS_CASE) }
 #undef PS_CASE
     return cudaErrorInvalidValue;

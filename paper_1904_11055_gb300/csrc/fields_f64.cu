@@ -4,11 +4,11 @@
 using namespace ps;
 
 cudaError_t ps_forward_f64(int n, const void* delta, int K, const void* tw_fwd, void* W, void* fhat, void* spill,
-                            cudaStream_t st) {
+                            cudaStream_t st, int nfields) {
 #define PS_CASE(NN)                                                                                             \
     case NN:                                                                                                    \
         return forward_n<double, NN>((const double*)delta, K, (const Cx<double>*)tw_fwd, (Cx<double>*)W, (Cx<double>*)fhat,  \
-                                 (Cx<double>*)spill, st);
+                                 (Cx<double>*)spill, st, nfields);
     switch (n) { PS_FOR_EACH_N(PS_CASE) }
 #undef PS_CASE
     return cudaErrorInvalidValue;

@@ -54,7 +54,10 @@ __global__ void __launch_bounds__(kPlaneThreads) fwd_plane_kernel(const T* __res
     Cx<T>* s_z = s_tw + N;                              // per-warp row buffers
     Cx<T>* s_t = s_z + (size_t)kPlaneWarps * LPW * ls;  // (K+1) lines of ls
     const int x = blockIdx.x;
-    Cx<T>* Tb = SPILL ? spill + (size_t)blockIdx.x * (K + 1) * ls : s_t;
+    // blockIdx.y: the field of a batch (fields N^3 apart, their W outputs N (2K+1)(K+1) apart)
+    delta += (size_t)blockIdx.y * N * N * N;
+    W += (size_t)blockIdx.y * N * (2 * K + 1) * (K + 1);
+    Cx<T>* Tb = SPILL ? spill + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * (K + 1) * ls : s_t;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     load_twiddles(s_tw, g_tw, N);
     __syncthreads();
@@ -108,6 +111,9 @@ __global__ void __launch_bounds__(kPlaneThreads) fwd_xlines_kernel(const Cx<T>* 
     const int nl = (2 * K + 1) * (K + 1);
     const int l0 = blockIdx.x * kXLines;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // blockIdx.y: the field of a batch
+    W += (size_t)blockIdx.y * N * nl;
+    fhat += (size_t)blockIdx.y * nl * (2 * K + 1);
     load_twiddles(s_tw, g_tw, N);
     for (int e = threadIdx.x; e < N * kXLines; e += blockDim.x) {
         const int x = e / kXLines, l = e - (e / kXLines) * kXLines;
@@ -400,9 +406,11 @@ static size_t xlines_smem_n() {
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
+// nfields fields N^3 apart -> W and fhat of each, (N (2K+1)(K+1)) and ((2K+1)(K+1)(2K+1)) apart; the spill
+// buffer (when the plane does not fit shared memory) holds nfields * N blocks
 template <typename T, int N>
 static cudaError_t forward_n(const T* delta, int K, const Cx<double>* tw_fwd, Cx<T>* W, Cx<T>* fhat, Cx<T>* spill,
-                             cudaStream_t st) {
+                             cudaStream_t st, int nfields = 1) {
     bool spill_on = plane_smem_n<T, N>(K, false) > kMaxSmem;
     if (spill_on && !spill) return cudaErrorInvalidValue;
     size_t sm = plane_smem_n<T, N>(K, spill_on);
@@ -410,18 +418,18 @@ static cudaError_t forward_n(const T* delta, int K, const Cx<double>* tw_fwd, Cx
     if (spill_on) {
         auto k = fwd_plane_kernel<T, N, true>;
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        k<<<N, kPlaneThreads, sm, st>>>(delta, K, tw_fwd, W, spill);
+        k<<<dim3(N, nfields), kPlaneThreads, sm, st>>>(delta, K, tw_fwd, W, spill);
     } else {
         auto k = fwd_plane_kernel<T, N, false>;
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        k<<<N, kPlaneThreads, sm, st>>>(delta, K, tw_fwd, W, nullptr);
+        k<<<dim3(N, nfields), kPlaneThreads, sm, st>>>(delta, K, tw_fwd, W, nullptr);
     }
     if ((e = cudaGetLastError())) return e;
     const int nl = (2 * K + 1) * (K + 1);
     size_t smx = xlines_smem_n<T, N>();
     auto kx = fwd_xlines_kernel<T, N>;
     if ((e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx))) return e;
-    kx<<<(nl + kXLines - 1) / kXLines, kPlaneThreads, smx, st>>>(W, K, tw_fwd, fhat);
+    kx<<<dim3((nl + kXLines - 1) / kXLines, nfields), kPlaneThreads, smx, st>>>(W, K, tw_fwd, fhat);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,10 @@ size_t ps_spill_elems(int n, int K, int nblocks, int is_double);
 // delta [N^3] real -> W [N][(2K+1)(K+1)] -> fhat [(2K+1)(K+1)][2K+1] (complex, same precision)
 cudaError_t ps_forward(int n, int is_double, const void* delta, int K, const void* tw_fwd, void* W, void* fhat,
                        void* spill, cudaStream_t st);
+// the same for nfields fields N^3 apart in one launch pair: W and fhat hold one output per field, N (2K+1)(K+1)
+// and (2K+1)(K+1)(2K+1) complex values apart; spill (when needed) nfields * N blocks
+cudaError_t ps_forward_batched(int n, int is_double, const void* delta, int nfields, int K, const void* tw_fwd, void* W,
+                               void* fhat, void* spill, cudaStream_t st);
 // shells s0..s0+ns-1, planes x0..x0+nx-1 -> out[(s-s0)*out_stride + (x-x0)*N*N + y*N + z].
 // xpre != NULL (and not unity): first run the x pass into xpre (sum over shells of lines * N complex values;
 // max_lines = the largest line count of the shells), then scatter; otherwise gather along x in the plane kernel.
