@@ -10,14 +10,18 @@
 // (round-to-nearest adds), and the per-block sums are reduced in FP64 across
 // blocks in a fixed order.
 //
-// Block layout: 16 producer warps in two teams and 4 issuer warps.  The last
+// Block layout: producer warps in teams of 8 (three teams where every group has
+// three A/B slots, else two) and 4 issuer warps.  The last
 // issuer warp when the block has fewer than 4 M tiles (else issuer 0) streams
 // 32-cell chunks of all shell fields (one contiguous block of the cell-tiled
 // field layout) into shared memory with TMA (128-byte swizzle).
-// Team t produces chunks t, t + 2, ..., so that one team's barrier waits overlap
-// the other team's work; chunk i goes to A/B slot i mod nslots (up to 4 slots,
-// as many as tensor memory holds next to the accumulators), so a team reuses a
-// slot only after the MMAs of an earlier chunk than its previous one.  Producer warp w of a team owns
+// With T teams, team t produces chunks t, t + T, ..., so that one team's barrier
+// waits overlap the other teams' work; chunk i goes to A/B slot i mod nslots (up
+// to 4 slots, as many as tensor memory holds next to the accumulators, and at
+// least T), so a team reuses a slot only after the MMAs of a chunk no later than its previous one.
+// Three teams at 72 registers a thread instead of two at 96 keep more producer warps
+// in flight: the products are issue- and latency-bound.
+// Producer warp w of a team owns
 // TMEM lane quadrant w % 4 and the 16-cell half w / 4 of a chunk: in every M tile
 // of the block, each lane forms the 16 products of its row in its half and
 // writes their hi and lo parts with one 16-column tcgen05.st (per M tile the A
@@ -50,12 +54,13 @@
 namespace ps {
 
 constexpr int kTcChunk = 32;         // cells per chunk (K of one pipeline step)
-constexpr int kTcStages = 6;         // TMA stages (even: each team cycles through its own three)
+constexpr int kTcStages = 6;         // TMA stages (a multiple of 2 and 3: each team cycles through its own)
 constexpr int kTcMaxMT = 4;          // M tiles per block
 constexpr int kTcTeamWarps = 8;      // producer warps per team: 4 lane quadrants x 2 pairs of M tiles
-constexpr int kTcProducers = 2 * kTcTeamWarps * 32;
 constexpr int kTcIssuers = kTcMaxMT;  // one MMA-issuing warp per M tile
-constexpr int kTcThreads = kTcProducers + 32 * kTcIssuers;
+// threads of a block with `teams` producer teams (team t takes chunks t, t + teams, ...):
+// three teams where every group has three A/B slots, else two
+__host__ __device__ constexpr int tc_threads(int teams) { return (teams * kTcTeamWarps + kTcIssuers) * 32; }
 constexpr int kTcAccMax = 256;       // accumulator columns per block
 constexpr int kTcABase = 256;        // first TMEM column of the A operand in the self-test
 constexpr int kTcMaxRunsMt = 4;      // N runs per M tile
@@ -185,8 +190,8 @@ __device__ __forceinline__ void tc_row_products(uint32_t r1, uint32_t r2, uint32
     }
 }
 
-template <int RA, int CA>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <int RA, int CA, int TEAMS>
+__global__ void __launch_bounds__(tc_threads(TEAMS), 1)
     tc_contract_kernel(const __grid_constant__ CUtensorMap fmap, int nshell, int stage_bytes, int bbuf_bytes,
                        int slot_cap, int acc_max, int window, const TcCta* __restrict__ ctas, const TcGroup* __restrict__ groups,
                        const TcMTile* __restrict__ mtiles, const int4* __restrict__ runs,
@@ -215,12 +220,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const TcGroup grp = groups[cta.group];
     const int nch = (int)(cta.c1 - cta.c0);
     const int nmt = grp.nmt, ncol = grp.ncol, acc_cols = grp.acc_cols;
-    constexpr int kProdWarps = kTcProducers / 32;
+    constexpr int kTcThreads = tc_threads(TEAMS);
+    constexpr int kProdWarps = TEAMS * kTcTeamWarps;
     // TMEM columns: accumulators [0, a0), then the A slots of nmt x 32 columns (hi 16 + lo 16 per M tile)
     const int a0 = (acc_cols + 31) / 32 * 32;
     const uint32_t slot_cols = (uint32_t)(nmt * 32);
     int nslots = (512 - a0) / (int)slot_cols;
     nslots = nslots < slot_cap ? nslots : slot_cap;  // >= 2: a0 <= 256 and nmt <= 4
+    // Producer teams at work: at most nslots.  A team reuses a slot after the MMAs of chunk
+    // i - nslots; the parity wait on that slot's barrier is unambiguous only if the slot's
+    // use before that (chunk i - 2 nslots) is known complete, which the team's own previous
+    // wait (chunk i - nteams - nslots, MMAs committed in chunk order) implies when
+    // nteams <= nslots.
+    const int nteams = nslots < TEAMS ? nslots : TEAMS;
 
     if (tid == 0) {
         for (int st = 0; st < kTcStages; st++) {
@@ -406,7 +418,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int st = team;
         uint32_t ph_full = 0;
         TcWindow win(team, window);
-        for (int i = team; i < nch; i += 2) {
+        for (int i = team < nteams ? team : nch; i < nch; i += nteams) {
             if (!tc::mbar_wait_warp(&full[st], ph_full, s_abort)) break;
             const int slot = i % nslots, use = i / nslots;  // slot and its use count
             if (use > 0) {
@@ -447,7 +459,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc::mbar_arrive(&empty[st]);
                 tc::mbar_arrive(&produced[slot]);
             }
-            st += 2;
+            st += nteams;
             if (st >= kTcStages) {
                 st -= kTcStages;
                 ph_full ^= 1u;
@@ -582,6 +594,7 @@ struct TcState {
     int stage_bytes = 0, bbuf_bytes = 0, smem_bytes = 0;
     int window = 64;
     int acc_max = 256, slot_cap = 2;
+    int teams = 2;  // producer teams per block
     int ra = 2, ca = 1;
     void *d_ctas = nullptr, *d_groups = nullptr, *d_mtiles = nullptr, *d_runs = nullptr, *d_rowf = nullptr,
          *d_colf = nullptr, *d_binmap = nullptr;
@@ -966,6 +979,11 @@ poly_status ps_tc_prepare(PsPlan* p) {
         t->slot_cap--;
     t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc);
     if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
+    // a third producer team where every group has three A/B slots (the kernel's slot count:
+    // what tensor memory holds beside the group's accumulators, at most slot_cap)
+    int min_slots = t->slot_cap;
+    for (auto& g : groups) min_slots = std::min(min_slots, (512 - (g.acc_cols + 31) / 32 * 32) / (g.nmt * 32));
+    t->teams = min_slots >= 3 ? 3 : 2;
     // Accumulation window (chunks of 32 cells summed in FP32 in tensor memory before a drain).
     // The tensor-core FP32 accumulation error grows with the window; at 256^3 the largest
     // error over the split-BF16 scale is 1.3e-6 for the bispectrum at 128 chunks (6e-7 at 64;
@@ -1046,20 +1064,21 @@ poly_status ps_tc_sums(PsPlan* p, cudaStream_t st) {
     TcState* t = p->tc;
     if (!t) return POLY_ERR_UNSUPPORTED;
     cudaError_t e;
-    auto launch = [&](auto kern) -> cudaError_t {
+    auto launch = [&](auto kern, int threads) -> cudaError_t {
         cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t->smem_bytes);
         if (e2) return e2;
-        kern<<<(unsigned)t->ctas.size(), kTcThreads, t->smem_bytes, st>>>(
+        kern<<<(unsigned)t->ctas.size(), threads, t->smem_bytes, st>>>(
             t->fmap, t->nshell, t->stage_bytes, t->bbuf_bytes, t->slot_cap, t->acc_max, t->window, (const TcCta*)t->d_ctas,
             (const TcGroup*)t->d_groups, (const TcMTile*)t->d_mtiles, (const int4*)t->d_runs,
             (const short4*)t->d_rowf, (const short4*)t->d_colf, t->d_partial, t->d_err);
         return cudaGetLastError();
     };
-    if (t->ra == 2 && t->ca == 1) e = launch(tc_contract_kernel<2, 1>);
-    else if (t->ra == 2 && t->ca == 2) e = launch(tc_contract_kernel<2, 2>);
-    else if (t->ra == 2 && t->ca == 3) e = launch(tc_contract_kernel<2, 3>);
-    else if (t->ra == 3 && t->ca == 3) e = launch(tc_contract_kernel<3, 3>);
-    else e = launch(tc_contract_kernel<1, 1>);
+    auto launch_teams = [&](auto k2, auto k3) { return t->teams == 3 ? launch(k3, tc_threads(3)) : launch(k2, tc_threads(2)); };
+    if (t->ra == 2 && t->ca == 1) e = launch_teams(tc_contract_kernel<2, 1, 2>, tc_contract_kernel<2, 1, 3>);
+    else if (t->ra == 2 && t->ca == 2) e = launch_teams(tc_contract_kernel<2, 2, 2>, tc_contract_kernel<2, 2, 3>);
+    else if (t->ra == 2 && t->ca == 3) e = launch_teams(tc_contract_kernel<2, 3, 2>, tc_contract_kernel<2, 3, 3>);
+    else if (t->ra == 3 && t->ca == 3) e = launch_teams(tc_contract_kernel<3, 3, 2>, tc_contract_kernel<3, 3, 3>);
+    else e = launch_teams(tc_contract_kernel<1, 1, 2>, tc_contract_kernel<1, 1, 3>);
     if (e) return POLY_ERR_CUDA;
     if (p->timing) cudaEventRecord(p->ev[3], st);
     const int blocks = (int)std::min<int64_t>((p->nbins + 255) / 256, 4096);
