@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #define PS_DEV __device__ __forceinline__
 #define PS_HD __host__ __device__ __forceinline__
 
@@ -21,10 +23,29 @@ PS_HD Cx<T> cx(T r, T i) {
     c.im = i;
     return c;
 }
+// Sums and differences of single-precision complex numbers take one packed FP32 pair
+// instruction on sm_100 and later (each part rounded to nearest, as the scalar form;
+// a - b as fma(-1, b, a), exact before its one rounding).
 template <typename T>
-PS_HD Cx<T> cadd(Cx<T> a, Cx<T> b) { return cx<T>(a.re + b.re, a.im + b.im); }
+PS_HD Cx<T> cadd(Cx<T> a, Cx<T> b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    if constexpr (std::is_same_v<T, float>) {
+        const float2 r = __fadd2_rn(make_float2(a.re, a.im), make_float2(b.re, b.im));
+        return cx<float>(r.x, r.y);
+    }
+#endif
+    return cx<T>(a.re + b.re, a.im + b.im);
+}
 template <typename T>
-PS_HD Cx<T> csub(Cx<T> a, Cx<T> b) { return cx<T>(a.re - b.re, a.im - b.im); }
+PS_HD Cx<T> csub(Cx<T> a, Cx<T> b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    if constexpr (std::is_same_v<T, float>) {
+        const float2 r = __ffma2_rn(make_float2(-1.f, -1.f), make_float2(b.re, b.im), make_float2(a.re, a.im));
+        return cx<float>(r.x, r.y);
+    }
+#endif
+    return cx<T>(a.re - b.re, a.im - b.im);
+}
 template <typename T>
 PS_HD Cx<T> cmul(Cx<T> a, Cx<T> b) { return cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
 template <typename T>
