@@ -47,7 +47,16 @@ PS_HD Cx<T> csub(Cx<T> a, Cx<T> b) {
     return cx<T>(a.re - b.re, a.im - b.im);
 }
 template <typename T>
-PS_HD Cx<T> cmul(Cx<T> a, Cx<T> b) { return cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+PS_HD Cx<T> cmul(Cx<T> a, Cx<T> b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    if constexpr (std::is_same_v<T, float>) {  // (a.re b.re - a.im b.im, a.re b.im + a.im b.re) in two pair operations
+        const float2 t = __fmul2_rn(make_float2(a.im, a.im), make_float2(-b.im, b.re));
+        const float2 r = __ffma2_rn(make_float2(a.re, a.re), make_float2(b.re, b.im), t);
+        return cx<float>(r.x, r.y);
+    }
+#endif
+    return cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
 template <typename T>
 PS_HD Cx<T> cconj(Cx<T> a) { return cx<T>(a.re, -a.im); }
 template <typename T>
