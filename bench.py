@@ -44,10 +44,10 @@ def set_workload(n: int, nshell: int, order: int, width: float = 1.0, ell: int =
 SAMPLE_SHELLS = (59, 60, 61, 62, 63, 64)  # CPU baseline sample: the bins among these shells
 
 
-TC_SOURCES = ["contract_tc.cu", "tc.cuh"]
-CC_SOURCES = ["contract_cc.cu"]
-FIELD_SOURCES = ["fields_impl.cuh", "fields_f32.cu", "fft.cuh"]
-ADJ_SOURCES = ["adjoint_tc.cu", "tc.cuh"]
+TC_SOURCES = ["contract_tc.cu", "tc.cuh", "common.cuh"]
+CC_SOURCES = ["contract_cc.cu", "common.cuh"]
+FIELD_SOURCES = ["fields_impl.cuh", "fields_f32.cu", "fft.cuh", "common.cuh"]
+ADJ_SOURCES = ["adjoint_tc.cu", "tc.cuh", "common.cuh"]
 
 
 def load_peaks():
