@@ -92,7 +92,12 @@ typedef enum {
 poly_status poly_plan_create(poly_plan* out, int N, double L, int order, int nshell, const double* edges,
                              poly_precision prec, unsigned flags);
 
-/* Number of bins the plan outputs. */
+/*
+ * Number of bins the plan outputs (*nbins, host): the sorted shell tuples
+ * b = (k_1 >= ... >= k_n) of Sec. 4.2 that satisfy the polygon inequality on
+ * the shell centres (App. B, Eq. polygon), or every sorted tuple with
+ * POLY_BINS_ALL_SORTED.  Host only; POLY_ERR_ARG for a NULL argument.
+ */
 poly_status poly_plan_nbins(poly_plan plan, int64_t* nbins);
 
 /*
@@ -115,10 +120,19 @@ poly_status poly_plan_nbins(poly_plan plan, int64_t* nbins);
 poly_status poly_plan_create_multipole(poly_plan* out, int N, double L, int order, int nshell, const double* edges,
                                        poly_precision prec, unsigned flags, int ell);
 
-/* Bins as 1-based shell numbers, host array of nbins * order int32, paper order. */
+/*
+ * The bins (Sec. 4.2 order: row-major over k_1 >= k_2 >= ... >= k_n, k_n
+ * fastest) as 1-based shell numbers: idx, host, caller-owned, nbins * order
+ * int32, bin b at idx[b * order ..].  Host only; POLY_ERR_ARG for NULL.
+ */
 poly_status poly_plan_bins(poly_plan plan, int32_t* idx);
 
-/* Exact polygon counts count_b, host array of nbins int64 (Eq. Ncalc). */
+/*
+ * Exact polygon counts count_b = N^{-3} sum_x prod_t iota_{k_t}(x) (Eqs. Vn,
+ * Ncalc; the number of closed n-gons of grid modes), computed at plan creation:
+ * counts, host, caller-owned, nbins int64, in poly_plan_bins order.  Host only;
+ * POLY_ERR_ARG for NULL.
+ */
 poly_status poly_plan_counts(poly_plan plan, int64_t* counts);
 
 /*
@@ -145,11 +159,17 @@ poly_status poly_plan_bin_wraps(poly_plan plan, uint8_t* wraps);
 poly_status poly_plan_device_bytes(poly_plan plan, int64_t* bytes);
 
 /*
- * Estimate B_b for one field.  delta_x: device, N^3 real (float for POLY_FP32 /
+ * Estimate B_b for one field: the forward transform of delta_x, the shell
+ * fields D_k (Eq. Bkfast), the product sums S_b (Eq. estimator) and the
+ * normalisation by the plan's counts (App. A, final discrete form).
+ * delta_x: device, N^3 real (float for POLY_FP32 /
  * POLY_SPLIT_BF16, double for POLY_FP64).  out: device, nbins double, B_b.
  * scale_or_null: device, nbins double or NULL; if given, receives
  * sum_x |prod_t D_{k_t}(x)| / (N^3 count_b) (the scale of the stated error
- * bound), at the cost of a second contraction.  Asynchronous on `stream`.
+ * bound), at the cost of a second contraction.  Asynchronous on `stream`.  Both
+ * buffers are caller-owned and must not alias delta_x or each other
+ * (POLY_ERR_ARG); kernel faults and bounded-wait timeouts of the contraction
+ * surface from poly_plan_sync or the next call on the plan.
  */
 poly_status poly_estimate(poly_plan plan, const void* delta_x, double* out, double* scale_or_null, void* stream);
 
@@ -201,14 +221,20 @@ poly_status poly_trispectrum_full(poly_plan plan, const void* delta_x, const int
                                   double* T_out, int64_t* counts_out, double* scale_or_null, void* stream);
 
 /*
- * The same as poly_estimate with HOST buffers: copies delta_x (host, N^3 real)
- * to the device, estimates, copies B_b to out (host, nbins double) and
- * synchronises `stream` before returning.
+ * The same as poly_estimate (Eq. estimator, App. A) with HOST buffers: copies
+ * delta_x (host, N^3 real of the plan's input type, caller-owned; pinned
+ * memory makes the copy asynchronous to other host work) into the plan's
+ * workspace, estimates, copies B_b to out (host, nbins double, caller-owned)
+ * and synchronises `stream` before returning, so device errors are reported
+ * by this call.
  */
 poly_status poly_estimate_host(poly_plan plan, const void* delta_x_host, double* out_host, void* stream);
 
 /*
- * Gradient of L = sum_b dL_dB[b] * B_b with respect to delta(x).
+ * Gradient of L = sum_b dL_dB[b] * B_b with respect to delta(x) (no
+ * counterpart in the paper: the adjoint of Eq. estimator and Eq. Bkfast,
+ * dL/ddelta = sum_q mask_{m(q)} Ghat_{m(q)}(q) e^{+2 pi i q.x/N} with
+ * G_m = dL/dD_m).
  * dL_dB: device, nbins double.  dL_ddelta: device, N^3 real of the plan's
  * input type, overwritten.  Recomputes the shell fields from delta_x (it
  * never stores pair products), contracts dL/dB with products of the other
@@ -219,7 +245,8 @@ poly_status poly_estimate_host(poly_plan plan, const void* delta_x_host, double*
 poly_status poly_backward(poly_plan plan, const void* delta_x, const double* dL_dB, void* dL_ddelta, void* stream);
 
 /*
- * Estimate `count` fields, possibly of different plans (e.g. mock catalogues
+ * Estimate `count` fields (Eq. estimator for each; the batching has no
+ * counterpart in the paper), possibly of different plans (e.g. mock catalogues
  * on different grid sizes), in one stream-ordered batch: fields[i] is a device
  * pointer for plans[i] and outs[i] a device array of plans[i]'s nbins doubles.
  * Results are bit-identical to calling poly_estimate on each field.
@@ -252,13 +279,28 @@ poly_status poly_estimate_batched(const poly_plan* plans, const void* const* fie
  */
 poly_status poly_plan_tune(poly_plan plan, const void* delta_x, int* config_out, double* ms_out, void* stream);
 
-/* Apply a configuration code from poly_plan_tune (0: keep the current one). */
+/*
+ * Apply a configuration code from poly_plan_tune (0: keep the current one).
+ * POLY_ERR_ARG for a code poly_plan_tune does not produce.  A shape that
+ * fails to build (shared memory, allocation) returns its error and rebuilds
+ * the previous shape; if that fails too, later estimates of the plan return
+ * POLY_ERR_UNSUPPORTED.
+ */
 poly_status poly_plan_set_config(poly_plan plan, int config);
 
-/* Wait for the plan's work on `stream` and report device-side errors. */
+/*
+ * Wait for the plan's work on `stream` (host blocks) and report device-side
+ * errors: POLY_ERR_CUDA for a failed kernel or runtime call,
+ * POLY_ERR_TIMEOUT when a bounded wait inside a pipeline gave up (the
+ * context stays usable; the estimate's outputs are then undefined).
+ */
 poly_status poly_plan_sync(poly_plan plan, void* stream);
 
-/* Release the plan and its workspace (NULL is ignored). */
+/*
+ * Release the plan, its workspace and the batched graphs that use it (NULL
+ * is ignored).  The workspace is freed with cudaFree, which waits for the
+ * device's outstanding work; buffers passed to the plan stay the caller's.
+ */
 void poly_plan_destroy(poly_plan plan);
 
 /* Per-plan instrumentation: launch counter and CUDA events per stage. */
