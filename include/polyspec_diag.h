@@ -119,8 +119,11 @@ int poly_diag_host_tables(int N, int order, const double* edges, int nshell, uns
  * sms (the device's SM count), max_mt (M tiles per group) and
  * cta_mult (the block budget is sms x cta_mult / 2) as poly_plan_set_config
  * and the device would set them.
- *   sizes[7] (required) receives the counts: bins, blocks, groups, M tiles,
- *   runs, row factor records, column factor records.  Other pointers may be
+ *   sizes[9] (required) receives the counts: bins, blocks, groups, M tiles,
+ *   runs, row factor records, column factor records, then the launch's
+ *   producer teams (2 or 3) and its A/B slot cap (what shared memory holds;
+ *   a group's slots are also bounded by tensor memory: (512 - its
+ *   accumulator columns rounded up to 32) / (32 x its M tiles)).  Other pointers may be
  *   NULL or caller-owned host buffers:
  *   ctas   int64 [nblocks][3]: group, first chunk, end chunk (chunks of 32 cells);
  *   groups int32 [ngroups][5]: first M tile, M tiles, first column record,

@@ -659,6 +659,8 @@ struct TcTables {
     std::vector<int4> binmap;
 };
 
+static poly_status tc_launch_shape(const PsPlan* p, const std::vector<TcGroup>& groups, TcState* t);
+
 static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
     const int n = p->order;
     t->ra = n >= 6 ? 3 : (n >= 3 ? 2 : 1);
@@ -925,6 +927,30 @@ static poly_status tc_build_tables(const PsPlan* p, TcState* t, TcTables& h) {
         auto gs = slot_of.at(pack(rk, ck));
         binmap[i] = make_int4(first[gs.first], nsplit[gs.first], gs.second, 0);
     }
+    return tc_launch_shape(p, h.groups, t);
+}
+
+// Launch shape of the contraction from the groups (host only): TMA stage bytes, B buffer
+// bytes, accumulator columns, A/B slot cap, shared memory and the producer team count.
+static poly_status tc_launch_shape(const PsPlan* p, const std::vector<TcGroup>& groups, TcState* t) {
+    t->stage_bytes = (p->nfield * 128 + 1023) / 1024 * 1024;
+    int maxcol = 16, maxacc = 16;
+    for (auto& g : groups) {
+        maxcol = std::max(maxcol, g.ncol);
+        maxacc = std::max(maxacc, g.acc_cols);
+    }
+    t->bbuf_bytes = maxcol * kTcChunk * 2;
+    t->acc_max = maxacc;
+    t->slot_cap = kTcMaxSlots;  // B slots: as many as shared memory holds (the kernel also bounds them by TMEM)
+    while (t->slot_cap > 2 && tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc) > 227 * 1024)
+        t->slot_cap--;
+    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc);
+    if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
+    // a third producer team where every group has three A/B slots (the kernel's slot count:
+    // what tensor memory holds beside the group's accumulators, at most slot_cap)
+    int min_slots = t->slot_cap;
+    for (auto& g : groups) min_slots = std::min(min_slots, (512 - (g.acc_cols + 31) / 32 * 32) / (g.nmt * 32));
+    t->teams = min_slots >= 3 ? 3 : 2;
     return POLY_OK;
 }
 
@@ -966,24 +992,6 @@ poly_status ps_tc_prepare(PsPlan* p) {
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return POLY_ERR_CUDA;
-    t->stage_bytes = (p->nfield * 128 + 1023) / 1024 * 1024;
-    int maxcol = 16, maxacc = 16;
-    for (auto& g : groups) {
-        maxcol = std::max(maxcol, g.ncol);
-        maxacc = std::max(maxacc, g.acc_cols);
-    }
-    t->bbuf_bytes = maxcol * kTcChunk * 2;
-    t->acc_max = maxacc;
-    t->slot_cap = kTcMaxSlots;  // B slots: as many as shared memory holds (the kernel also bounds them by TMEM)
-    while (t->slot_cap > 2 && tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc) > 227 * 1024)
-        t->slot_cap--;
-    t->smem_bytes = (int)tc_smem_bytes(t->stage_bytes, t->bbuf_bytes, t->slot_cap, maxacc);
-    if (t->smem_bytes > 227 * 1024) return POLY_ERR_UNSUPPORTED;
-    // a third producer team where every group has three A/B slots (the kernel's slot count:
-    // what tensor memory holds beside the group's accumulators, at most slot_cap)
-    int min_slots = t->slot_cap;
-    for (auto& g : groups) min_slots = std::min(min_slots, (512 - (g.acc_cols + 31) / 32 * 32) / (g.nmt * 32));
-    t->teams = min_slots >= 3 ? 3 : 2;
     // Accumulation window (chunks of 32 cells summed in FP32 in tensor memory before a drain).
     // The tensor-core FP32 accumulation error grows with the window; at 256^3 the largest
     // error over the split-BF16 scale is 1.3e-6 for the bispectrum at 128 chunks (6e-7 at 64;
@@ -1009,9 +1017,9 @@ static int diag_tc_tables(int N, int order, const double* edges, int nshell, uns
     TcState t;
     TcTables h;
     if (poly_status s = tc_build_tables(&hp, &t, h)) return s;
-    const int64_t n[7] = {hp.nbins, (int64_t)t.ctas.size(), (int64_t)h.groups.size(), (int64_t)h.mtiles.size(),
-                          (int64_t)h.runs.size(), (int64_t)h.rowf.size(), (int64_t)h.colf.size()};
-    for (int i = 0; i < 7; i++) sizes[i] = n[i];
+    const int64_t n[9] = {hp.nbins, (int64_t)t.ctas.size(), (int64_t)h.groups.size(), (int64_t)h.mtiles.size(),
+                          (int64_t)h.runs.size(), (int64_t)h.rowf.size(), (int64_t)h.colf.size(), t.teams, t.slot_cap};
+    for (int i = 0; i < 9; i++) sizes[i] = n[i];
     for (size_t i = 0; ctas && i < t.ctas.size(); i++) {
         ctas[3 * i] = t.ctas[i].group;
         ctas[3 * i + 1] = t.ctas[i].c0;

@@ -163,18 +163,30 @@ def tc_tables(lib, N, order, edges, sms=152, max_mt=4, cta_mult=4, flags=0, ell=
                    ctypes.c_int, ctypes.c_int] + [P] * 8
     fn.restype = ctypes.c_int
     e = np.ascontiguousarray(edges, dtype=np.float64)
-    sizes = np.zeros(7, dtype=np.int64)
+    sizes = np.zeros(9, dtype=np.int64)
     args = (N, order, e.ctypes.data, e.size - 1, flags, ell, sms, max_mt, cta_mult)
     rc = fn(*args, sizes.ctypes.data, *([None] * 7))
     if rc:
         return rc, None
-    nb, nc, ng, nm, nr, nrow, ncol = (int(v) for v in sizes)
+    nb, nc, ng, nm, nr, nrow, ncol, teams, slot_cap = (int(v) for v in sizes)
     t = dict(ctas=np.zeros((nc, 3), np.int64), groups=np.zeros((ng, 5), np.int32), mtiles=np.zeros((nm, 3), np.int32),
              runs=np.zeros((nr, 4), np.int32), rowf=np.zeros((nrow, 3), np.int16), colf=np.zeros((ncol, 3), np.int16),
              binmap=np.zeros((nb, 3), np.int32))
     ptrs = [t[k].ctypes.data for k in ("ctas", "groups", "mtiles", "runs", "rowf", "colf", "binmap")]
     assert fn(*args, sizes.ctypes.data, *ptrs) == 0
+    t["teams"], t["slot_cap"] = teams, slot_cap
     return 0, t
+
+
+def check_pipeline_teams(t):
+    """Producer teams never outnumber a group's A/B slots: a team's parity wait on a slot's barrier is
+    unambiguous only while the slot's previous use is known complete, which its own previous wait implies
+    when teams <= slots (the kernel also caps its teams by the slots of its group)."""
+    g = t["groups"]
+    acc = (g[:, 4] + 31) // 32 * 32
+    slots = np.minimum(t["slot_cap"], (512 - acc) // (g[:, 1] * 32))
+    assert t["teams"] in (2, 3) and 2 <= t["slot_cap"] <= 4 and slots.min() >= 2
+    assert t["teams"] == (3 if slots.min() >= 3 else 2)
 
 
 def check_tc_tables(t, bins, N, nshell, max_mt, shift=0):
@@ -240,6 +252,9 @@ def test_tc_tables_bispectrum_256cube_64shells(lib, max_mt, cta_mult):
     rc, t = tc_tables(lib, 256, 3, e, 152, max_mt, cta_mult)
     assert rc == 0
     check_tc_tables(t, oracle.enumerate_bins(e, 3), 256, 64, max_mt)
+    check_pipeline_teams(t)
+    if max_mt >= 3:
+        assert t["teams"] == 3  # groups of three M tiles: three slots beside at most 176 accumulator columns
 
 
 @pytest.mark.parametrize("N,order,nshell,width", [(256, 4, 32, 1.5), (96, 4, 10, 2.0), (48, 3, 12, 1.0),
@@ -252,6 +267,9 @@ def test_tc_tables_other_plans(lib, N, order, nshell, width, sms):
     rc, t = tc_tables(lib, N, order, e, sms)
     assert rc == 0
     check_tc_tables(t, oracle.enumerate_bins(e, order), N, nshell, 4)
+    check_pipeline_teams(t)
+    if (N, order, nshell) == (256, 4, 32):
+        assert t["teams"] == 2  # the pair columns' B buffers leave shared memory for two slots
 
 
 @pytest.mark.parametrize("N,order,nshell,ell", [(256, 3, 64, 2), (48, 3, 12, 4), (32, 4, 6, 2), (64, 2, 20, 2)])
@@ -264,6 +282,7 @@ def test_tc_tables_multipole_plans(lib, N, order, nshell, ell, max_mt):
     assert rc == 0
     check_tc_tables(t, oracle.enumerate_bins(e, order), N, nshell, max_mt, shift=nshell)
     assert t["groups"][:, 4].max() <= 256
+    check_pipeline_teams(t)
 
 
 @pytest.mark.parametrize("kwargs,status", [
