@@ -189,6 +189,24 @@ def check_pipeline_teams(t):
     assert t["teams"] == (3 if slots.min() >= 3 else 2)
 
 
+def factor_wavefronts(t, which):
+    """Shared-memory wavefronts of one 16-byte factor load (the row factor `which`: 0 first, 1 second)
+    per producer warp, averaged over the M tiles' warps: a quarter warp reads 8 lanes in one wavefront
+    unless two of its lanes read different staged rows equal modulo 8 (the 128-byte swizzle puts those
+    in the same banks)."""
+    rowf, total, n = t["rowf"], 0, 0
+    for r0, _, _ in t["mtiles"]:
+        for q in range(4):
+            rows = rowf[r0 + 32 * q:r0 + 32 * q + 32, which]
+            for qq in range(4):
+                by = {}
+                for r in set(rows[8 * qq:8 * qq + 8].tolist()):
+                    by.setdefault(r & 7, set()).add(r)
+                total += max(len(v) for v in by.values())
+            n += 1
+    return total / n
+
+
 def check_tc_tables(t, bins, N, nshell, max_mt, shift=0):
     """shift: the first row factor's slot offset (nshell for a multipole plan's weighted fields)."""
     order = bins.shape[1]
@@ -255,6 +273,8 @@ def test_tc_tables_bispectrum_256cube_64shells(lib, max_mt, cta_mult):
     check_pipeline_teams(t)
     if max_mt >= 3:
         assert t["teams"] == 3  # groups of three M tiles: three slots beside at most 176 accumulator columns
+    # every factor load of the producers is a conflict-free broadcast: four wavefronts per 16-byte load
+    assert factor_wavefronts(t, 0) == 4.0 and factor_wavefronts(t, 1) == 4.0
 
 
 @pytest.mark.parametrize("N,order,nshell,width", [(256, 4, 32, 1.5), (96, 4, 10, 2.0), (48, 3, 12, 1.0),
