@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(tc_threads(TEAMS), 1)
             if (RA == 3) key3[m] = tc_row_key(f.z) ^ (uint32_t)(64 * half);
         }
         const int ttid = tid % (kTcTeamWarps * 32);
-        // stages team, team + 2, team + 4 in turn; slots i mod nslots
+        // stages team, team + nteams, ... in turn; slots i mod nslots
         const uint32_t abase0 = tmem + lane_base + (uint32_t)a0 + (uint32_t)(16 * half);
         const uint32_t Bbase = tc::smem_u32(s_b);
         const uint32_t sd0 = tc::smem_u32(s_d);
