@@ -83,6 +83,23 @@ def test_full_shape_matches_oracle(N, L, nshell, k, dedges, prec, seed):
     plan.close()
 
 
+@pytest.mark.parametrize("order,prec,ell", [(3, "split_bf16", 0), (4, "fp32", 0), (3, "fp32", 2), (3, "fp64", 0)])
+def test_any_plan_serves(order, prec, ell):
+    """The full-shape trispectrum takes only the plan's shells, grid and forward transform from it: plans of
+    other orders, the split-BF16 precision and a multipole plan give the oracle's T and counts."""
+    N, L, nshell, k = 24, 400.0, 5, (5, 4, 3, 3)
+    e = fieldgen.unit_edges(nshell)
+    delta = fieldgen.field("lognormal", N, 75, np.float64 if prec == "fp64" else np.float32)
+    de = unit_diagonals(10)
+    plan = ps.Plan(N, L, order, e, prec, 0, ell)
+    d = torch.from_numpy(np.ascontiguousarray(delta)).to("cuda", plan.real_dtype)
+    T, C, sc = plan.trispectrum_full(d, k, de, scale=True)
+    torch.cuda.synchronize()
+    ref = oracle.trispectrum_full(delta.astype(np.float64), L, e, k, de)
+    compare(T.cpu().numpy(), C.cpu().numpy(), ref, TOL[prec])
+    plan.close()
+
+
 def test_aliased_quadrilaterals_are_counted():
     """On 16^3 with shells up to 4.5, q1 = q2 = q3 = (4, 0, 0) closes with q4 = (4, 0, 0) only
     through the grid's periodicity: the device counts must include such quadrilaterals, as the
