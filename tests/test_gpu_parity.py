@@ -206,6 +206,38 @@ def test_higher_orders_refuse_the_adjoint():
     assert ei.value.status == 6
 
 
+# every contraction shape poly_plan_set_config accepts: M tiles per group 1..4, CTA budget 1/2..4 x the SMs
+TC_SHAPES = [mt | (mult << 4) for mt in (1, 2, 3, 4) for mult in (1, 2, 4, 6, 8)]
+
+
+@pytest.mark.parametrize("N,order,nshell,width,seed,sample", [
+    (128, 3, 40, 1.0, 81, {40, 39, 27, 26, 20, 13, 7, 2}),  # 1 to 4 groups; two producer teams at 4 M tiles
+    (48, 4, 7, 1.5, 82, None),
+])
+def test_every_contraction_shape_matches_oracle(N, order, nshell, width, seed, sample):
+    """The tuner's shapes change the groups, their A/B slots, the producer team count (two or three) and the
+    CTA split of the chunks; every one of them gives the oracle's B within the split-BF16 bar (on the bins
+    among the sampled shells where given)."""
+    L = 700.0
+    e = fieldgen.unit_edges(nshell, width)
+    bins = oracle.enumerate_bins(e, order)
+    idx = np.arange(len(bins)) if sample is None else np.array(
+        [i for i, b in enumerate(bins) if set(b.tolist()) <= sample])
+    delta = fieldgen.field("lognormal", N, seed, np.float32)
+    ref = oracle.estimate(delta.astype(np.float64), L, e, order, bins=bins[idx])
+    plan = ps.Plan(N, L, order, e, "split_bf16")
+    assert np.array_equal(plan.bins[idx], bins[idx])
+    d = torch.from_numpy(delta).cuda()
+    live = ref["counts"] > 0
+    for code in TC_SHAPES:
+        plan.set_config(code)
+        B = plan.estimate(d).cpu().numpy()[idx]
+        plan.sync()
+        err = np.abs(B[live] - ref["B"][live]) / (norm(L, N, order) * ref["scale"][live])
+        assert err.max() <= TOL["split_bf16"], (hex(code), err.max())
+    plan.close()
+
+
 @pytest.fixture(scope="module")
 def field256():
     return fieldgen.field("lognormal", 256, 2, np.float32)
